@@ -1,0 +1,188 @@
+"""FP64 CPU oracle for the Top-K feature render -- TEST INFRASTRUCTURE.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg import this
+package; the product path (the CUDA library and its binding) never does, and this
+package imports nothing from the product.  The arithmetic lives in gs_oracle.c
+(plain C, FP64), compiled here with gcc into oracle/_build/liboracle.so.
+
+Functions follow the paper's definitions:
+  project   -- EWA projection of each Gaussian (Sec. 3.1, after 3D Gaussian Splatting)
+  render    -- per pixel: Eq. 1 colour/depth, Eq. 2 Top-K set, Eq. 3 renormalised
+               weights, Eq. 4 feature
+  backward  -- the adjoint of the above (no counterpart in the paper; written out from
+               Eqs. 1-4 by the chain rule), chained through the projection to the 3D
+               mean and covariance.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# near-decision margins (relative): ellipse test, alpha test, stop test, Top-K tie, clamp
+DEFAULT_MARGINS = (2e-5, 2e-5, 2e-5, 1e-6, 2e-5)
+F_NEAR_Q, F_NEAR_ALPHA, F_NEAR_TERM, F_NEAR_TIE, F_NEAR_CLAMP = 1, 2, 4, 8, 16
+F_SET_FRAGILE = F_NEAR_Q | F_NEAR_ALPHA | F_NEAR_TERM   # may change the contributor set
+P_VALID, P_X, P_Y, P_Z, P_U, P_V, P_SA, P_SB, P_SC, P_CA, P_CB, P_CC, P_ZF = range(13)
+
+
+def build(force: bool = False) -> str:
+    """Compile gs_oracle.c into a shared library (gcc, -O2, FP64, no fast-math)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB_PATH)
+                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            return _LIB_PATH
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
+                               "-ffp-contract=off", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        # GS_ORACLE_LIB lets the mutation test load a deliberately broken copy
+        lib = ctypes.CDLL(os.environ.get("GS_ORACLE_LIB") or build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        i = ctypes.c_int
+        lib.or_project.argtypes = [i, dp, dp, dp, dp]
+        lib.or_render.argtypes = [i, dp, dp, dp, dp, i, i, i, dp, dp, dp, dp, dp, ip, ip, dp, dp, ip]
+        lib.or_backward.argtypes = [i, dp, dp, dp, dp, i, i, i, dp, dp, dp, dp, dp,
+                                    dp, dp, dp, dp, dp, dp]
+        lib.or_backward_project.argtypes = [i, dp, dp, dp, dp, dp, dp, dp, dp]
+        lib.or_pixel_walk.argtypes = [i, dp, dp, ctypes.c_double, ctypes.c_double, dp, i, ip, dp, dp, ip]
+        _lib = lib
+        global PROJ_LEN, CAM_LEN
+        PROJ_LEN = lib.or_proj_len()
+        CAM_LEN = lib.or_cam_len()
+    return _lib
+
+
+PROJ_LEN = 17
+CAM_LEN = 19
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def cam_array(cam) -> np.ndarray:
+    vm = np.asarray(cam.viewmat, dtype=np.float64)
+    return np.concatenate([vm[:3, :3].ravel(), vm[:3, 3],
+                           [cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height, cam.near]])
+
+
+def pixel_centres(cam, pixels=None) -> np.ndarray:
+    """(P, 2) pixel-centre coordinates; pixels is None (all, row-major) or flat indices."""
+    if pixels is None:
+        pixels = np.arange(cam.width * cam.height)
+    pixels = np.asarray(pixels, dtype=np.int64)
+    return np.stack([pixels % cam.width + 0.5, pixels // cam.width + 0.5], axis=1).astype(np.float64)
+
+
+def project(scene, cam) -> np.ndarray:
+    L = _L()
+    n = scene.n
+    mean, pm = _d(scene.mean3d)
+    cov, pc = _d(scene.cov3d)
+    ca, pca = _d(cam_array(cam))
+    out, po = _d(np.zeros((n, PROJ_LEN)))
+    L.or_project(n, pm, pc, pca, po)
+    return out
+
+
+def render(scene, cam, K, pixels=None, proj=None, margins=DEFAULT_MARGINS, feats=None):
+    """Forward render at the given pixels (flat row-major indices, default: all).
+    feats overrides scene.feats (e.g. with bf16-rounded rows)."""
+    L = _L()
+    if proj is None:
+        proj = project(scene, cam)
+    feats = scene.feats if feats is None else feats
+    n, D = scene.n, feats.shape[1]
+    pxy, ppx = _d(pixel_centres(cam, pixels))
+    P = pxy.shape[0]
+    pr, ppr = _d(proj)
+    op, pop = _d(scene.opacity)
+    rgb, prgb = _d(scene.rgb)
+    ft, pft = _d(feats)
+    mg, pmg = _d(np.asarray(margins, dtype=np.float64))
+    C, pC = _d(np.zeros((P, 3)))
+    Dp, pD = _d(np.zeros(P))
+    T, pT = _d(np.zeros(P))
+    nc, pnc = _i(np.zeros(P))
+    idx, pidx = _i(np.zeros((P, K)))
+    w, pw = _d(np.zeros((P, K)))
+    F, pF = _d(np.zeros((P, D)))
+    fl, pfl = _i(np.zeros(P))
+    L.or_render(n, ppr, pop, prgb, pft, D, K, P, ppx, pmg, pC, pD, pT, pnc, pidx, pw, pF, pfl)
+    return dict(C=C, D=Dp, T=T, n=nc, idx=idx, w=w, F=F, flags=fl)
+
+
+def pixel_walk(scene, cam, px, py, proj=None, margins=DEFAULT_MARGINS, cap=4096):
+    """Contributors of one pixel centre (px, py) in walk order: (ids, alpha, T, w), T_final, flags."""
+    L = _L()
+    if proj is None:
+        proj = project(scene, cam)
+    pr, ppr = _d(proj)
+    op, pop = _d(scene.opacity)
+    mg, pmg = _d(np.asarray(margins, dtype=np.float64))
+    g, pg = _i(np.zeros(cap))
+    awt, pawt = _d(np.zeros((cap, 3)))
+    Tf, pTf = _d(np.zeros(1))
+    fl, pfl = _i(np.zeros(1))
+    nc = L.or_pixel_walk(scene.n, ppr, pop, float(px), float(py), pmg, cap, pg, pawt, pTf, pfl)
+    m = min(nc, cap)
+    return g[:m].copy(), awt[:m, 0].copy(), awt[:m, 1].copy(), awt[:m, 2].copy(), float(Tf[0]), int(fl[0])
+
+
+def backward(scene, cam, K, dF, dC, dD, pixels=None, proj=None, margins=DEFAULT_MARGINS, feats=None):
+    """Gradients of L with upstream dL/dF (P, D), dL/dC (P, 3), dL/dD (P,) at the given
+    pixels.  Returns per-Gaussian FP64 arrays: mean2d (n,2), conic (n,3), opac (n),
+    rgb (n,3), depth (n), feat (n,D), mean3d (n,3), cov3d (n,6)."""
+    L = _L()
+    if proj is None:
+        proj = project(scene, cam)
+    feats = scene.feats if feats is None else feats
+    n, D = scene.n, feats.shape[1]
+    pxy, ppx = _d(pixel_centres(cam, pixels))
+    P = pxy.shape[0]
+    pr, ppr = _d(proj)
+    op, pop = _d(scene.opacity)
+    rgb, prgb = _d(scene.rgb)
+    ft, pft = _d(feats)
+    mg, pmg = _d(np.asarray(margins, dtype=np.float64))
+    dF_, pdF = _d(np.asarray(dF).reshape(P, D))
+    dC_, pdC = _d(np.asarray(dC).reshape(P, 3))
+    dD_, pdD = _d(np.asarray(dD).reshape(P))
+    g2, pg2 = _d(np.zeros((n, 2)))
+    gq, pgq = _d(np.zeros((n, 3)))
+    go, pgo = _d(np.zeros(n))
+    gr, pgr = _d(np.zeros((n, 3)))
+    gz, pgz = _d(np.zeros(n))
+    gf, pgf = _d(np.zeros((n, D)))
+    L.or_backward(n, ppr, pop, prgb, pft, D, K, P, ppx, pmg, pdF, pdC, pdD, pg2, pgq, pgo, pgr, pgz, pgf)
+    cov, pcov = _d(scene.cov3d)
+    ca, pca = _d(cam_array(cam))
+    gm, pgm = _d(np.zeros((n, 3)))
+    gc, pgc = _d(np.zeros((n, 6)))
+    L.or_backward_project(n, pcov, pca, ppr, pg2, pgq, pgz, pgm, pgc)
+    return dict(mean2d=g2, conic=gq, opac=go, rgb=gr, depth=gz, feat=gf, mean3d=gm, cov3d=gc)
