@@ -1,0 +1,176 @@
+/*
+ * gs_topk.h -- C ABI of the Top-K feature renderer (B300, sm_103a).
+ *
+ * The library renders colour, depth and a D-dimensional language feature per pixel
+ * from 3D Gaussians, and back-propagates a loss to the Gaussians:
+ *   colour / depth  C(p) = sum_i c_i w_i,  D(p) = sum_i z_i w_i           (Sec. 3.1, Eq. 1)
+ *   weights         w_i = alpha_i prod_{j<i} (1 - alpha_j), front to back  (Eq. 1; Sec. 3.3 text of Eq. 8)
+ *   Top-K set       the K contributors of largest w                        (Sec. 3.2, Eq. 2)
+ *   renormalised    w'_k = w_k / sum_{j in K} w_j                          (Eq. 3)
+ *   feature         F(p) = sum_{k in K} w'_k f_k                           (Eq. 4)
+ * Colour and depth keep the full alpha blend; only the feature uses Top-K (Sec. 3.2).
+ * The projection and the per-pixel constants follow 3D Gaussian Splatting, which
+ * Sec. 3.1 defers to: EWA covariance with a 0.3 px^2 dilation, alpha = min(0.99,
+ * o exp(-q/2)); a Gaussian takes part at a pixel iff q <= 9, alpha >= 1/255 and the
+ * transmittance would stay >= 1e-4.  Pixel (i, j) is sampled at (i + 0.5, j + 0.5).
+ *
+ * Conventions for every call
+ *   - All array pointers are DEVICE memory owned by the caller (camera and config
+ *     structs are host memory, read during the call).  The library never allocates
+ *     device memory: scratch lives in the caller's workspace `ws` of at least
+ *     gs_workspace_size() bytes, 256-byte aligned.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream); none synchronises except gs_sync_status().
+ *   - Return value: GS_OK or an error code below.  Argument errors are detected on
+ *     the host before anything is launched.  Data-dependent failures (instance
+ *     overflow) are recorded in a device error word inside `ws`; kernels of later
+ *     calls on the same workspace skip their work once it is set, and
+ *     gs_sync_status() reads it back.
+ *   - Layouts: row-major; Gaussians are indexed 0..N-1; the pixels of camera c occupy
+ *     the flat range [pix_off(c), pix_off(c) + W_c H_c) of every per-pixel array,
+ *     pix_off(c) being the sum of W H over cameras 0..c-1; within a camera pixel
+ *     (x, y) is x + W y.  Feature rows (N x D) start 16-byte aligned, D is a multiple
+ *     of 8.
+ *   - One render = gs_preprocess, gs_bin_sort, gs_topk_select, gs_feature_blend in
+ *     this order on one workspace, which must stay untouched until gs_backward of
+ *     that render has run.
+ */
+#ifndef GS_TOPK_H
+#define GS_TOPK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_MAX_CAMERAS 16
+#define GS_MAX_K 32
+#define GS_PROJ_FLOATS 16      /* floats per (camera, Gaussian) projected record */
+
+enum gs_status_code {
+    GS_OK = 0,
+    GS_ERR_ARG = 1,            /* bad argument (null pointer, size, unsupported shape) */
+    GS_ERR_WORKSPACE = 2,      /* workspace smaller than gs_workspace_size() or misaligned */
+    GS_ERR_CUDA = 3,           /* a CUDA launch or runtime call failed */
+    GS_ERR_TIMEOUT = 4,        /* a bounded device-side wait ran out */
+    GS_ERR_OVERFLOW = 5,       /* more (Gaussian, tile) instances than the configured capacity */
+    GS_ERR_UNSUPPORTED = 6     /* configuration not compiled into this library */
+};
+
+enum gs_dtype { GS_F32 = 0, GS_BF16 = 1 };
+
+/* Pinhole camera.  viewmat: row-major 4x4 world->camera transform (camera looks
+ * along +z, x right, y down).  u = fx x/z + cx, v = fy y/z + cy. */
+typedef struct {
+    float viewmat[16];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_z;              /* Gaussians with camera depth <= near_z are culled */
+} gs_camera;
+
+/* Render configuration. */
+typedef struct {
+    int32_t K;                 /* Top-K size, 1..GS_MAX_K */
+    int32_t D;                 /* feature width, multiple of 8, 8..1024 */
+    int32_t tile_w, tile_h;    /* screen tile: 16x16, 32x8, 16x8 or 8x8 */
+    int32_t feat_dtype;        /* GS_F32 or GS_BF16: feature rows, F and dL/dF */
+    int32_t max_instances;     /* capacity of (Gaussian, tile) instances; 0: 32 per (camera, Gaussian) */
+} gs_config;
+
+/* Per-Gaussian gradient outputs of gs_backward (device, caller-allocated, fully
+ * overwritten).  feat is N x D float32 whatever the feature dtype.  mean2d and conic
+ * are per camera: n_cams x N x 2 and n_cams x N x 3, conic as (a, b, c) with
+ * q = a dx^2 + 2 b dx dy + c dy^2 and d = pixel - mean2d; they may be NULL. */
+typedef struct {
+    float *feat;               /* N x D  */
+    float *opacity;            /* N      */
+    float *rgb;                /* N x 3  */
+    float *mean3d;             /* N x 3  */
+    float *cov3d;              /* N x 6 (xx, xy, xz, yy, yz, zz); an off-diagonal entry stands for both symmetric entries */
+    float *mean2d;             /* n_cams x N x 2, or NULL */
+    float *conic;              /* n_cams x N x 3, or NULL */
+} gs_grads;
+
+/* Human-readable name of a status code (static string). */
+const char *gs_status_string(int status);
+
+/* Library version and the compute capability it was built for (e.g. 103). */
+int gs_version(int *major, int *minor, int *built_sm);
+
+/* Workspace bytes needed by one render (forward and backward) of n_gauss Gaussians
+ * seen by n_cams cameras under cfg.  Returns 0 on a bad argument. */
+size_t gs_workspace_size(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss);
+
+/* Total pixel count of the cameras (the P of every per-pixel array); -1 on a bad argument. */
+int64_t gs_pixel_count(const gs_camera *cams, int32_t n_cams);
+
+/* a1. EWA projection (Sec. 3.1, after 3DGS).  Inputs: mean3d N x 3, cov3d N x 6
+ * (xx, xy, xz, yy, yz, zz), opacity N, rgb N x 3, all float32.  Output proj:
+ * n_cams x N records of GS_PROJ_FLOATS floats (16-byte aligned); a culled Gaussian
+ * (depth <= near_z, or opacity too low to ever reach alpha >= 1/255) gets a record
+ * with zero extent.  Also clears the workspace error word. */
+int gs_preprocess(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                  const float *mean3d, const float *cov3d, const float *opacity, const float *rgb,
+                  float *proj, void *ws, size_t ws_bytes, void *stream);
+
+/* a2. Tile binning: every (camera, Gaussian) is duplicated into each screen tile its
+ * footprint box overlaps, and the instances are ordered by (tile, depth) with the
+ * library's own device radix sort; per-tile instance ranges stay in ws.  Instance
+ * overflow sets GS_ERR_OVERFLOW in the error word. */
+int gs_bin_sort(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                const float *proj, void *ws, size_t ws_bytes, void *stream);
+
+/* a3. Front-to-back walk of each pixel's tile list (Eq. 1) keeping the pixel's
+ * Top-K contributors (Eq. 2).  Outputs (P = gs_pixel_count): rgb_out P x 3, depth_out
+ * P, T_final P (transmittance after the walk), n_contrib P (contributor count),
+ * topk_idx P x K (Gaussian ids by descending w, -1 padded), topk_w P x K (the raw
+ * weights w, 0 padded). */
+int gs_topk_select(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                   const float *proj, void *ws, size_t ws_bytes,
+                   float *rgb_out, float *depth_out, float *T_final, int32_t *n_contrib,
+                   int32_t *topk_idx, float *topk_w, void *stream);
+
+/* a4. Gather-blend (Eqs. 3-4): F[p] = sum_k (w_k / S_p) feats[idx_k], S_p = sum_k w_k,
+ * F[p] = 0 where S_p = 0.  feats: N x D rows of cfg->feat_dtype; F_out: n_pix x D of
+ * cfg->feat_dtype (accumulation is float32 either way).  Needs no workspace. */
+int gs_feature_blend(const gs_config *cfg, int64_t n_pix, int32_t n_gauss, const int32_t *topk_idx,
+                     const float *topk_w, const void *feats, void *F_out, void *stream);
+
+/* a5. Adjoint of a1-a4.  Takes the forward inputs and outputs and the upstream
+ * gradients dL_dF (P x D, cfg->feat_dtype), dL_dC (P x 3), dL_dD (P), and writes
+ * every gradient in `grads`.  The walk is recomputed, not stored; feature gradients
+ * are reduced per Gaussian after a sort of the Top-K (pixel, slot) pairs by
+ * Gaussian, and geometry gradients per (Gaussian, tile) instance, without atomics,
+ * so the results are deterministic. */
+int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                const float *mean3d, const float *cov3d, const float *opacity, const float *rgb,
+                const void *feats, const float *proj,
+                const float *rgb_out, const float *depth_out, const int32_t *topk_idx, const float *topk_w,
+                const void *dL_dF, const float *dL_dC, const float *dL_dD,
+                const gs_grads *grads, void *ws, size_t ws_bytes, void *stream);
+
+/* Training loss of the benchmark workloads (Eqs. 5-7 leave the weights and the
+ * feature distance open; this one takes 1 - cosine for the feature, as the workload
+ * specifies): L = w_feat mean_p(1 - cos(F_p, Fgt_p)) + w_rgb mean_p |C_p - Cgt_p|_1 / 3
+ * + w_depth mean_p |D_p - Dgt_p|; a pixel with |F_p| = 0 or |Fgt_p| = 0 contributes
+ * w_feat to the cosine term and no gradient.  Writes dL_dF (P x D, cfg->feat_dtype),
+ * dL_dC, dL_dD and the scalar loss (device float, summed in a fixed order).
+ * `scratch` is caller device memory of gs_loss_scratch_size(n_pix) bytes. */
+size_t gs_loss_scratch_size(int64_t n_pix);
+int gs_loss_cos_l1(const gs_config *cfg, int64_t n_pix, const void *F, const void *F_gt,
+                   const float *rgb, const float *rgb_gt, const float *depth, const float *depth_gt,
+                   float w_feat, float w_rgb, float w_depth,
+                   void *dL_dF, float *dL_dC, float *dL_dD, float *loss,
+                   void *scratch, size_t scratch_bytes, void *stream);
+
+/* Synchronises `stream` and returns the workspace error word as a status (GS_OK if
+ * clear).  If n_instances is not NULL it receives the instance count of the last
+ * gs_bin_sort. */
+int gs_sync_status(const void *ws, size_t ws_bytes, void *stream, int64_t *n_instances);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_TOPK_H */

@@ -86,9 +86,13 @@ def _i(a):
 
 
 def cam_array(cam) -> np.ndarray:
-    vm = np.asarray(cam.viewmat, dtype=np.float64)
-    return np.concatenate([vm[:3, :3].ravel(), vm[:3, 3],
-                           [cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height, cam.near]])
+    """Camera as the oracle's 19 doubles.  Every value is first rounded to float32,
+    the precision in which a renderer receives its camera, so that both sides start
+    from identical parameters."""
+    vm = np.asarray(cam.viewmat, dtype=np.float32).astype(np.float64)
+    intr = np.asarray([cam.fx, cam.fy, cam.cx, cam.cy], dtype=np.float32).astype(np.float64)
+    return np.concatenate([vm[:3, :3].ravel(), vm[:3, 3], intr,
+                           [cam.width, cam.height, float(np.float32(cam.near))]])
 
 
 def pixel_centres(cam, pixels=None) -> np.ndarray:

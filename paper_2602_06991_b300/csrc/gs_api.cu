@@ -1,0 +1,312 @@
+// gs_api.cu -- the extern "C" entry points of include/gs_topk.h: argument checks,
+// workspace layout, camera tables and the launch sequence of each stage.
+#include "gs_internal.cuh"
+
+#include <string.h>
+
+#ifndef GS_BUILT_SM
+#define GS_BUILT_SM 0
+#endif
+
+namespace gs {
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static bool tile_ok(int tw, int th)
+{
+    return (tw == 16 && th == 16) || (tw == 32 && th == 8) || (tw == 16 && th == 8) || (tw == 8 && th == 8);
+}
+
+static bool cfg_ok(const gs_config *cfg)
+{
+    return cfg && cfg->K >= 1 && cfg->K <= GS_MAX_K && cfg->D >= 8 && cfg->D <= 1024 && cfg->D % 8 == 0 &&
+           tile_ok(cfg->tile_w, cfg->tile_h) && (cfg->feat_dtype == GS_F32 || cfg->feat_dtype == GS_BF16) &&
+           cfg->max_instances >= 0;
+}
+
+static bool cams_ok(const gs_camera *cams, int n_cams)
+{
+    if (!cams || n_cams < 1 || n_cams > GS_MAX_CAMERAS) return false;
+    for (int c = 0; c < n_cams; ++c) {
+        const gs_camera &k = cams[c];
+        if (k.width < 1 || k.height < 1 || k.width > 32768 || k.height > 32768) return false;
+        if (!(k.fx > 0.f) || !(k.fy > 0.f) || !(k.near_z > 0.f)) return false;
+    }
+    return true;
+}
+
+bool make_camtable(const gs_config *cfg, const gs_camera *cams, int n_cams, CamTable &ct)
+{
+    memset(&ct, 0, sizeof(ct));
+    ct.n = n_cams;
+    ct.tile_w = cfg->tile_w;
+    ct.tile_h = cfg->tile_h;
+    int tile_off = 0;
+    long long pix_off = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        const gs_camera &k = cams[c];
+        CamDev &d = ct.c[c];
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) d.R[3 * i + j] = k.viewmat[4 * i + j];
+            d.t[i] = k.viewmat[4 * i + 3];
+        }
+        d.fx = k.fx; d.fy = k.fy; d.cx = k.cx; d.cy = k.cy;
+        d.near_z = k.near_z;
+        d.limx = kFrustumClamp * ((float)k.width / (2.0f * k.fx));
+        d.limy = kFrustumClamp * ((float)k.height / (2.0f * k.fy));
+        d.W = k.width; d.H = k.height;
+        d.tiles_x = (k.width + cfg->tile_w - 1) / cfg->tile_w;
+        d.tiles_y = (k.height + cfg->tile_h - 1) / cfg->tile_h;
+        d.tile_off = tile_off;
+        d.pix_off = pix_off;
+        tile_off += d.tiles_x * d.tiles_y;
+        pix_off += (long long)k.width * k.height;
+    }
+    ct.n_tiles = tile_off;
+    return true;
+}
+
+bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N, WsLayout &L)
+{
+    if (!cfg_ok(cfg) || !cams_ok(cams, n_cams) || N < 0) return false;
+    memset(&L, 0, sizeof(L));
+    CamTable ct;
+    make_camtable(cfg, cams, n_cams, ct);
+    L.N = N; L.K = cfg->K; L.D = cfg->D; L.n_cams = n_cams; L.n_tiles = ct.n_tiles;
+    L.NE = (long long)n_cams * N;
+    L.P = 0;
+    for (int c = 0; c < n_cams; ++c) L.P += (long long)cams[c].width * cams[c].height;
+    L.PK = L.P * cfg->K;
+    long long mcap = cfg->max_instances > 0 ? cfg->max_instances : 32 * L.NE;
+    if (mcap < 4096) mcap = 4096;
+    if (mcap > 0x7fffffffll) mcap = 0x7fffffffll;
+    L.Mcap = mcap;
+    L.n_pairs = N + L.PK;
+    if (L.NE > 0x7fffffffll || L.n_pairs > 0x7fffffffll) return false;
+    L.max_pieces = N + (L.PK + kPieceLen - 1) / kPieceLen + 1;
+    L.max_multi_rows = 2 * ((L.PK + kPieceLen - 1) / kPieceLen) + 1;
+    L.inst_sorted = sorted_buffer(bits_for(L.n_tiles));
+    L.pair_bits = bits_for((long long)N + 1);
+    L.pair_sorted = sorted_buffer(L.pair_bits);
+    L.rank_sorted = sorted_buffer(30);
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes > 0 ? bytes : 1); return o; };
+    const size_t u = sizeof(uint32_t);
+    L.header = take(256);
+    for (int i = 0; i < 2; ++i) L.depth_keys[i] = take(u * L.NE);
+    for (int i = 0; i < 2; ++i) L.depth_vals[i] = take(u * L.NE);
+    L.elem_cnt = take(u * L.NE);
+    L.elem_off = take(u * L.NE);
+    L.counts = take(u * L.NE);
+    for (int i = 0; i < 2; ++i) L.inst_keys[i] = take(u * L.Mcap);
+    for (int i = 0; i < 2; ++i) L.inst_vals[i] = take(u * L.Mcap);
+    L.inst_elem = take(u * L.Mcap);
+    L.tile_range = take(8 * (size_t)L.n_tiles);
+    L.sort_hist = take(u * 256 * kSortBlocks);
+    L.scan_aux = take(u * (kSortBlocks + 32));
+    L.inst_grad = take(sizeof(float) * kGradVals * L.Mcap);
+    for (int i = 0; i < 2; ++i) L.rank_keys[i] = take(u * N);
+    for (int i = 0; i < 2; ++i) L.rank_vals[i] = take(u * N);
+    L.grank = take(u * N);
+    for (int i = 0; i < 2; ++i) L.pair_keys[i] = take(u * L.n_pairs);
+    for (int i = 0; i < 2; ++i) L.pair_vals[i] = take(u * L.n_pairs);
+    L.hbuf = take(sizeof(float) * L.PK);
+    L.seg_start = take(u * N);
+    L.seg_end = take(u * N);
+    L.pieces = take(u * N);
+    L.piece_off = take(u * N);
+    L.multi = take(u * N);
+    L.multi_off = take(u * N);
+    L.piece_rank = take(u * L.max_pieces);
+    L.piece_rows = take(sizeof(float) * (size_t)L.max_multi_rows * cfg->D);
+    L.loss_part = 0;
+    L.total = off;
+    return true;
+}
+
+static int ws_check(const WsLayout &L, const void *ws, size_t ws_bytes)
+{
+    if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < L.total) return GS_ERR_WORKSPACE;
+    return GS_OK;
+}
+
+static int launch_status()
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+const char *gs_status_string(int status)
+{
+    switch (status) {
+    case GS_OK: return "ok";
+    case GS_ERR_ARG: return "invalid argument";
+    case GS_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+    case GS_ERR_CUDA: return "CUDA launch or runtime error";
+    case GS_ERR_TIMEOUT: return "a bounded device-side wait ran out";
+    case GS_ERR_OVERFLOW: return "instance capacity exceeded (raise gs_config.max_instances)";
+    case GS_ERR_UNSUPPORTED: return "configuration not compiled into this library";
+    }
+    return "unknown status";
+}
+
+int gs_version(int *major, int *minor, int *built_sm)
+{
+    if (major) *major = 0;
+    if (minor) *minor = 1;
+    if (built_sm) *built_sm = GS_BUILT_SM;
+    return GS_OK;
+}
+
+size_t gs_workspace_size(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss)
+{
+    WsLayout L;
+    if (!make_layout(cfg, cams, n_cams, n_gauss, L)) return 0;
+    return L.total;
+}
+
+int64_t gs_pixel_count(const gs_camera *cams, int32_t n_cams)
+{
+    if (!cams_ok(cams, n_cams)) return -1;
+    int64_t P = 0;
+    for (int c = 0; c < n_cams; ++c) P += (int64_t)cams[c].width * cams[c].height;
+    return P;
+}
+
+int gs_preprocess(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                  const float *mean3d, const float *cov3d, const float *opacity, const float *rgb,
+                  float *proj, void *ws, size_t ws_bytes, void *stream)
+{
+    WsLayout L;
+    if (!make_layout(cfg, cams, n_cams, n_gauss, L)) return GS_ERR_ARG;
+    if (n_gauss > 0 && (!mean3d || !cov3d || !opacity || !rgb || !proj)) return GS_ERR_ARG;
+    if (((uintptr_t)proj & 15) != 0) return GS_ERR_ARG;
+    int st = ws_check(L, ws, ws_bytes);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CamTable ct;
+    make_camtable(cfg, cams, n_cams, ct);
+    cudaMemsetAsync(ws_ptr<char>(ws, L.header), 0, 16, s);
+    launch_preprocess(ct, n_gauss, mean3d, cov3d, opacity, rgb, proj, s);
+    return launch_status();
+}
+
+int gs_bin_sort(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                const float *proj, void *ws, size_t ws_bytes, void *stream)
+{
+    WsLayout L;
+    if (!make_layout(cfg, cams, n_cams, n_gauss, L)) return GS_ERR_ARG;
+    if (n_gauss > 0 && !proj) return GS_ERR_ARG;
+    int st = ws_check(L, ws, ws_bytes);
+    if (st) return st;
+    CamTable ct;
+    make_camtable(cfg, cams, n_cams, ct);
+    launch_bin_sort(ct, L, n_gauss, proj, ws, (cudaStream_t)stream);
+    return launch_status();
+}
+
+int gs_topk_select(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                   const float *proj, void *ws, size_t ws_bytes,
+                   float *rgb_out, float *depth_out, float *T_final, int32_t *n_contrib,
+                   int32_t *topk_idx, float *topk_w, void *stream)
+{
+    WsLayout L;
+    if (!make_layout(cfg, cams, n_cams, n_gauss, L)) return GS_ERR_ARG;
+    if ((n_gauss > 0 && !proj) || !rgb_out || !depth_out || !T_final || !n_contrib || !topk_idx || !topk_w)
+        return GS_ERR_ARG;
+    int st = ws_check(L, ws, ws_bytes);
+    if (st) return st;
+    CamTable ct;
+    make_camtable(cfg, cams, n_cams, ct);
+    if (!launch_walk_fwd(ct, L, cfg->K, n_gauss, proj, ws, rgb_out, depth_out, T_final, n_contrib, topk_idx, topk_w,
+                         (cudaStream_t)stream))
+        return GS_ERR_UNSUPPORTED;
+    return launch_status();
+}
+
+int gs_feature_blend(const gs_config *cfg, int64_t n_pix, int32_t n_gauss, const int32_t *topk_idx,
+                     const float *topk_w, const void *feats, void *F_out, void *stream)
+{
+    if (!cfg_ok(cfg) || n_pix < 0 || n_gauss < 0) return GS_ERR_ARG;
+    if (n_pix > 0 && (!topk_idx || !topk_w || !F_out)) return GS_ERR_ARG;
+    if (n_gauss > 0 && !feats) return GS_ERR_ARG;
+    if (((uintptr_t)feats & 15) != 0 || ((uintptr_t)F_out & 15) != 0) return GS_ERR_ARG;
+    if (!launch_blend(cfg->feat_dtype, cfg->K, cfg->D, n_pix, topk_idx, topk_w, feats, F_out, nullptr,
+                      (cudaStream_t)stream))
+        return GS_ERR_UNSUPPORTED;
+    return launch_status();
+}
+
+int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                const float *mean3d, const float *cov3d, const float *opacity, const float *rgb,
+                const void *feats, const float *proj,
+                const float *rgb_out, const float *depth_out, const int32_t *topk_idx, const float *topk_w,
+                const void *dL_dF, const float *dL_dC, const float *dL_dD,
+                const gs_grads *grads, void *ws, size_t ws_bytes, void *stream)
+{
+    WsLayout L;
+    if (!make_layout(cfg, cams, n_cams, n_gauss, L)) return GS_ERR_ARG;
+    if (!grads || !rgb_out || !depth_out || !topk_idx || !topk_w || !dL_dF || !dL_dC || !dL_dD) return GS_ERR_ARG;
+    if (n_gauss > 0 && (!mean3d || !cov3d || !opacity || !rgb || !feats || !proj || !grads->feat ||
+                        !grads->opacity || !grads->rgb || !grads->mean3d || !grads->cov3d))
+        return GS_ERR_ARG;
+    if (((uintptr_t)feats & 15) != 0 || ((uintptr_t)dL_dF & 15) != 0 || ((uintptr_t)grads->feat & 15) != 0)
+        return GS_ERR_ARG;
+    int st = ws_check(L, ws, ws_bytes);
+    if (st) return st;
+    if (n_gauss == 0) return GS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    CamTable ct;
+    make_camtable(cfg, cams, n_cams, ct);
+    if (!launch_feature_grad(L, cfg->feat_dtype, n_gauss, mean3d, topk_idx, topk_w, feats, dL_dF, grads->feat, ws, s))
+        return GS_ERR_UNSUPPORTED;
+    if (!launch_walk_bwd(ct, L, cfg->K, n_gauss, proj, ws, rgb_out, depth_out, topk_idx, topk_w, dL_dC, dL_dD, s))
+        return GS_ERR_UNSUPPORTED;
+    launch_project_backward(ct, n_gauss, mean3d, cov3d, proj, ws_ptr<uint32_t>(ws, L.elem_off),
+                            ws_ptr<uint32_t>(ws, L.elem_cnt), ws_ptr<float>(ws, L.inst_grad),
+                            ws_ptr<int>(ws, L.header), grads, s);
+    return launch_status();
+}
+
+size_t gs_loss_scratch_size(int64_t n_pix)
+{
+    if (n_pix < 0) return 0;
+    return sizeof(float) * (size_t)(n_pix + kSortBlocks + 64);
+}
+
+int gs_loss_cos_l1(const gs_config *cfg, int64_t n_pix, const void *F, const void *F_gt,
+                   const float *rgb, const float *rgb_gt, const float *depth, const float *depth_gt,
+                   float w_feat, float w_rgb, float w_depth,
+                   void *dL_dF, float *dL_dC, float *dL_dD, float *loss,
+                   void *scratch, size_t scratch_bytes, void *stream)
+{
+    if (!cfg_ok(cfg) || n_pix < 1) return GS_ERR_ARG;
+    if (!F || !F_gt || !rgb || !rgb_gt || !depth || !depth_gt || !dL_dF || !dL_dC || !dL_dD || !loss)
+        return GS_ERR_ARG;
+    if (((uintptr_t)F & 15) || ((uintptr_t)F_gt & 15) || ((uintptr_t)dL_dF & 15)) return GS_ERR_ARG;
+    if (!scratch || ((uintptr_t)scratch & 15) || scratch_bytes < gs_loss_scratch_size(n_pix)) return GS_ERR_WORKSPACE;
+    launch_loss(cfg->feat_dtype, cfg->D, n_pix, F, F_gt, rgb, rgb_gt, depth, depth_gt, w_feat, w_rgb, w_depth, dL_dF,
+                dL_dC, dL_dD, loss, (float *)scratch, (cudaStream_t)stream);
+    return launch_status();
+}
+
+int gs_sync_status(const void *ws, size_t ws_bytes, void *stream, int64_t *n_instances)
+{
+    if (!ws || ws_bytes < 256) return GS_ERR_WORKSPACE;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GS_ERR_CUDA;
+    uint32_t h[2];
+    if (cudaMemcpy(h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
+    if (n_instances) *n_instances = (int64_t)h[1];
+    if (h[0] & kErrOverflow) return GS_ERR_OVERFLOW;
+    if (h[0] & kErrTimeout) return GS_ERR_TIMEOUT;
+    return GS_OK;
+}
+
+}  // extern "C"

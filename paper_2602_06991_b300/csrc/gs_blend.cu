@@ -1,0 +1,244 @@
+// gs_blend.cu -- a4: the K-row gather-blend of Eqs. 3-4, and the training loss.
+//
+// Gather-blend: F[p] = sum_k (w_k / S_p) f_{idx_k}.  This is a weighted gather with
+// 2 K D flops per pixel against at least 4 D bytes written, far below the tensor-core
+// ridge, so it runs on the CUDA cores and is shaped for HBM: a group of lanes owns one
+// pixel (a full warp when the row has >= 32 16-byte chunks), every lane moves whole
+// 16-byte chunks (float4, or 8 bf16), all K row loads of a chunk are issued before the
+// FMAs, and the output row is written with 16-byte coalesced stores.  Rows reused by
+// neighbouring pixels are served by L2.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+template <bool BF16>
+struct Chunk;
+
+template <>
+struct Chunk<false> {                 // 4 floats
+    static constexpr int VEC = 4;
+    __device__ __forceinline__ static void load(const void *base, size_t chunk, float (&x)[4])
+    {
+        float4 v = __ldg((const float4 *)base + chunk);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    }
+    __device__ __forceinline__ static void store(void *base, size_t chunk, const float (&x)[4])
+    {
+        ((float4 *)base)[chunk] = make_float4(x[0], x[1], x[2], x[3]);
+    }
+};
+
+template <>
+struct Chunk<true> {                  // 8 bf16
+    static constexpr int VEC = 8;
+    __device__ __forceinline__ static void load(const void *base, size_t chunk, float (&x)[8])
+    {
+        uint4 v = __ldg((const uint4 *)base + chunk);
+        const __nv_bfloat162 *h = (const __nv_bfloat162 *)&v;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float2 f = __bfloat1622float2(h[i]);
+            x[2 * i] = f.x;
+            x[2 * i + 1] = f.y;
+        }
+    }
+    __device__ __forceinline__ static void store(void *base, size_t chunk, const float (&x)[8])
+    {
+        uint4 v;
+        __nv_bfloat162 *h = (__nv_bfloat162 *)&v;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+        ((uint4 *)base)[chunk] = v;
+    }
+};
+
+template <int KM, bool BF16>
+__global__ void __launch_bounds__(256) k_blend(long long n_pix, int K, int nch, int lpp_log2,
+                                               const int *__restrict__ idx, const float *__restrict__ wts,
+                                               const void *__restrict__ feats, void *__restrict__ F,
+                                               const int *__restrict__ err)
+{
+    using Ch = Chunk<BF16>;
+    constexpr int VEC = Ch::VEC;
+    const int lane = threadIdx.x & 31;
+    const int lpp = 1 << lpp_log2;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long p = warp * (32 >> lpp_log2) + (lane >> lpp_log2);
+    const int sub = lane & (lpp - 1);
+    if (p >= n_pix) return;
+    const bool bad = err && *err;
+    int ids[KM];
+    float ws[KM];
+    float S = 0.f;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        ids[k] = -1;
+        ws[k] = 0.f;
+        if (k < K && !bad) {
+            ids[k] = __ldg(idx + p * K + k);
+            ws[k] = __ldg(wts + p * K + k);
+            S += ws[k];
+        }
+    }
+    const float inv = S > 0.f ? 1.f / S : 0.f;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) ws[k] = ids[k] >= 0 ? ws[k] * inv : 0.f;
+    for (int ch = sub; ch < nch; ch += lpp) {
+        float x[KM][VEC];
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            if (ids[k] >= 0) {
+                Ch::load(feats, (size_t)ids[k] * nch + ch, x[k]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < VEC; ++i) x[k][i] = 0.f;
+            }
+        }
+        float acc[VEC];
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc[i] = 0.f;
+#pragma unroll
+        for (int k = 0; k < KM; ++k)
+#pragma unroll
+            for (int i = 0; i < VEC; ++i) acc[i] = fmaf(ws[k], x[k][i], acc[i]);
+        Ch::store(F, (size_t)p * nch + ch, acc);
+    }
+}
+
+static int lpp_log2_for(int nch)
+{
+    int l = 0;
+    while (l < 5 && (2 << l) <= nch) ++l;
+    return l;
+}
+
+template <bool BF16>
+static bool blend_k(int KM, int K, int nch, long long n_pix, const int *idx, const float *w, const void *feats,
+                    void *F, const int *err, cudaStream_t s)
+{
+    int l = lpp_log2_for(nch);
+    long long warps = (n_pix + (32 >> l) - 1) / (32 >> l);
+    unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+    switch (KM) {
+    case 4: k_blend<4, BF16><<<blocks, 256, 0, s>>>(n_pix, K, nch, l, idx, w, feats, F, err); return true;
+    case 8: k_blend<8, BF16><<<blocks, 256, 0, s>>>(n_pix, K, nch, l, idx, w, feats, F, err); return true;
+    case 16: k_blend<16, BF16><<<blocks, 256, 0, s>>>(n_pix, K, nch, l, idx, w, feats, F, err); return true;
+    case 32: k_blend<32, BF16><<<blocks, 256, 0, s>>>(n_pix, K, nch, l, idx, w, feats, F, err); return true;
+    }
+    return false;
+}
+
+bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, const float *w, const void *feats,
+                  void *F, const int *err, cudaStream_t s)
+{
+    if (n_pix <= 0) return true;
+    int KM = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
+    if (dtype == GS_BF16) return blend_k<true>(KM, K, D / 8, n_pix, idx, w, feats, F, err, s);
+    return blend_k<false>(KM, K, D / 4, n_pix, idx, w, feats, F, err, s);
+}
+
+// ------------------------------------------------------------------------------------
+// Loss: w_feat (1 - cos(F, Fgt)) + w_rgb |C - Cgt|_1 / 3 + w_depth |D - Dgt|, averaged
+// over pixels.  Per-pixel values go to `part`, then a fixed-order two-level sum.
+// ------------------------------------------------------------------------------------
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_loss(long long n_pix, int nch, int lpp_log2, const void *__restrict__ F,
+                                              const void *__restrict__ Fgt, const float *__restrict__ C,
+                                              const float *__restrict__ Cgt, const float *__restrict__ Dp,
+                                              const float *__restrict__ Dgt, float wf, float wc, float wd,
+                                              void *__restrict__ dLdF, float *__restrict__ dLdC,
+                                              float *__restrict__ dLdD, float *__restrict__ part)
+{
+    using Ch = Chunk<BF16>;
+    constexpr int VEC = Ch::VEC;
+    const int lane = threadIdx.x & 31;
+    const int lpp = 1 << lpp_log2;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long p = warp * (32 >> lpp_log2) + (lane >> lpp_log2);
+    const int sub = lane & (lpp - 1);
+    const bool live = p < n_pix;
+    if (!live) p = n_pix - 1;                    // keep every lane in the shuffles
+    float ff = 0.f, fg = 0.f, gg = 0.f;
+    for (int ch = sub; ch < nch; ch += lpp) {
+        float a[VEC], b[VEC];
+        Ch::load(F, (size_t)p * nch + ch, a);
+        Ch::load(Fgt, (size_t)p * nch + ch, b);
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+            ff = fmaf(a[i], a[i], ff);
+            fg = fmaf(a[i], b[i], fg);
+            gg = fmaf(b[i], b[i], gg);
+        }
+    }
+    for (int o = 1; o < lpp; o <<= 1) {
+        ff += __shfl_xor_sync(0xffffffffu, ff, o);
+        fg += __shfl_xor_sync(0xffffffffu, fg, o);
+        gg += __shfl_xor_sync(0xffffffffu, gg, o);
+    }
+    if (!live) return;
+    const float invP = 1.f / (float)n_pix;
+    float nf = sqrtf(ff), ng = sqrtf(gg);
+    bool ok = nf > 0.f && ng > 0.f;
+    float cosv = ok ? fg / (nf * ng) : 0.f;
+    float ca = ok ? -wf * invP / (nf * ng) : 0.f;          // coefficient of Fgt
+    float cb = ok ? wf * invP * cosv / ff : 0.f;           // coefficient of F
+    for (int ch = sub; ch < nch; ch += lpp) {
+        float a[VEC], b[VEC], gdx[VEC];
+        Ch::load(F, (size_t)p * nch + ch, a);
+        Ch::load(Fgt, (size_t)p * nch + ch, b);
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) gdx[i] = fmaf(ca, b[i], cb * a[i]);
+        Ch::store(dLdF, (size_t)p * nch + ch, gdx);
+    }
+    if (sub == 0) {
+        float l = wf * (1.f - cosv);
+        float lc = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float d = C[3 * p + i] - Cgt[3 * p + i];
+            lc += fabsf(d);
+            dLdC[3 * p + i] = wc * invP / 3.f * (float)((d > 0.f) - (d < 0.f));
+        }
+        float dd = Dp[p] - Dgt[p];
+        dLdD[p] = wd * invP * (float)((dd > 0.f) - (dd < 0.f));
+        part[p] = (l + wc * lc / 3.f + wd * fabsf(dd)) * invP;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_sum_fixed(const float *__restrict__ in, long long n, float *out)
+{
+    // fixed-order: each thread a contiguous slice, then a tree over threads
+    __shared__ float sm[1024];
+    long long per = (n + gridDim.x * 1024ll - 1) / (gridDim.x * 1024ll);
+    long long b = ((long long)blockIdx.x * 1024 + threadIdx.x) * per, e = min(b + per, n);
+    float s = 0.f;
+    for (long long i = b; i < e; ++i) s += in[i];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
+}
+
+bool launch_loss(int dtype, int D, long long n_pix, const void *F, const void *Fgt, const float *C, const float *Cgt,
+                 const float *Dp, const float *Dgt, float wf, float wc, float wd, void *dLdF, float *dLdC,
+                 float *dLdD, float *loss, float *part, cudaStream_t s)
+{
+    if (n_pix <= 0) return true;
+    int nch = dtype == GS_BF16 ? D / 8 : D / 4;
+    int l = lpp_log2_for(nch);
+    long long warps = (n_pix + (32 >> l) - 1) / (32 >> l);
+    unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+    if (dtype == GS_BF16)
+        k_loss<true><<<blocks, 256, 0, s>>>(n_pix, nch, l, F, Fgt, C, Cgt, Dp, Dgt, wf, wc, wd, dLdF, dLdC, dLdD, part);
+    else
+        k_loss<false><<<blocks, 256, 0, s>>>(n_pix, nch, l, F, Fgt, C, Cgt, Dp, Dgt, wf, wc, wd, dLdF, dLdC, dLdD, part);
+    float *part2 = part + n_pix;
+    k_sum_fixed<<<kSortBlocks, 1024, 0, s>>>(part, n_pix, part2);
+    k_sum_fixed<<<1, 1024, 0, s>>>(part2, kSortBlocks, loss);
+    return true;
+}
+
+}  // namespace gs

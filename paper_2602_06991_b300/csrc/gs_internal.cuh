@@ -1,0 +1,254 @@
+// gs_internal.cuh -- shared device/host internals of the Top-K feature renderer.
+// Not part of the public ABI (include/gs_topk.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/gs_topk.h"
+
+namespace gs {
+
+// ------------------------------------------------------------------------------------
+// Constants of the per-pixel test (3D Gaussian Splatting conventions that Sec. 3.1 of
+// the paper defers to).
+// ------------------------------------------------------------------------------------
+constexpr float kQMax = 9.0f;            // 3-sigma ellipse: q = d^T Sigma^-1 d <= 9
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaClamp = 0.99f;
+constexpr float kTStop = 1e-4f;
+constexpr float kDilation = 0.3f;        // low-pass dilation of Sigma2D (px^2)
+constexpr float kFrustumClamp = 1.3f;
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 elements per tile
+constexpr int kSortBlocks = 296;                       // 2 per SM on a 148-SM B300
+constexpr int kPieceLen = 128;                         // pairs per feature-gradient work piece
+constexpr int kGradVals = 10;                          // per-instance partial 2D gradient
+
+// Error word bits (in the workspace header).
+constexpr int kErrOverflow = 1;
+constexpr int kErrTimeout = 2;
+
+// ------------------------------------------------------------------------------------
+// Camera table passed by value to kernels.
+// ------------------------------------------------------------------------------------
+struct CamDev {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    float near_z;
+    float limx, limy;          // 1.3 tan(fov/2) clamp of x/z, y/z in the Jacobian
+    int W, H;
+    int tiles_x, tiles_y;
+    int tile_off;              // first global tile id of this camera
+    long long pix_off;         // first flat pixel index of this camera
+};
+
+struct CamTable {
+    int n;
+    int tile_w, tile_h;
+    int n_tiles;               // total over cameras
+    CamDev c[GS_MAX_CAMERAS];
+};
+
+__device__ __forceinline__ int cam_of_tile(const CamTable &ct, int tile)
+{
+    int c = 0;
+#pragma unroll 1
+    for (int i = 1; i < ct.n; ++i)
+        if (tile >= ct.c[i].tile_off) c = i;
+    return c;
+}
+
+// ------------------------------------------------------------------------------------
+// Error-free transformations (Knuth TwoSum, FMA-based TwoProduct) used to carry the
+// camera transform and the pixel coordinate of each Gaussian in double-float
+// precision, so that d = pixel - mean2d is accurate to the float32 rounding of d.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// ------------------------------------------------------------------------------------
+// Projected record layout (GS_PROJ_FLOATS = 16 floats = 4 x float4 per (camera, Gaussian))
+//   r0 = (u_hi, v_hi, u_lo, v_lo)          double-float pixel position of the mean
+//   r1 = (s1, m, s2, opacity)              Cholesky form of the conic:
+//                                          q = (dx s1)^2 + ((dy - m dx) s2)^2
+//   r2 = (r, g, b, z)                      colour and camera depth (float32, sort key)
+//   r3 = (a, b, c, extent)                 conic Sigma2D^-1 = [[a, b], [b, c]]; extent is
+//                                          two fp16 half-widths (x | y << 16) of the pixel
+//                                          box that can reach alpha >= 1/255; 0 = culled
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ void unpack_extent(float packed, float &ex, float &ey)
+{
+    unsigned int bits = __float_as_uint(packed);
+    ex = __half2float(__ushort_as_half((unsigned short)(bits & 0xffffu)));
+    ey = __half2float(__ushort_as_half((unsigned short)(bits >> 16)));
+}
+
+// Inclusive tile rectangle [tx0, tx1] x [ty0, ty1] of the pixels whose centres lie in
+// the box |x + 0.5 - u| <= ex, |y + 0.5 - v| <= ey.  Returns false if empty.
+__device__ __forceinline__ bool tile_rect(const CamDev &c, int tw, int th, float u, float v,
+                                          float ex, float ey, int &tx0, int &tx1, int &ty0, int &ty1)
+{
+    float x0 = ceilf(u - ex - 0.5f), x1 = floorf(u + ex - 0.5f);
+    float y0 = ceilf(v - ey - 0.5f), y1 = floorf(v + ey - 0.5f);
+    x0 = fmaxf(x0, 0.0f);
+    y0 = fmaxf(y0, 0.0f);
+    x1 = fminf(x1, (float)(c.W - 1));
+    y1 = fminf(y1, (float)(c.H - 1));
+    if (!(x0 <= x1) || !(y0 <= y1)) return false;
+    tx0 = (int)x0 / tw; tx1 = (int)x1 / tw;
+    ty0 = (int)y0 / th; ty1 = (int)y1 / th;
+    return true;
+}
+
+// Per-pixel evaluation shared by the forward walk and the backward re-walk: both must
+// take identical decisions, so both use these inlined sequences (explicit _rn
+// intrinsics keep the compiler from contracting them differently in the two kernels).
+__device__ __forceinline__ float eval_q(float pxf, float pyf, const float4 r0, const float4 r1, float &dx, float &dy)
+{
+    dx = __fsub_rn(__fsub_rn(pxf, r0.x), r0.z);
+    dy = __fsub_rn(__fsub_rn(pyf, r0.y), r0.w);
+    float y1 = __fmul_rn(dx, r1.x);
+    float y2 = __fmul_rn(__fmaf_rn(-r1.y, dx, dy), r1.z);
+    return __fmaf_rn(y1, y1, __fmul_rn(y2, y2));
+}
+
+// alpha = min(0.99, o exp(-q/2)); ao is the unclamped product.
+__device__ __forceinline__ float eval_alpha(float q, float o, float &G, float &ao)
+{
+    G = __expf(__fmul_rn(-0.5f, q));
+    ao = __fmul_rn(o, G);
+    return fminf(kAlphaClamp, ao);
+}
+
+// Top-K kept in registers, KM slots in descending weight.  Slots [0, KM - K) hold
+// +inf sentinels so that a runtime K <= KM keeps exactly its K largest in slots
+// [KM - K, KM); comparisons are strict, so among equal weights the earlier
+// contributor (depth order) stays ahead.
+template <int KM>
+struct TopK {
+    float w[KM];
+    int id[KM];
+    __device__ __forceinline__ void init(int K)
+    {
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            w[k] = (k < KM - K) ? __int_as_float(0x7f800000) : -1.0f;
+            id[k] = -1;
+        }
+    }
+    __device__ __forceinline__ void insert(float nw, int nid)
+    {
+        if (!(nw > w[KM - 1])) return;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            bool sw = nw > w[k];
+            float tw = sw ? nw : w[k];
+            int ti = sw ? nid : id[k];
+            nw = sw ? w[k] : nw;
+            nid = sw ? id[k] : nid;
+            w[k] = tw;
+            id[k] = ti;
+        }
+    }
+};
+
+// ------------------------------------------------------------------------------------
+// Workspace layout (host-computed; all offsets 256-byte aligned)
+// ------------------------------------------------------------------------------------
+struct WsLayout {
+    size_t header;             // 256 B: [0] error word, [1] instance count, [2] pieces, [3..] bbox
+    size_t depth_keys[2], depth_vals[2];   // NE
+    size_t elem_cnt;           // NE (tiles touched, per element)
+    size_t elem_off;           // NE (first pre-sort instance of each element)
+    size_t counts;             // NE (counts in depth order, scanned in place)
+    size_t inst_keys[2], inst_vals[2];     // Mcap
+    size_t inst_elem;          // Mcap
+    size_t tile_range;         // n_tiles x int2
+    size_t sort_hist;          // kSortBlocks x 256
+    size_t scan_aux;           // scan block sums
+    size_t inst_grad;          // Mcap x kGradVals floats (per-instance partial 2D gradients)
+    size_t rank_keys[2], rank_vals[2];     // N (Gaussians in 3D Morton order)
+    size_t grank;              // N: Morton rank of each Gaussian
+    size_t pair_keys[2], pair_vals[2];     // N + P K
+    size_t hbuf;               // P K floats: dL/dF_p . f_{idx_k}
+    size_t seg_start, seg_end; // N each
+    size_t pieces, piece_off;  // N each
+    size_t multi, multi_off;   // N each
+    size_t piece_rank;         // max_pieces
+    size_t piece_rows;         // max_multi_rows x D floats
+    size_t loss_part;          // P + kSortBlocks floats
+    size_t total;
+    int inst_sorted;           // buffer (0/1) holding the tile-sorted instances
+    int pair_sorted;           // buffer (0/1) holding the sorted feature-gradient pairs
+    int rank_sorted;           // buffer (0/1) holding the Morton-ordered Gaussians
+    int pair_bits;
+
+    long long NE, P, PK, Mcap, n_pairs, max_pieces, max_multi_rows;
+    int N, K, D, n_tiles, n_cams;
+};
+
+bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N, WsLayout &L);
+bool make_camtable(const gs_config *cfg, const gs_camera *cams, int n_cams, CamTable &ct);
+int bits_for(long long v);
+inline int sorted_buffer(int n_bits) { return ((n_bits + 7) / 8) & 1; }
+
+template <typename T>
+__host__ __device__ __forceinline__ T *ws_ptr(void *ws, size_t off) { return (T *)((char *)ws + off); }
+
+// ------------------------------------------------------------------------------------
+// Host-side launchers implemented in the .cu files
+// ------------------------------------------------------------------------------------
+// LSD radix sort of (key, value) uint32 pairs on key bits [0, n_bits); stable.  The
+// element count is n_host, or *n_dev clamped to n_host if n_dev is non-null.
+// Returns the index (0/1) of the buffer pair holding the sorted result.
+int radix_sort_pairs(uint32_t *keys0, uint32_t *keys1, uint32_t *vals0, uint32_t *vals1,
+                     long long n_host, const uint32_t *n_dev, int n_bits, uint32_t *hist,
+                     cudaStream_t s);
+// Exclusive scan of n uint32 in -> out (may alias); *total (device) = sum if non-null.
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t *total,
+                        uint32_t *aux, cudaStream_t s);
+
+void launch_preprocess(const CamTable &ct, int N, const float *mean3d, const float *cov3d, const float *opac,
+                       const float *rgb, float *proj, cudaStream_t s);
+void launch_project_backward(const CamTable &ct, int N, const float *mean3d, const float *cov3d, const float *proj,
+                             const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad, const int *err,
+                             const gs_grads *gr, cudaStream_t s);
+void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *proj, void *ws, cudaStream_t s);
+bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj, void *ws,
+                     float *rgb_out, float *depth_out, float *T_out, int *n_out, int *idx_out, float *w_out,
+                     cudaStream_t s);
+bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj, void *ws,
+                     const float *rgb_out, const float *depth_out, const int *topk_idx, const float *topk_w,
+                     const float *dLdC, const float *dLdD, cudaStream_t s);
+bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, const float *w, const void *feats,
+                  void *F, const int *err, cudaStream_t s);
+bool launch_feature_grad(const WsLayout &L, int dtype, int N, const float *mean3d, const int *topk_idx,
+                         const float *topk_w, const void *feats, const void *dLdF, float *grad_feat, void *ws,
+                         cudaStream_t s);
+bool launch_loss(int dtype, int D, long long n_pix, const void *F, const void *Fgt, const float *C, const float *Cgt,
+                 const float *Dp, const float *Dgt, float wf, float wc, float wd, void *dLdF, float *dLdC,
+                 float *dLdD, float *loss, float *part, cudaStream_t s);
+
+}  // namespace gs

@@ -1,0 +1,270 @@
+// gs_sort.cu -- the library's own device radix sort and exclusive scan.
+//
+// Radix sort: least-significant-digit, 8-bit digits, reduce-then-scan per pass:
+//   upsweep   : each block counts the digits of its contiguous range of tiles;
+//   scan      : one block turns the (digit-major, block-minor) counts into offsets;
+//   downsweep : each block ranks its keys stably (warp match + per-warp counters) and
+//               scatters them to their final positions.
+// No block waits on another, so nothing can spin.  Stability makes the multi-pass
+// sort correct and keeps equal keys in input order (used to keep depth order within
+// a tile, and to put each Gaussian's marker entry first in its segment).
+#include "gs_internal.cuh"
+
+namespace gs {
+
+__device__ __forceinline__ long long sort_count(long long n_host, const uint32_t *n_dev)
+{
+    if (n_dev) {
+        long long m = (long long)(*n_dev);
+        return m < n_host ? m : n_host;
+    }
+    return n_host;
+}
+
+__device__ __forceinline__ void block_tiles(long long n, long long &t0, long long &t1)
+{
+    long long n_tiles = (n + kSortTile - 1) / kSortTile;
+    long long tpb = (n_tiles + gridDim.x - 1) / gridDim.x;
+    t0 = (long long)blockIdx.x * tpb;
+    t1 = t0 + tpb;
+    if (t1 > n_tiles) t1 = n_tiles;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_rs_upsweep(const uint32_t *__restrict__ keys, long long n_host,
+                                                             const uint32_t *n_dev, int shift,
+                                                             uint32_t *__restrict__ hist)
+{
+    constexpr int W = kSortThreads / 32;
+    __shared__ uint32_t cnt[W][256];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < W * 256; i += kSortThreads) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+    long long n = sort_count(n_host, n_dev), t0, t1;
+    block_tiles(n, t0, t1);
+    long long e0 = t0 * kSortTile, e1 = t1 * kSortTile;
+    if (e1 > n) e1 = n;
+    for (long long i = e0 + tid; i < e1; i += kSortThreads) {
+        uint32_t d = (__ldg(keys + i) >> shift) & 255u;
+        atomicAdd(&cnt[warp][d], 1u);
+    }
+    __syncthreads();
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) s += cnt[w][tid];
+    hist[(size_t)tid * gridDim.x + blockIdx.x] = s;
+}
+
+// Exclusive scan in place of len uint32 by one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_single(uint32_t *data, int len, uint32_t *total)
+{
+    __shared__ uint32_t warp_sums[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int per = (len + 1023) / 1024;
+    int b = tid * per, e = min(b + per, len);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += data[i];
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        warp_sums[lane] = v;          // inclusive
+    }
+    __syncthreads();
+    uint32_t run = x - s + (warp > 0 ? warp_sums[warp - 1] : 0u);
+    for (int i = b; i < e; ++i) {
+        uint32_t v = data[i];
+        data[i] = run;
+        run += v;
+    }
+    if (total && tid == 1023) *total = run;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_rs_downsweep(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                               uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                               long long n_host, const uint32_t *n_dev, int shift,
+                                                               const uint32_t *__restrict__ hist)
+{
+    constexpr int W = kSortThreads / 32;
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_wcnt[W][257];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    s_base[tid] = hist[(size_t)tid * gridDim.x + blockIdx.x];
+    long long n = sort_count(n_host, n_dev), t0, t1;
+    block_tiles(n, t0, t1);
+    for (long long t = t0; t < t1; ++t) {
+        for (int i = tid; i < W * 257; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
+        __syncthreads();
+        long long wbase = t * kSortTile + (long long)warp * 32 * kSortItems;
+        uint32_t k[kSortItems], v[kSortItems], lr[kSortItems];
+        int dg[kSortItems];
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            long long idx = wbase + i * 32 + lane;
+            bool valid = idx < n;
+            k[i] = valid ? __ldg(kin + idx) : 0u;
+            v[i] = valid ? __ldg(vin + idx) : 0u;
+            dg[i] = valid ? (int)((k[i] >> shift) & 255u) : 256;
+        }
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            uint32_t peers = __match_any_sync(0xffffffffu, dg[i]);
+            int leader = __ffs(peers) - 1;
+            uint32_t before = s_wcnt[warp][dg[i]];
+            __syncwarp();
+            if (lane == leader) s_wcnt[warp][dg[i]] = before + __popc(peers);
+            __syncwarp();
+            lr[i] = before + __popc(peers & lt_mask);
+        }
+        __syncthreads();
+        {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint32_t c = s_wcnt[w][tid];
+                s_wcnt[w][tid] = run;
+                run += c;
+            }
+            s_tot[tid] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kSortItems; ++i) {
+            if (dg[i] < 256) {
+                uint32_t pos = s_base[dg[i]] + s_wcnt[warp][dg[i]] + lr[i];
+                kout[pos] = k[i];
+                vout[pos] = v[i];
+            }
+        }
+        __syncthreads();
+        s_base[tid] += s_tot[tid];
+    }
+}
+
+int radix_sort_pairs(uint32_t *keys0, uint32_t *keys1, uint32_t *vals0, uint32_t *vals1,
+                     long long n_host, const uint32_t *n_dev, int n_bits, uint32_t *hist, cudaStream_t s)
+{
+    if (n_host <= 0 || n_bits <= 0) return 0;
+    int passes = (n_bits + 7) / 8;
+    long long n_tiles = (n_host + kSortTile - 1) / kSortTile;
+    int G = (int)(n_tiles < kSortBlocks ? n_tiles : kSortBlocks);
+    uint32_t *kb[2] = {keys0, keys1}, *vb[2] = {vals0, vals1};
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        k_rs_upsweep<<<G, kSortThreads, 0, s>>>(kb[cur], n_host, n_dev, shift, hist);
+        k_scan_single<<<1, 1024, 0, s>>>(hist, 256 * G, nullptr);
+        k_rs_downsweep<<<G, kSortThreads, 0, s>>>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n_host, n_dev, shift, hist);
+        cur ^= 1;
+    }
+    return cur;
+}
+
+// ------------------------------------------------------------------------------------
+// Exclusive scan of uint32 (reduce, scan block sums, downsweep), tiles of 4096.
+// ------------------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *warp_sums, uint32_t &block_total)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        warp_sums[lane] = v;
+    }
+    __syncthreads();
+    block_total = warp_sums[31];
+    uint32_t r = inc - x + (warp > 0 ? warp_sums[warp - 1] : 0u);
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ in, long long n,
+                                                              long long per_block, uint32_t *aux)
+{
+    __shared__ uint32_t warp_sums[32];
+    long long b0 = (long long)blockIdx.x * per_block, b1 = min(b0 + per_block, n);
+    uint32_t s = 0;
+    for (long long i = b0 + threadIdx.x; i < b1; i += kScanThreads) s += in[i];
+    uint32_t tot;
+    block_excl_scan(s, warp_sums, tot);
+    if (threadIdx.x == 0) aux[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *in, uint32_t *out, long long n,
+                                                            long long per_block, const uint32_t *aux)
+{
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t tile[kScanTile];
+    const int tid = threadIdx.x;
+    long long b0 = (long long)blockIdx.x * per_block, b1 = min(b0 + per_block, n);
+    uint32_t carry = aux[blockIdx.x];
+    for (long long t = b0; t < b1; t += kScanTile) {
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            long long idx = t + i * kScanThreads + tid;
+            tile[i * kScanThreads + tid] = idx < b1 ? in[idx] : 0u;
+        }
+        __syncthreads();
+        uint32_t v[kScanItems], s = 0;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) { v[i] = tile[tid * kScanItems + i]; s += v[i]; }
+        uint32_t tot;
+        uint32_t run = block_excl_scan(s, warp_sums, tot) + carry;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) { tile[tid * kScanItems + i] = run; run += v[i]; }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            long long idx = t + i * kScanThreads + tid;
+            if (idx < b1) out[idx] = tile[i * kScanThreads + tid];
+        }
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t *total, uint32_t *aux, cudaStream_t s)
+{
+    if (n <= 0) {
+        if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+        return;
+    }
+    long long n_tiles = (n + kScanTile - 1) / kScanTile;
+    int G = (int)(n_tiles < kSortBlocks ? n_tiles : kSortBlocks);
+    long long tiles_per_block = (n_tiles + G - 1) / G;
+    long long per_block = tiles_per_block * kScanTile;
+    G = (int)((n + per_block - 1) / per_block);
+    k_scan_reduce<<<G, kScanThreads, 0, s>>>(in, n, per_block, aux);
+    k_scan_single<<<1, 1024, 0, s>>>(aux, G, total);
+    k_scan_down<<<G, kScanThreads, 0, s>>>(in, out, n, per_block, aux);
+}
+
+}  // namespace gs

@@ -1,0 +1,354 @@
+// gs_walk.cu -- a3: front-to-back walk with per-pixel Top-K (forward) and the re-walk
+// of the adjoint (geometry part of a5).
+//
+// Forward (Eqs. 1-2): one CTA per screen tile, one thread per pixel.  The tile's
+// depth-ordered instance list is staged through shared memory in batches of one
+// record per thread; each pixel evaluates alpha with the double-float offset and the
+// Cholesky-form conic, accumulates colour and depth (Eq. 1) and keeps its Top-K
+// (Eq. 2) in registers by insertion.  A batch loop ends as soon as every pixel of the
+// tile has stopped.
+//
+// Backward: the same walk is recomputed (not stored) with the very same inlined
+// evaluation, so contributor sets and transmittances match the forward bit for bit.
+// For contributor i with upstream dL/dC, dL/dD and the feature term,
+//   dL/dw_i = dL/dC . c_i + dL/dD z_i + [i in K] (h_i - H) / S,
+//   dL/dalpha_i = dL/dw_i T_i - (sum_{m>i} dL/dw_m w_m) / (1 - alpha_i),
+// where h_i = dL/dF . f_i (computed by the feature-gradient pass), H = sum_k w'_k h_k,
+// and the suffix sum is total - prefix with total = dL/dC . C + dL/dD . D (the
+// feature terms sum to zero over the Top-K set).  Per-Gaussian partials are reduced
+// across the tile's pixels (warp reduce-scatter, then a fixed-order sum over warps)
+// and written once per (Gaussian, tile) instance: no atomics, deterministic.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+template <int TW, int TH, int KM>
+__global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, const float4 *__restrict__ proj,
+                                                     const uint32_t *__restrict__ inst_vals,
+                                                     const uint32_t *__restrict__ inst_elem,
+                                                     const int2 *__restrict__ ranges, const int *__restrict__ err,
+                                                     float *__restrict__ rgb_out, float *__restrict__ depth_out,
+                                                     float *__restrict__ T_out, int *__restrict__ n_out,
+                                                     int *__restrict__ idx_out, float *__restrict__ w_out)
+{
+    constexpr int B = TW * TH;
+    __shared__ float4 s_r0[B], s_r1[B], s_r2[B];
+    __shared__ int s_g[B];
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int c = cam_of_tile(ct, tile);
+    const CamDev &cam = ct.c[c];
+    const int lt = tile - cam.tile_off;
+    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+    const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
+    const bool inside = px < cam.W && py < cam.H;
+    int2 rg = ranges[tile];
+    if (*err) rg.y = rg.x;
+    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dd = 0.f;
+    int nc = 0;
+    TopK<KM> tk;
+    tk.init(K);
+    bool done = !inside;
+    const int cN = c * N;
+    for (int b0 = rg.x; b0 < rg.y; b0 += B) {
+        if (__syncthreads_count(done) == B) break;
+        int m = b0 + tid;
+        if (m < rg.y) {
+            uint32_t e = inst_elem[inst_vals[m]];
+            const float4 *r = proj + 4 * (size_t)e;
+            s_r0[tid] = r[0];
+            s_r1[tid] = r[1];
+            s_r2[tid] = r[2];
+            s_g[tid] = (int)e - cN;
+        }
+        __syncthreads();
+        const int cnt = min(B, rg.y - b0);
+        for (int j = 0; j < cnt && !done; ++j) {
+            float dx, dy;
+            const float4 r1 = s_r1[j];
+            float q = eval_q(pxf, pyf, s_r0[j], r1, dx, dy);
+            if (q > kQMax) continue;
+            float G, ao;
+            float alpha = eval_alpha(q, r1.w, G, ao);
+            if (alpha < kAlphaMin) continue;
+            float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+            if (test_T < kTStop) {
+                done = true;
+                break;
+            }
+            float w = __fmul_rn(alpha, T);
+            const float4 r2 = s_r2[j];
+            C0 = fmaf(w, r2.x, C0);
+            C1 = fmaf(w, r2.y, C1);
+            C2 = fmaf(w, r2.z, C2);
+            Dd = fmaf(w, r2.w, Dd);
+            T = test_T;
+            ++nc;
+            tk.insert(w, s_g[j]);
+        }
+    }
+    if (!inside) return;
+    const long long p = cam.pix_off + (long long)py * cam.W + px;
+    rgb_out[3 * p] = C0;
+    rgb_out[3 * p + 1] = C1;
+    rgb_out[3 * p + 2] = C2;
+    depth_out[p] = Dd;
+    T_out[p] = T;
+    n_out[p] = nc;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        if (k >= KM - K) {
+            int slot = k - (KM - K);
+            idx_out[p * K + slot] = tk.id[k];
+            w_out[p * K + slot] = tk.w[k] > 0.f ? tk.w[k] : 0.f;
+        }
+    }
+}
+
+// Sum 16 per-lane values over the warp with 16 shuffles (reduce-scatter): on return
+// lane l holds the total of value index (l >> 1) & 15; lanes l and l ^ 1 agree.
+__device__ __forceinline__ float warp_reduce16(const float (&v)[16], int lane)
+{
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float a[8], b[4], c2[2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float send = b4 ? v[i] : v[i + 8], keep = b4 ? v[i + 8] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float send = b3 ? a[i] : a[i + 4], keep = b3 ? a[i + 4] : a[i];
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        float send = b2 ? b[i] : b[i + 2], keep = b2 ? b[i + 2] : b[i];
+        c2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    float d = (b1 ? c2[1] : c2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? c2[0] : c2[1], 2);
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    return d;
+}
+
+template <int TW, int TH, int KM>
+__global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, const float4 *__restrict__ proj,
+                                                     const uint32_t *__restrict__ inst_vals,
+                                                     const uint32_t *__restrict__ inst_elem,
+                                                     const int2 *__restrict__ ranges, const int *__restrict__ err,
+                                                     const float *__restrict__ rgb_out, const float *__restrict__ depth_out,
+                                                     const int *__restrict__ topk_idx, const float *__restrict__ topk_w,
+                                                     const float *__restrict__ hbuf, const float *__restrict__ dLdC,
+                                                     const float *__restrict__ dLdD, float *__restrict__ inst_grad)
+{
+    constexpr int B = TW * TH;
+    constexpr int NW = B / 32;
+    constexpr int BB = 64;                       // Gaussians per staged batch
+    __shared__ float4 s_r0[BB], s_r1[BB], s_r2[BB], s_r3[BB];
+    __shared__ int s_g[BB];
+    __shared__ uint32_t s_o[BB];
+    __shared__ float s_red[NW][BB][kGradVals];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x;
+    const int c = cam_of_tile(ct, tile);
+    const CamDev &cam = ct.c[c];
+    const int lt = tile - cam.tile_off;
+    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+    const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
+    const bool inside = px < cam.W && py < cam.H;
+    int2 rg = ranges[tile];
+    if (*err) rg.y = rg.x;
+    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
+    const long long p = cam.pix_off + (long long)py * cam.W + px;
+
+    float dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dD = 0.f, total = 0.f;
+    int kid[KM];
+    float kfp[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) { kid[k] = -2; kfp[k] = 0.f; }
+    if (inside) {
+        dC0 = dLdC[3 * p]; dC1 = dLdC[3 * p + 1]; dC2 = dLdC[3 * p + 2];
+        dD = dLdD[p];
+        total = dC0 * rgb_out[3 * p] + dC1 * rgb_out[3 * p + 1] + dC2 * rgb_out[3 * p + 2] + dD * depth_out[p];
+        float S = 0.f;
+#pragma unroll
+        for (int k = 0; k < KM; ++k)
+            if (k < K) S += topk_w[p * K + k];
+        float inv = S > 0.f ? 1.f / S : 0.f;
+        float H = 0.f;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            if (k < K) {
+                int id = topk_idx[p * K + k];
+                if (id >= 0) {
+                    kid[k] = id;
+                    kfp[k] = hbuf[p * K + k];
+                    H += topk_w[p * K + k] * inv * kfp[k];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KM; ++k) kfp[k] = (kfp[k] - H) * inv;
+    }
+    float T = 1.f, prefix = 0.f;
+    bool done = !inside;
+    const int cN = c * N;
+    for (int b0 = rg.x; b0 < rg.y; b0 += BB) {
+        if (__syncthreads_count(!done) == 0) {
+            // every pixel stopped: the remaining instances of this tile contribute nothing
+            for (int m = b0 + tid; m < rg.y; m += B) {
+                float *dst = inst_grad + (size_t)kGradVals * inst_vals[m];
+#pragma unroll
+                for (int v = 0; v < kGradVals; ++v) dst[v] = 0.f;
+            }
+            break;
+        }
+        if (tid < BB && b0 + tid < rg.y) {
+            uint32_t o = inst_vals[b0 + tid];
+            uint32_t e = inst_elem[o];
+            const float4 *r = proj + 4 * (size_t)e;
+            s_r0[tid] = r[0];
+            s_r1[tid] = r[1];
+            s_r2[tid] = r[2];
+            s_r3[tid] = r[3];
+            s_g[tid] = (int)e - cN;
+            s_o[tid] = o;
+        }
+        __syncthreads();
+        const int cnt = min(BB, rg.y - b0);
+        for (int j = 0; j < cnt; ++j) {
+            float v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+            bool contrib = false;
+            if (!done) {
+                float dx, dy;
+                const float4 r1 = s_r1[j];
+                float q = eval_q(pxf, pyf, s_r0[j], r1, dx, dy);
+                if (q <= kQMax) {
+                    float G, ao;
+                    float alpha = eval_alpha(q, r1.w, G, ao);
+                    if (alpha >= kAlphaMin) {
+                        float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                        if (test_T < kTStop) {
+                            done = true;
+                        } else {
+                            contrib = true;
+                            float w = __fmul_rn(alpha, T);
+                            const float4 r2 = s_r2[j];
+                            const int gid = s_g[j];
+                            float fp = 0.f;
+#pragma unroll
+                            for (int k = 0; k < KM; ++k) fp = (kid[k] == gid) ? kfp[k] : fp;
+                            float gi = dC0 * r2.x + dC1 * r2.y + dC2 * r2.z + dD * r2.w + fp;
+                            prefix = fmaf(gi, w, prefix);
+                            float suffix = total - prefix;
+                            float dalpha = gi * T - suffix / (1.f - alpha);
+                            v[6] = w * dC0; v[7] = w * dC1; v[8] = w * dC2; v[9] = w * dD;
+                            if (ao < kAlphaClamp) {
+                                const float4 r3 = s_r3[j];
+                                v[5] = dalpha * G;
+                                float dq = -0.5f * alpha * dalpha;
+                                v[2] = dq * dx * dx;
+                                v[3] = dq * 2.f * dx * dy;
+                                v[4] = dq * dy * dy;
+                                v[0] = -2.f * dq * (r3.x * dx + r3.y * dy);
+                                v[1] = -2.f * dq * (r3.y * dx + r3.z * dy);
+                            }
+                            T = test_T;
+                        }
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                float d = warp_reduce16(v, lane);
+                int vi = (lane >> 1) & 15;
+                if (!(lane & 1) && vi < kGradVals) s_red[warp][j][vi] = d;
+            } else if (lane < kGradVals) {
+                s_red[warp][j][lane] = 0.f;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < cnt * kGradVals; i += B) {
+            int j = i / kGradVals, vi = i - j * kGradVals;
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) s += s_red[w][j][vi];
+            inst_grad[(size_t)kGradVals * s_o[j] + vi] = s;
+        }
+    }
+}
+
+template <int TW, int TH>
+static bool walk_fwd_k(int KM, dim3 grid, cudaStream_t s, const CamTable &ct, int K, int N, const float4 *proj,
+                       const uint32_t *iv, const uint32_t *ie, const int2 *rg, const int *err, float *a, float *b,
+                       float *cc, int *d, int *e, float *f)
+{
+    constexpr int B = TW * TH;
+    switch (KM) {
+    case 4: k_walk_fwd<TW, TH, 4><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, a, b, cc, d, e, f); return true;
+    case 8: k_walk_fwd<TW, TH, 8><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, a, b, cc, d, e, f); return true;
+    case 16: k_walk_fwd<TW, TH, 16><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, a, b, cc, d, e, f); return true;
+    case 32: k_walk_fwd<TW, TH, 32><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, a, b, cc, d, e, f); return true;
+    }
+    return false;
+}
+
+template <int TW, int TH>
+static bool walk_bwd_k(int KM, dim3 grid, cudaStream_t s, const CamTable &ct, int K, int N, const float4 *proj,
+                       const uint32_t *iv, const uint32_t *ie, const int2 *rg, const int *err, const float *C,
+                       const float *Dp, const int *ti, const float *tw, const float *h, const float *dC,
+                       const float *dD, float *ig)
+{
+    constexpr int B = TW * TH;
+    switch (KM) {
+    case 4: k_walk_bwd<TW, TH, 4><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig); return true;
+    case 8: k_walk_bwd<TW, TH, 8><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig); return true;
+    case 16: k_walk_bwd<TW, TH, 16><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig); return true;
+    case 32: k_walk_bwd<TW, TH, 32><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig); return true;
+    }
+    return false;
+}
+
+static int k_bucket(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32; }
+
+bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj_f, void *ws,
+                     float *rgb_out, float *depth_out, float *T_out, int *n_out, int *idx_out, float *w_out,
+                     cudaStream_t s)
+{
+    const float4 *proj = (const float4 *)proj_f;
+    const int *err = ws_ptr<int>(ws, L.header);
+    const uint32_t *iv = ws_ptr<uint32_t>(ws, L.inst_vals[L.inst_sorted]);
+    const uint32_t *ie = ws_ptr<uint32_t>(ws, L.inst_elem);
+    const int2 *rg = ws_ptr<int2>(ws, L.tile_range);
+    dim3 grid(ct.n_tiles);
+    int KM = k_bucket(K);
+    if (ct.tile_w == 16 && ct.tile_h == 16) return walk_fwd_k<16, 16>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
+    if (ct.tile_w == 32 && ct.tile_h == 8) return walk_fwd_k<32, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
+    if (ct.tile_w == 16 && ct.tile_h == 8) return walk_fwd_k<16, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
+    if (ct.tile_w == 8 && ct.tile_h == 8) return walk_fwd_k<8, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
+    return false;
+}
+
+bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj_f, void *ws,
+                     const float *rgb_out, const float *depth_out, const int *topk_idx, const float *topk_w,
+                     const float *dLdC, const float *dLdD, cudaStream_t s)
+{
+    const float4 *proj = (const float4 *)proj_f;
+    const int *err = ws_ptr<int>(ws, L.header);
+    const uint32_t *iv = ws_ptr<uint32_t>(ws, L.inst_vals[L.inst_sorted]);
+    const uint32_t *ie = ws_ptr<uint32_t>(ws, L.inst_elem);
+    const int2 *rg = ws_ptr<int2>(ws, L.tile_range);
+    const float *h = ws_ptr<float>(ws, L.hbuf);
+    float *ig = ws_ptr<float>(ws, L.inst_grad);
+    dim3 grid(ct.n_tiles);
+    int KM = k_bucket(K);
+    if (ct.tile_w == 16 && ct.tile_h == 16) return walk_bwd_k<16, 16>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig);
+    if (ct.tile_w == 32 && ct.tile_h == 8) return walk_bwd_k<32, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig);
+    if (ct.tile_w == 16 && ct.tile_h == 8) return walk_bwd_k<16, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig);
+    if (ct.tile_w == 8 && ct.tile_h == 8) return walk_bwd_k<8, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig);
+    return false;
+}
+
+}  // namespace gs
