@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark of the Top-K feature render training step on B300.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl ours|reference]
+                    [--workload frame] [--no-graph] [--no-cpu-baseline] [--no-e2e]
+
+A step is one pass of the whole hot path over one synthetic batch: EWA projection,
+tile binning + radix sort, the Top-K walk, the gather-blend (forward), the training loss
+(1 - cosine on features, L1 on colour and depth) and the full adjoint down to every
+per-Gaussian gradient.  The default workload is 200k Gaussians (80% on 5 planes, 20%
+clutter), 640x480, D=512, K=8, float32 ('frame').  Inputs are resident in HBM; the
+step's working set (410 MB of feature rows, 629 MB of F, 629 MB of target features) is
+larger than the 126 MB L2, so nothing is flushed between steps.  The step is replayed
+as one CUDA graph (--no-graph: direct launches).
+
+Prints ONE JSON line (rank 0).  With N>1 (torchrun) every rank renders its own
+replica of the workload (replicas only: the path has no exchange step) and the line
+reports total pixels over the max per-rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TopK feature render fwd+bwd Mpix/s (D=512,K=8), BF16-batched vs FP32; %HBM peak"
+UNIT = "Mpix/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------
+class Step:
+    """All buffers of one training step, resident on the device."""
+
+    def __init__(self, workload, seed=0):
+        import torch
+        import gs_scenes as S
+        from paper_2602_06991_b300.renderer import TopKRenderer
+        sc, cams, K, tile, fdt = S.make_config(workload, seed)
+        self.scene, self.cams, self.K, self.tile, self.fdt = sc, cams, K, tile, fdt
+        self.r = TopKRenderer(cams, K=K, D=sc.d, tile=tile, feat_dtype=fdt, check_overflow=True)
+        dev = self.r.device
+        tdt = self.r.feat_torch_dtype
+        t = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(dev).to(dt).contiguous()
+        self.inp = [t(sc.mean3d), t(sc.cov3d), t(sc.opacity), t(sc.rgb), t(sc.feats, tdt)]
+        Fgt, Cgt, Dgt = S.voronoi_targets(seed + 100, cams, sc.d)
+        self.tgt = [t(Fgt, tdt), t(Cgt), t(Dgt)]
+        self.N, self.P, self.D = sc.n, self.r.P, sc.d
+        # first forward checks the instance capacity once (host sync), then steps run free
+        self.out = self.r.forward(*self.inp)
+        self.r.check_overflow = False
+        self.lo = self.r.loss(self.out["F"], self.tgt[0], self.out["rgb"], self.tgt[1], self.out["depth"], self.tgt[2])
+        self.grads = self.r.alloc_grads(self.N)
+        self.r.backward(self.lo["dL_dF"], self.lo["dL_dC"], self.lo["dL_dD"], grads=self.grads)
+        torch.cuda.synchronize()
+
+    def run(self, events=None):
+        r, o = self.r, self.out
+        if events: events[0].record()
+        r._forward_into(self.N, *self.inp, o)
+        if events: events[1].record()
+        r.loss(o["F"], self.tgt[0], o["rgb"], self.tgt[1], o["depth"], self.tgt[2], out=self.lo)
+        if events: events[2].record()
+        r.backward(self.lo["dL_dF"], self.lo["dL_dC"], self.lo["dL_dD"], grads=self.grads)
+        if events: events[3].record()
+
+    def run_blend_only(self):
+        import ctypes
+        from paper_2602_06991_b300.renderer import _p
+        o = self.out
+        self.r.lib.gs_feature_blend(ctypes.byref(self.r.cfg), self.P, self.N, _p(o["topk_idx"]), _p(o["topk_w"]),
+                                    _p(self.inp[4]), _p(o["F"]), self.r._stream())
+
+
+def blend_algorithmic_bytes(step):
+    """Bytes the gather-blend must move: F written (P D s), the Top-K record read
+    (P K (4 + 4)), and each distinct selected feature row read once (U D s)."""
+    idx = step.out["topk_idx"]
+    uniq = int(np.unique(idx.cpu().numpy()[idx.cpu().numpy() >= 0]).size)
+    s = 2 if step.fdt == "bf16" else 4
+    return step.P * step.D * s + step.P * step.K * 8 + uniq * step.D * s, uniq
+
+
+def count_launches(step):
+    """Kernels of this library launched by one step, counted with the torch profiler
+    (CUPTI) on one extra untimed step."""
+    import torch
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            step.run()
+            torch.cuda.synchronize()
+        n = 0
+        for ev in prof.events():
+            if getattr(ev, "device_type", None) is not None and "CUDA" in str(ev.device_type):
+                nm = ev.name
+                if nm.startswith("void gs::") or nm.startswith("gs::") or "gs::k_" in nm:
+                    n += 1
+        return n if n > 0 else None
+    except Exception:
+        return None
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2602_06991_b300 import build
+    build()
+    step = Step(args.workload, seed=rank)
+    stream = torch.cuda.current_stream()
+    launches_per_step = count_launches(step)
+    graph = None
+    if not args.no_graph:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(stream)
+        with torch.cuda.stream(s):
+            step.run()                      # warm inside the side stream before capture
+        stream.wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            step.run()
+        graph = g
+    fn = graph.replay if graph is not None else step.run
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    # stage breakdown (untimed pass, direct launches, events on the launching stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    step.run(events=ev)
+    torch.cuda.synchronize()
+    stages = {"forward_ms": ev[0].elapsed_time(ev[1]), "loss_ms": ev[1].elapsed_time(ev[2]),
+              "backward_ms": ev[2].elapsed_time(ev[3])}
+    # blend kernel alone, averaged, for the roofline
+    nb = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(nb):
+        step.run_blend_only()
+    e1.record()
+    torch.cuda.synchronize()
+    blend_ms = e0.elapsed_time(e1) / nb
+
+    clocks = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        fn()
+    t1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms = float(tt.item())
+    value = world * step.P / (ms * 1e-3) / 1e6
+
+    hbm, peak_kind = peaks()
+    ab, uniq = blend_algorithmic_bytes(step)
+    achieved = ab / (blend_ms * 1e-3) / 1e9
+    res = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if step.fdt == "f32" else "bf16", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {__import__('gs_scenes').CONFIGS[args.workload]}",
+                   "gaussians": step.N, "pixels_per_step": step.P, "D": step.D, "K": step.K,
+                   "tile": list(step.tile), "graph": graph is not None,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "stages": {k: round(v, 4) for k, v in stages.items()},
+        "roofline": {"kernel": "gs_feature_blend (k_blend)", "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                     "traffic": None, "algorithmic_bytes": ab, "unique_rows": uniq,
+                     "kernel_ms": round(blend_ms, 4)},
+        "clocks": clk,
+        "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
+        "launches_per_step": launches_per_step,
+    }
+    if rank == 0 and not args.no_e2e:
+        res["e2e"] = run_e2e(step, args)
+    if rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
+    return res
+
+
+def run_e2e(step, args):
+    """Same metric through the C ABI with host buffers: every step copies its inputs
+    (Gaussian parameters and target maps) from pinned host memory, runs the step, and
+    reads the loss and every per-Gaussian gradient back."""
+    import torch
+    host_in = [t.cpu().pin_memory() for t in step.inp + step.tgt]
+    host_out = [t.cpu().pin_memory() for t in list(step.grads.values()) + [step.lo["loss"]]]
+    dev_in = step.inp + step.tgt
+    dev_out = list(step.grads.values()) + [step.lo["loss"]]
+    bi = sum(t.numel() * t.element_size() for t in host_in)
+    bo = sum(t.numel() * t.element_size() for t in host_out)
+
+    def one():
+        for h, d in zip(host_in, dev_in):
+            d.copy_(h, non_blocking=True)
+        step.run()
+        for h, d in zip(host_out, dev_out):
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(2):
+        one()
+    torch.cuda.synchronize()
+    n = max(3, min(args.steps, 10))
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(n):
+        one()
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / n
+    return {"value": round(step.P / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": bi,
+            "d2h_bytes_per_step": bo, "ms_per_step": round(ms, 3), "steps": n}
+
+
+# ----------------------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle, as it stands, on a bounded pixel sample
+# ----------------------------------------------------------------------------------------
+def cpu_baseline(workload, budget_s=15.0, seed=0):
+    import gs_scenes as S
+    import oracle
+    sc, cams, K, tile, fdt = S.make_config(workload, seed)
+    cam = cams[0]
+    Fgt, Cgt, Dgt = S.voronoi_targets(seed + 100, [cam], sc.d)
+    rng = np.random.default_rng(seed)
+    t_start = time.perf_counter()
+    proj = oracle.project(sc, cam)
+    done = 0
+    batch = 8
+    while time.perf_counter() - t_start < budget_s:
+        pix = rng.choice(cam.n_pix, batch, replace=False)
+        r = oracle.render(sc, cam, K, pixels=pix, proj=proj)
+        # loss gradient at those pixels (plain numpy, FP64), then the oracle adjoint
+        F, Fg = r["F"], Fgt[pix].astype(np.float64)
+        nf = np.linalg.norm(F, axis=1, keepdims=True)
+        ng = np.linalg.norm(Fg, axis=1, keepdims=True)
+        ok = (nf > 0) & (ng > 0)
+        cosv = np.where(ok, (F * Fg).sum(1, keepdims=True) / np.maximum(nf * ng, 1e-300), 0)
+        dF = np.where(ok, -(Fg / np.maximum(nf * ng, 1e-300) - cosv * F / np.maximum(nf ** 2, 1e-300)), 0) / cam.n_pix
+        dC = np.sign(r["C"] - Cgt[pix]) / (3 * cam.n_pix)
+        dD = np.sign(r["D"] - Dgt[pix]) / cam.n_pix
+        oracle.backward(sc, cam, K, dF, dC, dD, pixels=pix, proj=proj)
+        done += batch
+    el = time.perf_counter() - t_start
+    return {"value": round(done / el / 1e6, 9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} random pixels of the '{workload}' workload, forward + loss + backward, "
+                      f"FP64 single-threaded C, {el:.1f} s (projection included)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    cb = cpu_baseline(args.workload, budget_s=max(5.0, min(60.0, 3.0 * args.steps)))
+    return {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"{args.workload}: {__import__('gs_scenes').CONFIGS[args.workload]}"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="frame")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            torch.cuda.set_device(local_rank)
+            torch.distributed.init_process_group("nccl")
+        res = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,130 @@
+"""GPU parity of the forward path (a1-a4) against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import gs_scenes as S
+import oracle
+import parity_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+def test_small_full_frame_parity():
+    """2,000 Gaussians, 128x96, D=16, K=4: every pixel against the oracle."""
+    sc, cams, K, tile, _ = S.make_config("small", 0)
+    r, ts, out = U.gpu_forward(sc, cams, K, tile)
+    g = U.to_np(out)
+    o = U.oracle_forward(sc, cams, K)
+    st = U.compare_forward(g, o, K)
+    print("small", st)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (16, 8), (8, 8)])
+def test_tile_shape_independence(tile):
+    """The contributor set is defined per pixel, so every tile shape gives bit-identical
+    outputs (and all match the oracle)."""
+    sc, cams, K, _, _ = S.make_config("small", 1)
+    _, _, ref = U.gpu_forward(sc, cams, K, (16, 16))
+    _, _, out = U.gpu_forward(sc, cams, K, tile)
+    for k in ("rgb", "depth", "T", "n_contrib", "topk_idx", "topk_w", "F"):
+        assert torch.equal(ref[k], out[k]), k
+    U.compare_forward(U.to_np(out), U.oracle_forward(sc, cams, K), K)
+
+
+@pytest.mark.parametrize("K", [1, 3, 5, 8, 10, 16, 32])
+def test_k_values(K):
+    sc, cams, _, tile, _ = S.make_config("small", 2)
+    _, _, out = U.gpu_forward(sc, cams, K, tile)
+    o = U.oracle_forward(sc, cams, K, pixels_per_cam=[np.arange(0, cams[0].n_pix, 3)])
+    U.compare_forward(U.to_np(out), o, K)
+
+
+@pytest.mark.parametrize("D", [8, 24, 136, 512, 1024])
+def test_feature_widths(D):
+    sc = S.random_scene_box(3, 1500, D)
+    cams = [S.pinhole(96, 64, 80.0)]
+    _, _, out = U.gpu_forward(sc, cams, 6)
+    o = U.oracle_forward(sc, cams, 6, pixels_per_cam=[np.arange(0, cams[0].n_pix, 5)])
+    U.compare_forward(U.to_np(out), o, 6)
+
+
+def test_ragged_multi_camera_general_poses():
+    """Three cameras of uneven, non-tile-multiple sizes on an orbit (general rotations):
+    one flat pixel space, each camera against the oracle."""
+    sc = S.random_scene_box(4, 3000, 32, box=((-1, 1), (-1, 1), (2, 4)))
+    cams = S.orbit_cameras(7, [(100, 75, 90.0), (64, 48, 50.0), (131, 97, 120.0)], radius=3.0)
+    _, _, out = U.gpu_forward(sc, cams, 8, (16, 8))
+    o = U.oracle_forward(sc, cams, 8)
+    st = U.compare_forward(U.to_np(out), o, 8)
+    print("multi", st)
+
+
+def test_empty_and_degenerate_scenes():
+    cams = [S.pinhole(40, 30, 40.0)]
+    # N = 0
+    sc0 = S.random_scene_box(0, 0, 8)
+    _, _, out = U.gpu_forward(sc0, cams, 4)
+    assert torch.all(out["T"] == 1) and torch.all(out["topk_idx"] == -1) and torch.all(out["F"] == 0)
+    assert torch.all(out["n_contrib"] == 0)
+    # everything behind the camera or below the opacity floor
+    sc = S.random_scene_box(1, 50, 8)
+    sc.mean3d[:, 2] = -sc.mean3d[:, 2]
+    _, _, out = U.gpu_forward(sc, cams, 4)
+    assert torch.all(out["n_contrib"] == 0) and torch.all(out["F"] == 0)
+    sc = S.random_scene_box(1, 50, 8)
+    sc.opacity[:] = 1e-3
+    _, _, out = U.gpu_forward(sc, cams, 4)
+    assert torch.all(out["n_contrib"] == 0)
+    # a single Gaussian
+    sc = S.random_scene_box(2, 1, 8, box=((0, 0), (0, 0), (2, 2)), log_scale_mu=-2.0)
+    _, _, out = U.gpu_forward(sc, cams, 4)
+    U.compare_forward(U.to_np(out), U.oracle_forward(sc, cams, 4), 4)
+
+
+def test_overflow_reported_and_recovered():
+    """A too-small instance capacity is reported as GS_ERR_OVERFLOW by the device error
+    word; the binding then grows the capacity and renders correctly."""
+    from paper_2602_06991_b300 import _abi as A
+    from paper_2602_06991_b300.renderer import TopKRenderer
+    sc, cams, K, tile, _ = S.make_config("small", 0)
+    r = TopKRenderer(cams, K=K, D=sc.d, tile=tile, max_instances=4096, check_overflow=False)
+    out = r.forward(*U.tensors(sc))
+    st, m = r.sync_status()
+    assert st == A.GS_ERR_OVERFLOW and m > 4096
+    r.check_overflow = True
+    out = r.forward(*U.tensors(sc))
+    U.compare_forward(U.to_np(out), U.oracle_forward(sc, cams, K), K)
+
+
+def test_frame_workload_sampled_pixels():
+    """The full 'frame' workload (200k Gaussians on planes, 640x480, D=512, K=8) in the
+    launch configuration the benchmark times; 384 seeded pixels against the oracle."""
+    sc, cams, K, tile, _ = S.make_config("frame", 0)
+    _, _, out = U.gpu_forward(sc, cams, K, tile)
+    rng = np.random.default_rng(0)
+    pix = np.sort(rng.choice(cams[0].n_pix, 384, replace=False))
+    o = U.oracle_forward(sc, cams, K, pixels_per_cam=[pix])
+    st = U.compare_forward(U.to_np(out), o, K)
+    print("frame", st)
+    # invariants over every pixel
+    w = out["topk_w"]
+    assert torch.all(w >= 0) and torch.all(w <= 1)
+    assert torch.all(w[:, :-1] >= w[:, 1:])
+    nrm = out["F"].norm(dim=1)
+    assert torch.all(nrm <= 1 + 1e-5)
+
+
+def test_bf16_rows_cosine():
+    """BF16 feature rows and BF16 F: per-pixel cosine >= 0.999 against the FP64 oracle
+    with the float32 rows; index sets as in float32."""
+    sc, cams, K, tile, _ = S.make_config("small", 5)
+    _, _, out = U.gpu_forward(sc, cams, K, tile, feat_dtype="bf16")
+    o = U.oracle_forward(sc, cams, K)
+    g = U.to_np(out)
+    ok = (o["flags"] & U.FRAGILE_SET) == 0
+    Fg, Fo = g["F"][ok].astype(np.float64), o["F"][ok]
+    nz = np.linalg.norm(Fo, axis=1) > 0
+    cos = (Fg[nz] * Fo[nz]).sum(1) / (np.linalg.norm(Fg[nz], axis=1) * np.linalg.norm(Fo[nz], axis=1))
+    assert cos.min() >= 0.999, cos.min()
+    assert np.array_equal(g["n_contrib"][ok], o["n"][ok])
