@@ -176,7 +176,7 @@ def run_ours(args, rank, world, local_rank):
     build()
     step = Step(args.workload, seed=rank)
     stream = torch.cuda.current_stream()
-    launches_per_step = count_launches(step)
+    launches_per_step = None if args.no_launch_count else count_launches(step)
     graph = None
     if not args.no_graph:
         g = torch.cuda.CUDAGraph()
@@ -347,6 +347,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-launch-count", action="store_true", help="skip the CUPTI launch count (for ncu runs)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
