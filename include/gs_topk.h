@@ -165,6 +165,22 @@ int gs_loss_cos_l1(const gs_config *cfg, int64_t n_pix, const void *F, const voi
                    void *dL_dF, float *dL_dC, float *dL_dD, float *loss,
                    void *scratch, size_t scratch_bytes, void *stream);
 
+/* Same loss as gs_loss_cos_l1, for callers that cannot allocate device memory (code in
+ * a real-time loop where cudaMalloc may stall the device, a plug-in inside a host
+ * framework that owns all device memory, a component handed only its buffers).  The
+ * paper has no counterpart; this is a property of the library.  No scratch argument:
+ * the per-pixel partial sums live in a fixed array the library holds on every GPU that
+ * loads it (GS_LOSS_NOALLOC_MAX_PIX + 360 floats, about 16.8 MB, kept until exit).
+ * n_pix > GS_LOSS_NOALLOC_MAX_PIX returns GS_ERR_WORKSPACE without launching.  The
+ * first call on a device looks up the array's device address for that device; make
+ * it before any stream capture.  All calls share the array: calls whose kernels
+ * overlap on the GPU race.  Allocates nothing. */
+#define GS_LOSS_NOALLOC_MAX_PIX (1 << 22)
+int gs_loss_cos_l1_noalloc(const gs_config *cfg, int64_t n_pix, const void *F, const void *F_gt,
+                           const float *rgb, const float *rgb_gt, const float *depth, const float *depth_gt,
+                           float w_feat, float w_rgb, float w_depth,
+                           void *dL_dF, float *dL_dC, float *dL_dD, float *loss, void *stream);
+
 /* Synchronises `stream` and returns the workspace error word as a status (GS_OK if
  * clear).  If n_instances is not NULL it receives the instance count of the last
  * gs_bin_sort. */

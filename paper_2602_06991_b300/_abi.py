@@ -16,6 +16,7 @@ GS_F32, GS_BF16 = 0, 1
 GS_MAX_CAMERAS = 16
 GS_MAX_K = 32
 GS_PROJ_FLOATS = 16
+GS_LOSS_NOALLOC_MAX_PIX = 1 << 22
 
 c_float_p = ctypes.c_void_p
 vp = ctypes.c_void_p
@@ -65,6 +66,8 @@ PROTOTYPES = {
     "gs_loss_cos_l1": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.c_int64, vp, vp, vp, vp, vp, vp,
                                       ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, vp, vp, vp, vp,
                                       ctypes.c_size_t, vp]),
+    "gs_loss_cos_l1_noalloc": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.c_int64, vp, vp, vp, vp, vp, vp,
+                                              ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, vp, vp, vp, vp]),
     "gs_sync_status": (ctypes.c_int, [vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int64)]),
 }
 
