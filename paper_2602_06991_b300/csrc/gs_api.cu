@@ -103,21 +103,25 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     for (int i = 0; i < 2; ++i) L.inst_vals[i] = take(u * L.Mcap);
     L.inst_elem = take(u * L.Mcap);
     L.tile_range = take(8 * (size_t)L.n_tiles);
-    L.sort_hist = take(u * 256 * kSortBlocks);
+    L.sort_hist = take(u * 256 * (kSortBlocks + 1));
     L.scan_aux = take(u * (kSortBlocks + 32));
     L.inst_grad = take(sizeof(float) * kGradVals * L.Mcap);
+    L.elem_grad = take(sizeof(float) * kGradVals * L.NE);
     for (int i = 0; i < 2; ++i) L.rank_keys[i] = take(u * N);
     for (int i = 0; i < 2; ++i) L.rank_vals[i] = take(u * N);
     L.grank = take(u * N);
     for (int i = 0; i < 2; ++i) L.pair_keys[i] = take(u * L.n_pairs);
     for (int i = 0; i < 2; ++i) L.pair_vals[i] = take(u * L.n_pairs);
     L.hbuf = take(sizeof(float) * L.PK);
+    L.wnorm = take(sizeof(float) * L.PK);
     L.seg_start = take(u * N);
     L.seg_end = take(u * N);
     L.pieces = take(u * N);
     L.piece_off = take(u * N);
     L.multi = take(u * N);
     L.multi_off = take(u * N);
+    L.mflag = take(u * N);
+    L.mlist = take(u * N);
     L.piece_rank = take(u * L.max_pieces);
     L.piece_rows = take(sizeof(float) * (size_t)L.max_multi_rows * cfg->D);
     L.loss_part = 0;
@@ -271,7 +275,7 @@ int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int
         return GS_ERR_UNSUPPORTED;
     launch_project_backward(ct, n_gauss, mean3d, cov3d, proj, ws_ptr<uint32_t>(ws, L.elem_off),
                             ws_ptr<uint32_t>(ws, L.elem_cnt), ws_ptr<float>(ws, L.inst_grad),
-                            ws_ptr<int>(ws, L.header), grads, s);
+                            ws_ptr<float>(ws, L.elem_grad), ws_ptr<int>(ws, L.header), grads, s);
     return launch_status();
 }
 

@@ -49,32 +49,48 @@ __global__ void k_count_tiles(CamTable ct, int N, long long NE, const float4 *__
     elem_cnt[e] = n;
 }
 
-__global__ void k_duplicate(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
-                            const uint32_t *__restrict__ sorted_e, const uint32_t *__restrict__ offsets,
-                            uint32_t mcap, uint32_t *inst_keys, uint32_t *inst_vals, uint32_t *inst_elem,
-                            uint32_t *elem_off, uint32_t *elem_cnt, int *err)
+// One warp per 32 consecutive depth ranks: each lane works out its element's tile
+// rectangle, then the warp writes the instances element by element, lanes striding over
+// the rectangle, so large footprints are written in parallel and coalesced.
+__global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
+                                                   const uint32_t *__restrict__ sorted_e,
+                                                   const uint32_t *__restrict__ offsets, uint32_t mcap,
+                                                   uint32_t *inst_keys, uint32_t *inst_vals, uint32_t *inst_elem,
+                                                   uint32_t *elem_off, uint32_t *elem_cnt, int *err)
 {
-    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= NE) return;
-    uint32_t e = sorted_e[r];
-    uint32_t o = offsets[r];
-    elem_off[e] = o;
-    int c, tx0, tx1, ty0, ty1;
-    uint32_t n = tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1);
-    if (n == 0) return;
-    if ((unsigned long long)o + n > mcap) {
-        // instances past the capacity are dropped; the render is reported as failed
-        atomicOr(err, kErrOverflow);
-        elem_cnt[e] = o < mcap ? mcap - o : 0u;
-    }
-    const CamDev &cam = ct.c[c];
-    for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1 && o < mcap; ++tx) {
-            inst_keys[o] = (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx);
-            inst_vals[o] = o;
-            inst_elem[o] = e;
-            ++o;
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    uint32_t e = 0, o = 0, n = 0;
+    int c = 0, tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+    if (r < NE) {
+        e = sorted_e[r];
+        o = offsets[r];
+        elem_off[e] = o;
+        n = tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1);
+        if (n > 0 && (unsigned long long)o + n > mcap) {
+            // instances past the capacity are dropped; the render is reported as failed
+            atomicOr(err, kErrOverflow);
+            elem_cnt[e] = o < mcap ? mcap - o : 0u;
         }
+    }
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t nj = __shfl_sync(0xffffffffu, n, j);
+        if (nj == 0) continue;
+        const uint32_t ej = __shfl_sync(0xffffffffu, e, j), oj = __shfl_sync(0xffffffffu, o, j);
+        const int cj = __shfl_sync(0xffffffffu, c, j);
+        const int x0 = __shfl_sync(0xffffffffu, tx0, j), x1 = __shfl_sync(0xffffffffu, tx1, j);
+        const int y0 = __shfl_sync(0xffffffffu, ty0, j);
+        const int w = x1 - x0 + 1;
+        const CamDev &cam = ct.c[cj];
+        for (uint32_t t = lane; t < nj; t += 32) {
+            uint32_t oo = oj + t;
+            if (oo >= mcap) break;
+            int ty = y0 + (int)(t / (uint32_t)w), tx = x0 + (int)(t % (uint32_t)w);
+            inst_keys[oo] = (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx);
+            inst_vals[oo] = oo;
+            inst_elem[oo] = ej;
+        }
+    }
 }
 
 __global__ void k_tile_ranges(const uint32_t *__restrict__ keys, const uint32_t *n_dev, uint32_t mcap, int2 *ranges,

@@ -93,8 +93,9 @@ __global__ void k_rank_scatter(int N, const uint32_t *__restrict__ order, uint32
 
 constexpr uint32_t kMarker = 0xffffffffu;
 
-__global__ void k_pairs(int N, long long PK, const int *__restrict__ topk_idx, const uint32_t *__restrict__ grank,
-                        uint32_t *keys, uint32_t *vals)
+__global__ void k_pairs(int N, int K, long long PK, const int *__restrict__ topk_idx,
+                        const float *__restrict__ topk_w, const uint32_t *__restrict__ grank, uint32_t *keys,
+                        uint32_t *vals, float *wnorm)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) {
@@ -105,6 +106,11 @@ __global__ void k_pairs(int N, long long PK, const int *__restrict__ topk_idx, c
         int id = topk_idx[s];
         keys[i] = id >= 0 ? grank[id] : (uint32_t)N;
         vals[i] = (uint32_t)s;
+        // renormalised weight w / S (Eq. 3), summed in slot order as the blend does
+        long long p = s / K;
+        float S = 0.f;
+        for (int k = 0; k < K; ++k) S += topk_w[p * K + k];
+        wnorm[s] = S > 0.f ? topk_w[s] * (1.f / S) : 0.f;
     }
 }
 
@@ -131,12 +137,20 @@ __global__ void k_pieces(int N, const uint32_t *__restrict__ seg_start, const ui
 }
 
 __global__ void k_piece_rank(int N, const uint32_t *__restrict__ pieces, const uint32_t *__restrict__ piece_off,
-                             uint32_t *piece_rank)
+                             const uint32_t *__restrict__ multi, const uint32_t *__restrict__ mflag_off,
+                             uint32_t *piece_rank, uint32_t *mlist)
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= N) return;
     uint32_t o = piece_off[r], n = pieces[r];
     for (uint32_t j = 0; j < n; ++j) piece_rank[o + j] = (uint32_t)r;
+    if (multi[r] > 0) mlist[mflag_off[r]] = (uint32_t)r;
+}
+
+__global__ void k_multi_flags(int N, const uint32_t *__restrict__ multi, uint32_t *mflag)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < N) mflag[r] = multi[r] > 0 ? 1u : 0u;
 }
 
 template <bool BF16>
@@ -169,6 +183,9 @@ struct Row<true> {
 };
 
 // One warp per piece.  CPL = 16-byte chunks per lane (row has nch <= 32 CPL chunks).
+// Four pairs are in flight at a time: their dL/dF chunks are loaded together, then
+// accumulated, and their four dot products with the Gaussian's own row are reduced with
+// one reduce-scatter (6 shuffles for 4 dots).
 template <bool BF16, int CPL>
 __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32_t *__restrict__ n_pieces_dev,
                                                     const uint32_t *__restrict__ piece_rank,
@@ -179,12 +196,13 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
                                                     const uint32_t *__restrict__ seg_end,
                                                     const uint32_t *__restrict__ order,
                                                     const uint32_t *__restrict__ pair_vals,
-                                                    const float *__restrict__ topk_w, const void *__restrict__ feats,
+                                                    const float *__restrict__ wnorm, const void *__restrict__ feats,
                                                     const void *__restrict__ dLdF, float *__restrict__ hbuf,
                                                     float *__restrict__ grad_f, float *__restrict__ piece_rows)
 {
     using Rw = Row<BF16>;
     constexpr int VEC = Rw::VEC;
+    constexpr int U = 4;
     const int lane = threadIdx.x & 31;
     const long long pc = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (pc >= (long long)*n_pieces_dev) return;
@@ -201,19 +219,54 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
         for (int i = 0; i < VEC; ++i) { f[c][i] = 0.f; acc[c][i] = 0.f; }
         if (ch < nch) Rw::load(feats, (size_t)g * nch + ch, f[c]);
     }
-    for (uint32_t m = m0; m < m1; ++m) {
-        const uint32_t s = pair_vals[m];
-        const uint32_t p = s / (uint32_t)K;
-        float S = 0.f;
-        for (int k = 0; k < K; ++k) S += __ldg(topk_w + (size_t)p * K + k);
-        const float wp = __ldg(topk_w + s) * (1.f / S);
+    uint32_t m = m0;
+    for (; m + U <= m1; m += U) {
+        uint32_t sv[U], pv[U];
+        float wp[U], dot[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            sv[u] = pair_vals[m + u];
+            pv[u] = sv[u] / (uint32_t)K;
+            wp[u] = __ldg(wnorm + sv[u]);
+            dot[u] = 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            int ch = lane + 32 * c;
+            if (ch < nch) {
+                float x[U][VEC];
+#pragma unroll
+                for (int u = 0; u < U; ++u) Rw::load(dLdF, (size_t)pv[u] * nch + ch, x[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int i = 0; i < VEC; ++i) {
+                        acc[c][i] = fmaf(wp[u], x[u][i], acc[c][i]);
+                        dot[u] = fmaf(x[u][i], f[c][i], dot[u]);
+                    }
+            }
+        }
+        // reduce-scatter of 4 dots: lane l ends with dot (l >> 3) & 3 (lanes 0, 8, 16, 24)
+        const bool b4 = lane & 16, b3 = lane & 8;
+        float a0 = (b4 ? dot[2] : dot[0]) + __shfl_xor_sync(0xffffffffu, b4 ? dot[0] : dot[2], 16);
+        float a1 = (b4 ? dot[3] : dot[1]) + __shfl_xor_sync(0xffffffffu, b4 ? dot[1] : dot[3], 16);
+        float d = (b3 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, b3 ? a0 : a1, 8);
+        d += __shfl_xor_sync(0xffffffffu, d, 4);
+        d += __shfl_xor_sync(0xffffffffu, d, 2);
+        d += __shfl_xor_sync(0xffffffffu, d, 1);
+        if ((lane & 7) == 0) hbuf[sv[(lane >> 3) & 3]] = d;
+    }
+    for (; m < m1; ++m) {
+        const uint32_t sv = pair_vals[m];
+        const uint32_t pv = sv / (uint32_t)K;
+        const float wp = __ldg(wnorm + sv);
         float dot = 0.f;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             int ch = lane + 32 * c;
             if (ch < nch) {
                 float x[VEC];
-                Rw::load(dLdF, (size_t)p * nch + ch, x);
+                Rw::load(dLdF, (size_t)pv * nch + ch, x);
 #pragma unroll
                 for (int i = 0; i < VEC; ++i) {
                     acc[c][i] = fmaf(wp, x[i], acc[c][i]);
@@ -223,7 +276,7 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        if (lane == 0) hbuf[s] = dot;
+        if (lane == 0) hbuf[sv] = dot;
     }
     float *dst = pieces[r] == 1 ? grad_f + (size_t)g * nch * VEC
                                 : piece_rows + (size_t)(multi_off[r] + j) * nch * VEC;
@@ -239,24 +292,41 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
     }
 }
 
-__global__ void __launch_bounds__(256) k_fgrad_fixup(int N, int D4, const uint32_t *__restrict__ multi,
+// Gaussians whose segment was cut into several pieces: one CTA per such Gaussian (from
+// the compact list), threads over float4 columns, rows summed in a fixed order with
+// four independent accumulators.
+__global__ void __launch_bounds__(128) k_fgrad_fixup(int D4, const uint32_t *__restrict__ n_multi_dev,
+                                                     const uint32_t *__restrict__ mlist,
+                                                     const uint32_t *__restrict__ multi,
                                                      const uint32_t *__restrict__ multi_off,
                                                      const uint32_t *__restrict__ order,
                                                      const float4 *__restrict__ piece_rows, float4 *__restrict__ grad_f)
 {
-    const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (r >= N) return;
-    const uint32_t n = multi[r];
-    if (n == 0) return;
-    const uint32_t base = multi_off[r], g = order[r];
-    for (int c = lane; c < D4; c += 32) {
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (uint32_t i = 0; i < n; ++i) {
-            float4 v = piece_rows[(size_t)(base + i) * D4 + c];
-            a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+    const uint32_t n_multi = *n_multi_dev;
+    for (uint32_t i = blockIdx.x; i < n_multi; i += gridDim.x) {
+        const uint32_t r = mlist[i];
+        const uint32_t n = multi[r], base = multi_off[r], g = order[r];
+        for (int c = threadIdx.x; c < D4; c += blockDim.x) {
+            float4 a[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) a[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            uint32_t k = 0;
+            for (; k + 4 <= n; k += 4) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float4 v = __ldg(piece_rows + (size_t)(base + k + q) * D4 + c);
+                    a[q].x += v.x; a[q].y += v.y; a[q].z += v.z; a[q].w += v.w;
+                }
+            }
+            for (; k < n; ++k) {
+                float4 v = __ldg(piece_rows + (size_t)(base + k) * D4 + c);
+                a[0].x += v.x; a[0].y += v.y; a[0].z += v.z; a[0].w += v.w;
+            }
+            grad_f[(size_t)g * D4 + c] = make_float4((a[0].x + a[1].x) + (a[2].x + a[3].x),
+                                                     (a[0].y + a[1].y) + (a[2].y + a[3].y),
+                                                     (a[0].z + a[1].z) + (a[2].z + a[3].z),
+                                                     (a[0].w + a[1].w) + (a[2].w + a[3].w));
         }
-        grad_f[(size_t)g * D4 + c] = a;
     }
 }
 
@@ -264,13 +334,13 @@ template <bool BF16>
 static bool fgrad_main(int cpl, unsigned blocks, cudaStream_t s, int K, int nch, const uint32_t *np,
                        const uint32_t *pr, const uint32_t *po, const uint32_t *pcs, const uint32_t *mo,
                        const uint32_t *ss, const uint32_t *se, const uint32_t *ord, const uint32_t *pv,
-                       const float *tw, const void *feats, const void *dLdF, float *h, float *gf, float *rows)
+                       const float *wn, const void *feats, const void *dLdF, float *h, float *gf, float *rows)
 {
     switch (cpl) {
-    case 1: k_fgrad_main<BF16, 1><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, tw, feats, dLdF, h, gf, rows); return true;
-    case 2: k_fgrad_main<BF16, 2><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, tw, feats, dLdF, h, gf, rows); return true;
-    case 4: k_fgrad_main<BF16, 4><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, tw, feats, dLdF, h, gf, rows); return true;
-    case 8: k_fgrad_main<BF16, 8><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, tw, feats, dLdF, h, gf, rows); return true;
+    case 1: k_fgrad_main<BF16, 1><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
+    case 2: k_fgrad_main<BF16, 2><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
+    case 4: k_fgrad_main<BF16, 4><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
+    case 8: k_fgrad_main<BF16, 8><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
     }
     return false;
 }
@@ -281,6 +351,7 @@ bool launch_feature_grad(const WsLayout &L, int dtype, int N, const float *mean3
 {
     uint32_t *hdr = ws_ptr<uint32_t>(ws, L.header);
     uint32_t *n_pieces = hdr + 2;
+    uint32_t *n_multi = hdr + 3;
     int *bb = (int *)(hdr + 4);
     uint32_t *hist = ws_ptr<uint32_t>(ws, L.sort_hist);
     uint32_t *aux = ws_ptr<uint32_t>(ws, L.scan_aux);
@@ -290,9 +361,11 @@ bool launch_feature_grad(const WsLayout &L, int dtype, int N, const float *mean3
     uint32_t *pk[2] = {ws_ptr<uint32_t>(ws, L.pair_keys[0]), ws_ptr<uint32_t>(ws, L.pair_keys[1])};
     uint32_t *pv[2] = {ws_ptr<uint32_t>(ws, L.pair_vals[0]), ws_ptr<uint32_t>(ws, L.pair_vals[1])};
     float *hbuf = ws_ptr<float>(ws, L.hbuf);
+    float *wnorm = ws_ptr<float>(ws, L.wnorm);
     uint32_t *seg_start = ws_ptr<uint32_t>(ws, L.seg_start), *seg_end = ws_ptr<uint32_t>(ws, L.seg_end);
     uint32_t *pieces = ws_ptr<uint32_t>(ws, L.pieces), *piece_off = ws_ptr<uint32_t>(ws, L.piece_off);
     uint32_t *multi = ws_ptr<uint32_t>(ws, L.multi), *multi_off = ws_ptr<uint32_t>(ws, L.multi_off);
+    uint32_t *mflag = ws_ptr<uint32_t>(ws, L.mflag), *mlist = ws_ptr<uint32_t>(ws, L.mlist);
     uint32_t *piece_rank = ws_ptr<uint32_t>(ws, L.piece_rank);
     float *rows = ws_ptr<float>(ws, L.piece_rows);
 
@@ -304,16 +377,19 @@ bool launch_feature_grad(const WsLayout &L, int dtype, int N, const float *mean3
     int rcur = radix_sort_pairs(rk[0], rk[1], rv[0], rv[1], N, nullptr, 30, hist, s);
     const uint32_t *order = rv[rcur];
     k_rank_scatter<<<nbN, 256, 0, s>>>(N, order, grank);
-    // 2. pairs sorted by rank
+    // 2. pairs sorted by rank (plus the renormalised weight of every slot)
     long long n_pairs = L.n_pairs;
-    k_pairs<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(N, L.PK, topk_idx, grank, pk[0], pv[0]);
+    k_pairs<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(N, L.K, L.PK, topk_idx, topk_w, grank, pk[0], pv[0],
+                                                              wnorm);
     int pcur = radix_sort_pairs(pk[0], pk[1], pv[0], pv[1], n_pairs, nullptr, L.pair_bits, hist, s);
     k_segments<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(N, n_pairs, pk[pcur], pv[pcur], seg_start, seg_end);
-    // 3. pieces
+    // 3. pieces, and the compact list of Gaussians cut into several pieces
     k_pieces<<<nbN, 256, 0, s>>>(N, seg_start, seg_end, pieces, multi);
     exclusive_scan_u32(pieces, piece_off, N, n_pieces, aux, s);
     exclusive_scan_u32(multi, multi_off, N, nullptr, aux, s);
-    k_piece_rank<<<nbN, 256, 0, s>>>(N, pieces, piece_off, piece_rank);
+    k_multi_flags<<<nbN, 256, 0, s>>>(N, multi, mflag);
+    exclusive_scan_u32(mflag, mflag, N, n_multi, aux, s);
+    k_piece_rank<<<nbN, 256, 0, s>>>(N, pieces, piece_off, multi, mflag, piece_rank, mlist);
     // 4. reduce
     const int vec = dtype == GS_BF16 ? 8 : 4;
     const int nch = L.D / vec;
@@ -321,12 +397,12 @@ bool launch_feature_grad(const WsLayout &L, int dtype, int N, const float *mean3
     unsigned blocks = (unsigned)((L.max_pieces * 32 + 255) / 256);
     bool ok = dtype == GS_BF16
                   ? fgrad_main<true>(cpl, blocks, s, L.K, nch, n_pieces, piece_rank, piece_off, pieces, multi_off,
-                                     seg_start, seg_end, order, pv[pcur], topk_w, feats, dLdF, hbuf, grad_feat, rows)
+                                     seg_start, seg_end, order, pv[pcur], wnorm, feats, dLdF, hbuf, grad_feat, rows)
                   : fgrad_main<false>(cpl, blocks, s, L.K, nch, n_pieces, piece_rank, piece_off, pieces, multi_off,
-                                      seg_start, seg_end, order, pv[pcur], topk_w, feats, dLdF, hbuf, grad_feat, rows);
+                                      seg_start, seg_end, order, pv[pcur], wnorm, feats, dLdF, hbuf, grad_feat, rows);
     if (!ok) return false;
-    k_fgrad_fixup<<<(unsigned)(((long long)N * 32 + 255) / 256), 256, 0, s>>>(N, L.D / 4, multi, multi_off, order,
-                                                                             (const float4 *)rows, (float4 *)grad_feat);
+    k_fgrad_fixup<<<148 * 4, 128, 0, s>>>(L.D / 4, n_multi, mlist, multi, multi_off, order, (const float4 *)rows,
+                                          (float4 *)grad_feat);
     return true;
 }
 

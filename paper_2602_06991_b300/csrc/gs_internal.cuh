@@ -142,6 +142,32 @@ __device__ __forceinline__ float eval_alpha(float q, float o, float &G, float &a
     return fminf(kAlphaClamp, ao);
 }
 
+// Sum 16 per-lane values over the warp with 16 shuffles (reduce-scatter): on return
+// lane l holds the total of value index (l >> 1) & 15; lanes l and l ^ 1 agree.
+__device__ __forceinline__ float warp_reduce16(const float (&v)[16], int lane)
+{
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float a[8], b[4], c2[2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float send = b4 ? v[i] : v[i + 8], keep = b4 ? v[i + 8] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float send = b3 ? a[i] : a[i + 4], keep = b3 ? a[i + 4] : a[i];
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        float send = b2 ? b[i] : b[i + 2], keep = b2 ? b[i + 2] : b[i];
+        c2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    float d = (b1 ? c2[1] : c2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? c2[0] : c2[1], 2);
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    return d;
+}
+
 // Top-K kept in registers, KM slots in descending weight.  Slots [0, KM - K) hold
 // +inf sentinels so that a runtime K <= KM keeps exactly its K largest in slots
 // [KM - K, KM); comparisons are strict, so among equal weights the earlier
@@ -189,13 +215,16 @@ struct WsLayout {
     size_t sort_hist;          // kSortBlocks x 256
     size_t scan_aux;           // scan block sums
     size_t inst_grad;          // Mcap x kGradVals floats (per-instance partial 2D gradients)
+    size_t elem_grad;          // NE x kGradVals floats (per-element sums of the instance partials)
     size_t rank_keys[2], rank_vals[2];     // N (Gaussians in 3D Morton order)
     size_t grank;              // N: Morton rank of each Gaussian
     size_t pair_keys[2], pair_vals[2];     // N + P K
     size_t hbuf;               // P K floats: dL/dF_p . f_{idx_k}
+    size_t wnorm;              // P K floats: renormalised Top-K weights w / S
     size_t seg_start, seg_end; // N each
     size_t pieces, piece_off;  // N each
     size_t multi, multi_off;   // N each
+    size_t mflag, mlist;       // N each: ranks with a multi-piece segment (flag scan, compact list)
     size_t piece_rank;         // max_pieces
     size_t piece_rows;         // max_multi_rows x D floats
     size_t loss_part;          // P + kSortBlocks floats
@@ -233,8 +262,8 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t
 void launch_preprocess(const CamTable &ct, int N, const float *mean3d, const float *cov3d, const float *opac,
                        const float *rgb, float *proj, cudaStream_t s);
 void launch_project_backward(const CamTable &ct, int N, const float *mean3d, const float *cov3d, const float *proj,
-                             const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad, const int *err,
-                             const gs_grads *gr, cudaStream_t s);
+                             const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad,
+                             float *elem_grad, const int *err, const gs_grads *gr, cudaStream_t s);
 void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *proj, void *ws, cudaStream_t s);
 bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj, void *ws,
                      float *rgb_out, float *depth_out, float *T_out, int *n_out, int *idx_out, float *w_out,

@@ -155,11 +155,35 @@ __global__ void __launch_bounds__(256) k_preprocess(CamTable ct, int N, const fl
 // then chain through conic -> Sigma2D -> (J R, Sigma3D) -> camera-space mean -> world
 // mean.  Partial layout per instance: du, dv, da, db, dc, dopacity, dr, dg, db, dz.
 // ------------------------------------------------------------------------------------
+// One warp per (camera, Gaussian) element: lanes stride over the element's instances
+// (contiguous pre-sort indices) and the 10 partial sums are reduced across the warp.
+__global__ void __launch_bounds__(256) k_elem_grad_sum(long long NE, const uint32_t *__restrict__ elem_off,
+                                                       const uint32_t *__restrict__ elem_cnt,
+                                                       const float *__restrict__ inst_grad, const int *err,
+                                                       float *__restrict__ elem_grad)
+{
+    const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (e >= NE) return;
+    float v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = 0.f;
+    if (*err == 0) {
+        const uint32_t o0 = elem_off[e], n = elem_cnt[e];
+        for (uint32_t i = lane; i < n; i += 32) {
+            const float *pg = inst_grad + kGradVals * (size_t)(o0 + i);
+#pragma unroll
+            for (int k = 0; k < kGradVals; ++k) v[k] += pg[k];
+        }
+    }
+    float d = warp_reduce16(v, lane);
+    int vi = (lane >> 1) & 15;
+    if (!(lane & 1) && vi < kGradVals) elem_grad[kGradVals * e + vi] = d;
+}
+
 __global__ void __launch_bounds__(256) k_project_backward(CamTable ct, int N, const float *__restrict__ mean3d,
                                                           const float *__restrict__ cov3d, const float4 *__restrict__ proj,
-                                                          const uint32_t *__restrict__ elem_off,
-                                                          const uint32_t *__restrict__ elem_cnt,
-                                                          const float *__restrict__ inst_grad, const int *err,
+                                                          const float *__restrict__ elem_grad, const int *err,
                                                           float *g_opac, float *g_rgb, float *g_mean3d, float *g_cov3d,
                                                           float *g_mean2d, float *g_conic)
 {
@@ -176,12 +200,8 @@ __global__ void __launch_bounds__(256) k_project_backward(CamTable ct, int N, co
         for (int v = 0; v < kGradVals; ++v) acc[v] = 0.f;
         bool live = __float_as_uint(r3.w) != 0u && !bad;
         if (live) {
-            uint32_t o0 = elem_off[e], n = elem_cnt[e];
-            for (uint32_t i = 0; i < n; ++i) {
-                const float *pg = inst_grad + kGradVals * (size_t)(o0 + i);
 #pragma unroll
-                for (int v = 0; v < kGradVals; ++v) acc[v] += pg[v];
-            }
+            for (int v = 0; v < kGradVals; ++v) acc[v] = elem_grad[kGradVals * e + v];
         }
         if (g_mean2d) {
             g_mean2d[2 * e] = acc[0];
@@ -276,13 +296,15 @@ void launch_preprocess(const CamTable &ct, int N, const float *mean3d, const flo
 }
 
 void launch_project_backward(const CamTable &ct, int N, const float *mean3d, const float *cov3d, const float *proj,
-                             const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad, const int *err,
-                             const gs_grads *gr, cudaStream_t s)
+                             const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad,
+                             float *elem_grad, const int *err, const gs_grads *gr, cudaStream_t s)
 {
     if (N <= 0) return;
-    k_project_backward<<<(N + 255) / 256, 256, 0, s>>>(ct, N, mean3d, cov3d, (const float4 *)proj, elem_off, elem_cnt,
-                                                      inst_grad, err, gr->opacity, gr->rgb, gr->mean3d, gr->cov3d,
-                                                      gr->mean2d, gr->conic);
+    long long NE = (long long)ct.n * N;
+    k_elem_grad_sum<<<(unsigned)((NE * 32 + 255) / 256), 256, 0, s>>>(NE, elem_off, elem_cnt, inst_grad, err, elem_grad);
+    k_project_backward<<<(N + 255) / 256, 256, 0, s>>>(ct, N, mean3d, cov3d, (const float4 *)proj, elem_grad, err,
+                                                      gr->opacity, gr->rgb, gr->mean3d, gr->cov3d, gr->mean2d,
+                                                      gr->conic);
 }
 
 }  // namespace gs

@@ -106,32 +106,6 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
     }
 }
 
-// Sum 16 per-lane values over the warp with 16 shuffles (reduce-scatter): on return
-// lane l holds the total of value index (l >> 1) & 15; lanes l and l ^ 1 agree.
-__device__ __forceinline__ float warp_reduce16(const float (&v)[16], int lane)
-{
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-    float a[8], b[4], c2[2];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        float send = b4 ? v[i] : v[i + 8], keep = b4 ? v[i + 8] : v[i];
-        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float send = b3 ? a[i] : a[i + 4], keep = b3 ? a[i + 4] : a[i];
-        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        float send = b2 ? b[i] : b[i + 2], keep = b2 ? b[i + 2] : b[i];
-        c2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    float d = (b1 ? c2[1] : c2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? c2[0] : c2[1], 2);
-    d += __shfl_xor_sync(0xffffffffu, d, 1);
-    return d;
-}
-
 template <int TW, int TH, int KM>
 __global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, const float4 *__restrict__ proj,
                                                      const uint32_t *__restrict__ inst_vals,
