@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
         int ch = lane + 32 * c;
 #pragma unroll
         for (int i = 0; i < VEC; ++i) { f[c][i] = 0.f; acc[c][i] = 0.f; }
-        if (ch < nch) Rw::load(feats, (size_t)g * nch + ch, f[c]);
+        if (ch < nch && m1 > m0) Rw::load(feats, (size_t)g * nch + ch, f[c]);   // unselected: zero row only
     }
     uint32_t m = m0;
     for (; m + U <= m1; m += U) {
@@ -293,39 +293,53 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
 }
 
 // Gaussians whose segment was cut into several pieces: one CTA per such Gaussian (from
-// the compact list), threads over float4 columns, rows summed in a fixed order with
-// four independent accumulators.
-__global__ void __launch_bounds__(128) k_fgrad_fixup(int D4, const uint32_t *__restrict__ n_multi_dev,
-                                                     const uint32_t *__restrict__ mlist,
-                                                     const uint32_t *__restrict__ multi,
-                                                     const uint32_t *__restrict__ multi_off,
-                                                     const uint32_t *__restrict__ order,
-                                                     const float4 *__restrict__ piece_rows, float4 *__restrict__ grad_f)
+// the compact list).  Its 1024 threads are 8 row groups x 128 float4 columns; each
+// group sums every 8th piece row with two accumulators, and the 8 group sums are
+// combined in shared memory in a fixed order -- deterministic, and a Gaussian selected
+// by most of the frame (thousands of piece rows) is summed 8 ways in parallel.
+constexpr int kFixCols = 128, kFixGroups = 8;
+__global__ void __launch_bounds__(kFixCols *kFixGroups) k_fgrad_fixup(int D4, const uint32_t *__restrict__ n_multi_dev,
+                                                                      const uint32_t *__restrict__ mlist,
+                                                                      const uint32_t *__restrict__ multi,
+                                                                      const uint32_t *__restrict__ multi_off,
+                                                                      const uint32_t *__restrict__ order,
+                                                                      const float4 *__restrict__ piece_rows,
+                                                                      float4 *__restrict__ grad_f)
 {
+    __shared__ float4 part[kFixGroups][kFixCols];
+    const int col = threadIdx.x % kFixCols, grp = threadIdx.x / kFixCols;
     const uint32_t n_multi = *n_multi_dev;
     for (uint32_t i = blockIdx.x; i < n_multi; i += gridDim.x) {
         const uint32_t r = mlist[i];
         const uint32_t n = multi[r], base = multi_off[r], g = order[r];
-        for (int c = threadIdx.x; c < D4; c += blockDim.x) {
-            float4 a[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) a[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            uint32_t k = 0;
-            for (; k + 4 <= n; k += 4) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    float4 v = __ldg(piece_rows + (size_t)(base + k + q) * D4 + c);
-                    a[q].x += v.x; a[q].y += v.y; a[q].z += v.z; a[q].w += v.w;
+        for (int c0 = 0; c0 < D4; c0 += kFixCols) {
+            const int c = c0 + col;
+            float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+            if (c < D4) {
+                uint32_t k = grp;
+                for (; k + kFixGroups < n; k += 2 * kFixGroups) {
+                    float4 v = __ldg(piece_rows + (size_t)(base + k) * D4 + c);
+                    float4 w = __ldg(piece_rows + (size_t)(base + k + kFixGroups) * D4 + c);
+                    a0.x += v.x; a0.y += v.y; a0.z += v.z; a0.w += v.w;
+                    a1.x += w.x; a1.y += w.y; a1.z += w.z; a1.w += w.w;
+                }
+                if (k < n) {
+                    float4 v = __ldg(piece_rows + (size_t)(base + k) * D4 + c);
+                    a0.x += v.x; a0.y += v.y; a0.z += v.z; a0.w += v.w;
                 }
             }
-            for (; k < n; ++k) {
-                float4 v = __ldg(piece_rows + (size_t)(base + k) * D4 + c);
-                a[0].x += v.x; a[0].y += v.y; a[0].z += v.z; a[0].w += v.w;
+            part[grp][col] = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+            __syncthreads();
+            if (grp == 0 && c < D4) {
+                float4 t = part[0][col];
+#pragma unroll
+                for (int q = 1; q < kFixGroups; ++q) {
+                    float4 v = part[q][col];
+                    t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+                }
+                grad_f[(size_t)g * D4 + c] = t;
             }
-            grad_f[(size_t)g * D4 + c] = make_float4((a[0].x + a[1].x) + (a[2].x + a[3].x),
-                                                     (a[0].y + a[1].y) + (a[2].y + a[3].y),
-                                                     (a[0].z + a[1].z) + (a[2].z + a[3].z),
-                                                     (a[0].w + a[1].w) + (a[2].w + a[3].w));
+            __syncthreads();
         }
     }
 }
@@ -401,8 +415,8 @@ bool launch_feature_grad(const WsLayout &L, int dtype, int N, const float *mean3
                   : fgrad_main<false>(cpl, blocks, s, L.K, nch, n_pieces, piece_rank, piece_off, pieces, multi_off,
                                       seg_start, seg_end, order, pv[pcur], wnorm, feats, dLdF, hbuf, grad_feat, rows);
     if (!ok) return false;
-    k_fgrad_fixup<<<148 * 4, 128, 0, s>>>(L.D / 4, n_multi, mlist, multi, multi_off, order, (const float4 *)rows,
-                                          (float4 *)grad_feat);
+    k_fgrad_fixup<<<148 * 2, kFixCols * kFixGroups, 0, s>>>(L.D / 4, n_multi, mlist, multi, multi_off, order,
+                                                            (const float4 *)rows, (float4 *)grad_feat);
     return true;
 }
 

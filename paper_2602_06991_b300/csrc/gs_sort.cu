@@ -54,28 +54,15 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_upsweep(const uint32_t *__r
     hist[(size_t)blockIdx.x * 256 + tid] = s;          // block-major: coalesced
 }
 
-// Offsets of a pass: hist[b][d] becomes the exclusive prefix of digit d over blocks
-// 0..b-1; hist[G][d] receives the exclusive prefix over digits of the digit totals.
-// One thread per digit, coalesced across threads, loads pipelined by unrolling.
-__global__ void __launch_bounds__(256) k_rs_scan(uint32_t *hist, int G)
+// Offsets of a pass, step 1: one CTA per digit d scans that digit's counts over the
+// G blocks (hist[b][d] becomes the exclusive prefix over blocks 0..b-1) and writes the
+// digit total to hist[G][d].  The downsweep adds the prefix of the digit totals.
+__global__ void __launch_bounds__(512) k_rs_scan(uint32_t *hist, int G)
 {
-    __shared__ uint32_t warp_sums[8];
-    const int d = threadIdx.x, lane = d & 31, warp = d >> 5;
-    uint32_t run = 0;
-    int b = 0;
-    for (; b + 8 <= G; b += 8) {
-        uint32_t v[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = hist[(size_t)(b + i) * 256 + d];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) { hist[(size_t)(b + i) * 256 + d] = run; run += v[i]; }
-    }
-    for (; b < G; ++b) {
-        uint32_t v = hist[(size_t)b * 256 + d];
-        hist[(size_t)b * 256 + d] = run;
-        run += v;
-    }
-    uint32_t inc = run;
+    __shared__ uint32_t warp_sums[16];
+    const int d = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    uint32_t v = t < G ? hist[(size_t)t * 256 + d] : 0u;
+    uint32_t inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
@@ -83,9 +70,14 @@ __global__ void __launch_bounds__(256) k_rs_scan(uint32_t *hist, int G)
     }
     if (lane == 31) warp_sums[warp] = inc;
     __syncthreads();
-    uint32_t base = inc - run;
-    for (int w = 0; w < warp; ++w) base += warp_sums[w];
-    hist[(size_t)G * 256 + d] = base;
+    uint32_t before = 0, total = 0;
+    for (int w = 0; w < 16; ++w) {
+        uint32_t x = warp_sums[w];
+        before += w < warp ? x : 0u;
+        total += x;
+    }
+    if (t < G) hist[(size_t)t * 256 + d] = inc - v + before;
+    if (t == 0) hist[(size_t)G * 256 + d] = total;
 }
 
 // Exclusive scan in place of len uint32 by one block of 1024 threads.
@@ -135,7 +127,22 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_downsweep(const uint32_t *_
     __shared__ uint32_t s_wcnt[W][257];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    s_base[tid] = hist[(size_t)blockIdx.x * 256 + tid] + hist[(size_t)gridDim.x * 256 + tid];
+    {
+        // digit base = exclusive prefix over digits of the digit totals
+        uint32_t tot = hist[(size_t)gridDim.x * 256 + tid];
+        uint32_t inc = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_tot[warp] = inc;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += s_tot[w];
+        s_base[tid] = hist[(size_t)blockIdx.x * 256 + tid] + inc - tot + before;
+        __syncthreads();
+    }
     long long n = sort_count(n_host, n_dev), t0, t1;
     block_tiles(n, t0, t1);
     for (long long t = t0; t < t1; ++t) {
@@ -199,7 +206,7 @@ int radix_sort_pairs(uint32_t *keys0, uint32_t *keys1, uint32_t *vals0, uint32_t
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
         k_rs_upsweep<<<G, kSortThreads, 0, s>>>(kb[cur], n_host, n_dev, shift, hist);
-        k_rs_scan<<<1, 256, 0, s>>>(hist, G);
+        k_rs_scan<<<256, 512, 0, s>>>(hist, G);
         k_rs_downsweep<<<G, kSortThreads, 0, s>>>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n_host, n_dev, shift, hist);
         cur ^= 1;
     }
