@@ -4,6 +4,8 @@
 
 #include <string.h>
 
+#include <algorithm>
+
 #ifndef GS_BUILT_SM
 #define GS_BUILT_SM 0
 #endif
@@ -81,10 +83,15 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     if (mcap < 4096) mcap = 4096;
     if (mcap > 0x7fffffffll) mcap = 0x7fffffffll;
     L.Mcap = mcap;
-    L.n_pairs = N + L.PK;
+    L.use_tiles = tile_grad_supported(cfg->feat_dtype, cfg->D, cfg->K, cfg->tile_w, cfg->tile_h);
+    // partial feature-gradient rows: one per (tile, selected Gaussian), itself one of the
+    // instances, so never more than Mcap; sized for 128 per tile or Mcap / 32.
+    L.rows_cap = L.use_tiles ? std::min(mcap, std::max((long long)ct.n_tiles * 128, mcap / 32)) : 0;
+    L.n_pairs = N + std::max(L.PK, L.rows_cap);
     if (L.NE > 0x7fffffffll || L.n_pairs > 0x7fffffffll) return false;
+    L.max_pieces_rows = N + (L.rows_cap + kPieceLen - 1) / kPieceLen + 1;
     L.max_pieces = N + (L.PK + kPieceLen - 1) / kPieceLen + 1;
-    L.max_multi_rows = 2 * ((L.PK + kPieceLen - 1) / kPieceLen) + 1;
+    L.max_multi_rows = 2 * ((std::max(L.PK, L.rows_cap) + kPieceLen - 1) / kPieceLen) + 1;
     L.inst_sorted = sorted_buffer(bits_for(L.n_tiles));
     L.pair_bits = bits_for((long long)N + 1);
     L.pair_sorted = sorted_buffer(L.pair_bits);
@@ -125,6 +132,12 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     L.piece_rank = take(u * L.max_pieces);
     L.piece_rows = take(sizeof(float) * (size_t)L.max_multi_rows * cfg->D);
     L.loss_part = 0;
+    if (L.use_tiles) {
+        L.tile_keys = take(8 * (size_t)ct.n_tiles * cfg->tile_w * cfg->tile_h * cfg->K);
+        L.tile_u = take(u * ct.n_tiles);
+        L.tile_rowbase = take(u * ct.n_tiles);
+        L.tile_rows = take(sizeof(float) * (size_t)L.rows_cap * cfg->D);
+    }
     L.total = off;
     return true;
 }
@@ -269,7 +282,8 @@ int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int
     cudaStream_t s = (cudaStream_t)stream;
     CamTable ct;
     make_camtable(cfg, cams, n_cams, ct);
-    if (!launch_feature_grad(L, cfg->feat_dtype, n_gauss, mean3d, topk_idx, topk_w, feats, dL_dF, grads->feat, ws, s))
+    if (!launch_feature_grad(ct, L, cfg->feat_dtype, n_gauss, mean3d, topk_idx, topk_w, feats, dL_dF, grads->feat, ws,
+                             s))
         return GS_ERR_UNSUPPORTED;
     if (!launch_walk_bwd(ct, L, cfg->K, n_gauss, proj, ws, rgb_out, depth_out, topk_idx, topk_w, dL_dC, dL_dD, s))
         return GS_ERR_UNSUPPORTED;

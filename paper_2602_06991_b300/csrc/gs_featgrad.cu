@@ -114,15 +114,31 @@ __global__ void k_pairs(int N, int K, long long PK, const int *__restrict__ topk
     }
 }
 
-__global__ void k_segments(int N, long long n_pairs, const uint32_t *__restrict__ keys,
+__global__ void k_segments(int N, long long n_host, const uint32_t *n_dev, const uint32_t *__restrict__ keys,
                            const uint32_t *__restrict__ vals, uint32_t *seg_start, uint32_t *seg_end)
 {
+    long long n_pairs = n_dev ? min((long long)*n_dev, n_host) : n_host;
     long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= n_pairs) return;
     uint32_t k = keys[m];
     if (k >= (uint32_t)N) return;
     if (vals[m] == kMarker) seg_start[k] = (uint32_t)(m + 1);
     if (m + 1 == n_pairs || keys[m + 1] != k) seg_end[k] = (uint32_t)(m + 1);
+}
+
+// Row mode: one marker entry per Gaussian id, then the pair count N + U_tot.
+__global__ void k_markers(int N, uint32_t *keys, uint32_t *vals)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) {
+        keys[i] = (uint32_t)i;
+        vals[i] = kMarker;
+    }
+}
+
+__global__ void k_pair_count(int N, const uint32_t *u_tot, uint32_t rows_cap, uint32_t *n_pairs)
+{
+    *n_pairs = (uint32_t)N + min(*u_tot, rows_cap);
 }
 
 __global__ void k_pieces(int N, const uint32_t *__restrict__ seg_start, const uint32_t *__restrict__ seg_end,
@@ -186,7 +202,7 @@ struct Row<true> {
 // Four pairs are in flight at a time: their dL/dF chunks are loaded together, then
 // accumulated, and their four dot products with the Gaussian's own row are reduced with
 // one reduce-scatter (6 shuffles for 4 dots).
-template <bool BF16, int CPL>
+template <bool BF16, int CPL, bool ROWS>
 __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32_t *__restrict__ n_pieces_dev,
                                                     const uint32_t *__restrict__ piece_rank,
                                                     const uint32_t *__restrict__ piece_off,
@@ -200,7 +216,9 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
                                                     const void *__restrict__ dLdF, float *__restrict__ hbuf,
                                                     float *__restrict__ grad_f, float *__restrict__ piece_rows)
 {
-    using Rw = Row<BF16>;
+    // ROWS: the pairs point at float32 partial rows (one per (tile, Gaussian)), the
+    // weight is 1 and no dot products are formed; ranks are Gaussian ids (order unused).
+    using Rw = Row<BF16 && !ROWS>;
     constexpr int VEC = Rw::VEC;
     constexpr int U = 4;
     const int lane = threadIdx.x & 31;
@@ -208,7 +226,7 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
     if (pc >= (long long)*n_pieces_dev) return;
     const uint32_t r = piece_rank[pc];
     const uint32_t j = (uint32_t)pc - piece_off[r];
-    const uint32_t g = order[r];
+    const uint32_t g = ROWS ? r : order[r];
     const uint32_t m0 = seg_start[r] + j * kPieceLen;
     const uint32_t m1 = min(m0 + kPieceLen, seg_end[r]);
     float f[CPL][VEC], acc[CPL][VEC];
@@ -217,7 +235,7 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
         int ch = lane + 32 * c;
 #pragma unroll
         for (int i = 0; i < VEC; ++i) { f[c][i] = 0.f; acc[c][i] = 0.f; }
-        if (ch < nch && m1 > m0) Rw::load(feats, (size_t)g * nch + ch, f[c]);   // unselected: zero row only
+        if (!ROWS && ch < nch && m1 > m0) Rw::load(feats, (size_t)g * nch + ch, f[c]);   // unselected: zero row only
     }
     uint32_t m = m0;
     for (; m + U <= m1; m += U) {
@@ -226,8 +244,8 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             sv[u] = pair_vals[m + u];
-            pv[u] = sv[u] / (uint32_t)K;
-            wp[u] = __ldg(wnorm + sv[u]);
+            pv[u] = ROWS ? sv[u] : sv[u] / (uint32_t)K;
+            wp[u] = ROWS ? 1.f : __ldg(wnorm + sv[u]);
             dot[u] = 0.f;
         }
 #pragma unroll
@@ -246,6 +264,7 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
                     }
             }
         }
+        if (ROWS) continue;
         // reduce-scatter of 4 dots: lane l ends with dot (l >> 3) & 3 (lanes 0, 8, 16, 24)
         const bool b4 = lane & 16, b3 = lane & 8;
         float a0 = (b4 ? dot[2] : dot[0]) + __shfl_xor_sync(0xffffffffu, b4 ? dot[0] : dot[2], 16);
@@ -258,8 +277,8 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
     }
     for (; m < m1; ++m) {
         const uint32_t sv = pair_vals[m];
-        const uint32_t pv = sv / (uint32_t)K;
-        const float wp = __ldg(wnorm + sv);
+        const uint32_t pv = ROWS ? sv : sv / (uint32_t)K;
+        const float wp = ROWS ? 1.f : __ldg(wnorm + sv);
         float dot = 0.f;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
@@ -274,6 +293,7 @@ __global__ void __launch_bounds__(256) k_fgrad_main(int K, int nch, const uint32
                 }
             }
         }
+        if (ROWS) continue;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
         if (lane == 0) hbuf[sv] = dot;
@@ -311,7 +331,7 @@ __global__ void __launch_bounds__(kFixCols *kFixGroups) k_fgrad_fixup(int D4, co
     const uint32_t n_multi = *n_multi_dev;
     for (uint32_t i = blockIdx.x; i < n_multi; i += gridDim.x) {
         const uint32_t r = mlist[i];
-        const uint32_t n = multi[r], base = multi_off[r], g = order[r];
+        const uint32_t n = multi[r], base = multi_off[r], g = order ? order[r] : r;
         for (int c0 = 0; c0 < D4; c0 += kFixCols) {
             const int c = c0 + col;
             float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
@@ -344,25 +364,78 @@ __global__ void __launch_bounds__(kFixCols *kFixGroups) k_fgrad_fixup(int D4, co
     }
 }
 
-template <bool BF16>
+template <bool BF16, bool ROWS>
 static bool fgrad_main(int cpl, unsigned blocks, cudaStream_t s, int K, int nch, const uint32_t *np,
                        const uint32_t *pr, const uint32_t *po, const uint32_t *pcs, const uint32_t *mo,
                        const uint32_t *ss, const uint32_t *se, const uint32_t *ord, const uint32_t *pv,
                        const float *wn, const void *feats, const void *dLdF, float *h, float *gf, float *rows)
 {
     switch (cpl) {
-    case 1: k_fgrad_main<BF16, 1><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
-    case 2: k_fgrad_main<BF16, 2><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
-    case 4: k_fgrad_main<BF16, 4><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
-    case 8: k_fgrad_main<BF16, 8><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
+    case 1: k_fgrad_main<BF16, 1, ROWS><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
+    case 2: k_fgrad_main<BF16, 2, ROWS><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
+    case 4: k_fgrad_main<BF16, 4, ROWS><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
+    case 8: k_fgrad_main<BF16, 8, ROWS><<<blocks, 256, 0, s>>>(K, nch, np, pr, po, pcs, mo, ss, se, ord, pv, wn, feats, dLdF, h, gf, rows); return true;
     }
     return false;
 }
 
-bool launch_feature_grad(const WsLayout &L, int dtype, int N, const float *mean3d, const int *topk_idx,
-                         const float *topk_w, const void *feats, const void *dLdF, float *grad_feat, void *ws,
-                         cudaStream_t s)
+static int cpl_for(int nch) { return nch <= 32 ? 1 : nch <= 64 ? 2 : nch <= 128 ? 4 : 8; }
+
+bool launch_tile_grad(const CamTable &ct, const WsLayout &L, int dtype, const int *topk_idx, const float *topk_w,
+                      const void *feats, const void *dLdF, void *ws, cudaStream_t s);
+bool tile_grad_supported(int dtype, int D, int K, int tw, int th);
+
+// Tile-major path: T1-T3 in gs_tilegrad.cu, then the per-Gaussian reduction of the
+// partial rows (row mode of the segmented reduction).
+static bool feature_grad_tiles(const CamTable &ct, const WsLayout &L, int dtype, int N, const int *topk_idx,
+                               const float *topk_w, const void *feats, const void *dLdF, float *grad_feat, void *ws,
+                               cudaStream_t s)
 {
+    uint32_t *hdr = ws_ptr<uint32_t>(ws, L.header);
+    uint32_t *n_pieces = hdr + 2, *n_multi = hdr + 3, *u_tot = hdr + 8, *n_pairs_dev = hdr + 9;
+    uint32_t *hist = ws_ptr<uint32_t>(ws, L.sort_hist);
+    uint32_t *aux = ws_ptr<uint32_t>(ws, L.scan_aux);
+    uint32_t *pk[2] = {ws_ptr<uint32_t>(ws, L.pair_keys[0]), ws_ptr<uint32_t>(ws, L.pair_keys[1])};
+    uint32_t *pv[2] = {ws_ptr<uint32_t>(ws, L.pair_vals[0]), ws_ptr<uint32_t>(ws, L.pair_vals[1])};
+    uint32_t *seg_start = ws_ptr<uint32_t>(ws, L.seg_start), *seg_end = ws_ptr<uint32_t>(ws, L.seg_end);
+    uint32_t *pieces = ws_ptr<uint32_t>(ws, L.pieces), *piece_off = ws_ptr<uint32_t>(ws, L.piece_off);
+    uint32_t *multi = ws_ptr<uint32_t>(ws, L.multi), *multi_off = ws_ptr<uint32_t>(ws, L.multi_off);
+    uint32_t *mflag = ws_ptr<uint32_t>(ws, L.mflag), *mlist = ws_ptr<uint32_t>(ws, L.mlist);
+    uint32_t *piece_rank = ws_ptr<uint32_t>(ws, L.piece_rank);
+    float *prow = ws_ptr<float>(ws, L.piece_rows);
+    float *trows = ws_ptr<float>(ws, L.tile_rows);
+    const unsigned nbN = (unsigned)((N + 255) / 256);
+
+    if (!launch_tile_grad(ct, L, dtype, topk_idx, topk_w, feats, dLdF, ws, s)) return false;
+    k_markers<<<nbN, 256, 0, s>>>(N, pk[0], pv[0]);
+    k_pair_count<<<1, 1, 0, s>>>(N, u_tot, (uint32_t)L.rows_cap, n_pairs_dev);
+    const long long n_host = N + L.rows_cap;
+    int pcur = radix_sort_pairs(pk[0], pk[1], pv[0], pv[1], n_host, n_pairs_dev, L.pair_bits, hist, s);
+    k_segments<<<(unsigned)((n_host + 255) / 256), 256, 0, s>>>(N, n_host, n_pairs_dev, pk[pcur], pv[pcur], seg_start,
+                                                                seg_end);
+    k_pieces<<<nbN, 256, 0, s>>>(N, seg_start, seg_end, pieces, multi);
+    exclusive_scan_u32(pieces, piece_off, N, n_pieces, aux, s);
+    exclusive_scan_u32(multi, multi_off, N, nullptr, aux, s);
+    k_multi_flags<<<nbN, 256, 0, s>>>(N, multi, mflag);
+    exclusive_scan_u32(mflag, mflag, N, n_multi, aux, s);
+    k_piece_rank<<<nbN, 256, 0, s>>>(N, pieces, piece_off, multi, mflag, piece_rank, mlist);
+    const int nch = L.D / 4;
+    unsigned blocks = (unsigned)((L.max_pieces_rows * 32 + 255) / 256);
+    if (!fgrad_main<false, true>(cpl_for(nch), blocks, s, L.K, nch, n_pieces, piece_rank, piece_off, pieces,
+                                 multi_off, seg_start, seg_end, nullptr, pv[pcur], nullptr, nullptr, trows, nullptr,
+                                 grad_feat, prow))
+        return false;
+    k_fgrad_fixup<<<148 * 2, kFixCols * kFixGroups, 0, s>>>(L.D / 4, n_multi, mlist, multi, multi_off, nullptr,
+                                                            (const float4 *)prow, (float4 *)grad_feat);
+    return true;
+}
+
+bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N, const float *mean3d,
+                         const int *topk_idx, const float *topk_w, const void *feats, const void *dLdF,
+                         float *grad_feat, void *ws, cudaStream_t s)
+{
+    if (L.use_tiles)
+        return feature_grad_tiles(ct, L, dtype, N, topk_idx, topk_w, feats, dLdF, grad_feat, ws, s);
     uint32_t *hdr = ws_ptr<uint32_t>(ws, L.header);
     uint32_t *n_pieces = hdr + 2;
     uint32_t *n_multi = hdr + 3;
@@ -396,7 +469,8 @@ bool launch_feature_grad(const WsLayout &L, int dtype, int N, const float *mean3
     k_pairs<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(N, L.K, L.PK, topk_idx, topk_w, grank, pk[0], pv[0],
                                                               wnorm);
     int pcur = radix_sort_pairs(pk[0], pk[1], pv[0], pv[1], n_pairs, nullptr, L.pair_bits, hist, s);
-    k_segments<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(N, n_pairs, pk[pcur], pv[pcur], seg_start, seg_end);
+    k_segments<<<(unsigned)((n_pairs + 255) / 256), 256, 0, s>>>(N, n_pairs, nullptr, pk[pcur], pv[pcur], seg_start,
+                                                                 seg_end);
     // 3. pieces, and the compact list of Gaussians cut into several pieces
     k_pieces<<<nbN, 256, 0, s>>>(N, seg_start, seg_end, pieces, multi);
     exclusive_scan_u32(pieces, piece_off, N, n_pieces, aux, s);
@@ -407,12 +481,12 @@ bool launch_feature_grad(const WsLayout &L, int dtype, int N, const float *mean3
     // 4. reduce
     const int vec = dtype == GS_BF16 ? 8 : 4;
     const int nch = L.D / vec;
-    const int cpl = nch <= 32 ? 1 : nch <= 64 ? 2 : nch <= 128 ? 4 : 8;
+    const int cpl = cpl_for(nch);
     unsigned blocks = (unsigned)((L.max_pieces * 32 + 255) / 256);
     bool ok = dtype == GS_BF16
-                  ? fgrad_main<true>(cpl, blocks, s, L.K, nch, n_pieces, piece_rank, piece_off, pieces, multi_off,
+                  ? fgrad_main<true, false>(cpl, blocks, s, L.K, nch, n_pieces, piece_rank, piece_off, pieces, multi_off,
                                      seg_start, seg_end, order, pv[pcur], wnorm, feats, dLdF, hbuf, grad_feat, rows)
-                  : fgrad_main<false>(cpl, blocks, s, L.K, nch, n_pieces, piece_rank, piece_off, pieces, multi_off,
+                  : fgrad_main<false, false>(cpl, blocks, s, L.K, nch, n_pieces, piece_rank, piece_off, pieces, multi_off,
                                       seg_start, seg_end, order, pv[pcur], wnorm, feats, dLdF, hbuf, grad_feat, rows);
     if (!ok) return false;
     k_fgrad_fixup<<<148 * 2, kFixCols * kFixGroups, 0, s>>>(L.D / 4, n_multi, mlist, multi, multi_off, order,

@@ -227,7 +227,10 @@ struct WsLayout {
     size_t mflag, mlist;       // N each: ranks with a multi-piece segment (flag scan, compact list)
     size_t piece_rank;         // max_pieces
     size_t piece_rows;         // max_multi_rows x D floats
-    size_t loss_part;          // P + kSortBlocks floats
+    size_t loss_part;          // unused (the loss takes caller scratch)
+    size_t tile_keys;          // n_tiles x B K uint64 sorted (Gaussian, slot) keys (tile-major feature gradient)
+    size_t tile_u, tile_rowbase; // n_tiles each
+    size_t tile_rows;          // rows_cap x D floats: partial feature-gradient rows per (tile, Gaussian)
     size_t total;
     int inst_sorted;           // buffer (0/1) holding the tile-sorted instances
     int pair_sorted;           // buffer (0/1) holding the sorted feature-gradient pairs
@@ -235,6 +238,8 @@ struct WsLayout {
     int pair_bits;
 
     long long NE, P, PK, Mcap, n_pairs, max_pieces, max_multi_rows;
+    long long rows_cap, max_pieces_rows;
+    bool use_tiles;
     int N, K, D, n_tiles, n_cams;
 };
 
@@ -273,9 +278,10 @@ bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const 
                      const float *dLdC, const float *dLdD, cudaStream_t s);
 bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, const float *w, const void *feats,
                   void *F, const int *err, cudaStream_t s);
-bool launch_feature_grad(const WsLayout &L, int dtype, int N, const float *mean3d, const int *topk_idx,
-                         const float *topk_w, const void *feats, const void *dLdF, float *grad_feat, void *ws,
-                         cudaStream_t s);
+bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N, const float *mean3d,
+                         const int *topk_idx, const float *topk_w, const void *feats, const void *dLdF,
+                         float *grad_feat, void *ws, cudaStream_t s);
+bool tile_grad_supported(int dtype, int D, int K, int tw, int th);
 bool launch_loss(int dtype, int D, long long n_pix, const void *F, const void *Fgt, const float *C, const float *Cgt,
                  const float *Dp, const float *Dgt, float wf, float wc, float wd, void *dLdF, float *dLdC,
                  float *dLdD, float *loss, float *part, cudaStream_t s);
