@@ -190,8 +190,10 @@ __global__ void __launch_bounds__(TW *TH) k_tile_accum(const __grid_constant__ C
     __shared__ uint32_t s_scan[NW];
     __shared__ int s_nu, s_nvalid;
     const int nslots = B * K;
-    unsigned char *stage = smem;
-    uint64_t *bars = (uint64_t *)(smem + (size_t)kStages * B * kChunkBytes);
+    // TMA destinations must be 128-byte aligned: align the base explicitly (the launch
+    // adds 1024 bytes of slack for this)
+    unsigned char *stage = (unsigned char *)(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(stage + (size_t)kStages * B * kChunkBytes);
     uint16_t *s_slot = (uint16_t *)(bars + 8);
     uint16_t *s_ustart = s_slot + nslots;
     uint32_t *s_uid = (uint32_t *)(((uintptr_t)(s_ustart + nslots + 1) + 15) & ~(uintptr_t)15);
