@@ -160,13 +160,15 @@ struct Chunk16<true> {      // 16 bytes = 8 bf16
     }
 };
 
-// Dynamic shared memory, in order: [kStages][B pixels][256 B] staged dL/dF,
-// kStages mbarriers, then per slot (B K): sorted slot (u16), run start (u16, + 1),
-// distinct id (u32), h (f32), renormalised weight indexed by slot (f32).
+// Dynamic shared memory, in order: [kStages][B pixels][256 B] staged dL/dF (1024-byte
+// aligned), kStages mbarriers, edge partials [B/16][2][256 B as float32 accumulators x2],
+// then per sorted position (B K): slot (u16), pixel (u16), run index (u16), weight (f32),
+// h (f32); per run: start (u16, + 1) and Gaussian id (u32).
 size_t tile_accum_smem(int B, int K)
 {
     size_t n = (size_t)B * K;
-    return (size_t)kStages * B * kChunkBytes + 64 + 2 * n + 2 * (n + 1) + 16 + 4 * n + 4 * n + 4 * n + 64;
+    size_t e = (size_t)(B / 16) * 2 * 128 * sizeof(float);
+    return 1024 + (size_t)kStages * B * kChunkBytes + 64 + e + 2 * n * 3 + 16 + 4 * n * 2 + 2 * (n + 1) + 16 + 4 * n + 64;
 }
 
 template <int TW, int TH, bool BF16>
@@ -182,23 +184,26 @@ __global__ void __launch_bounds__(TW *TH) k_tile_accum(const __grid_constant__ C
 {
     constexpr int B = TW * TH;
     constexpr int NW = B / 32;
+    constexpr int NH = B / 16;                        // half-warps
     using Ch = Chunk16<BF16>;
     constexpr int VEC = Ch::VEC;
     constexpr int ELEM = BF16 ? 2 : 4;
     constexpr int CE = kChunkBytes / ELEM;           // elements per staged chunk
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ unsigned char smem_raw[];
     __shared__ uint32_t s_scan[NW];
     __shared__ int s_nu, s_nvalid;
     const int nslots = B * K;
-    // TMA destinations must be 128-byte aligned: align the base explicitly (the launch
-    // adds 1024 bytes of slack for this)
-    unsigned char *stage = (unsigned char *)(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
+    // TMA destinations must be 128-byte aligned: align explicitly (the launch adds slack)
+    unsigned char *stage = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(stage + (size_t)kStages * B * kChunkBytes);
-    uint16_t *s_slot = (uint16_t *)(bars + 8);
-    uint16_t *s_ustart = s_slot + nslots;
+    float *s_edge = (float *)(bars + 8);                               // [NH][2][CE]
+    uint16_t *s_slot = (uint16_t *)(s_edge + NH * 2 * CE);
+    uint16_t *s_pl = s_slot + nslots;
+    uint16_t *s_run = s_pl + nslots;
+    float *s_wn = (float *)(((uintptr_t)(s_run + nslots) + 15) & ~(uintptr_t)15);
+    float *s_h = s_wn + nslots;
+    uint16_t *s_ustart = (uint16_t *)(s_h + nslots);
     uint32_t *s_uid = (uint32_t *)(((uintptr_t)(s_ustart + nslots + 1) + 15) & ~(uintptr_t)15);
-    float *s_h = (float *)(s_uid + nslots);
-    float *s_wn = s_h + nslots;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(TW *TH) k_tile_accum(const __grid_constant__ C
         if (tid == 0) atomicOr(err, kErrOverflow);
         return;
     }
-    // renormalised weights of this thread's pixel, indexed by slot (Eq. 3)
+    // renormalised weights of this thread's pixel, indexed by slot (Eq. 3); staged in s_h
     {
         const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
         if (px < cam.W && py < cam.H) {
@@ -221,10 +226,11 @@ __global__ void __launch_bounds__(TW *TH) k_tile_accum(const __grid_constant__ C
             float S = 0.f;
             for (int k = 0; k < K; ++k) S += topk_w[p * K + k];
             const float inv = S > 0.f ? 1.f / S : 0.f;
-            for (int k = 0; k < K; ++k) s_wn[tid * K + k] = topk_w[p * K + k] * inv;
+            for (int k = 0; k < K; ++k) s_h[tid * K + k] = topk_w[p * K + k] * inv;
         }
     }
-    // sorted slots; run starts of distinct Gaussians via a block scan over K-long runs
+    __syncthreads();
+    // sorted positions: slot, pixel, weight; run starts via a block scan over K-long runs
     {
         const unsigned long long *keys = tile_keys + (size_t)tile * nslots;
         uint32_t n_start = 0, n_valid = 0;
@@ -233,8 +239,10 @@ __global__ void __launch_bounds__(TW *TH) k_tile_accum(const __grid_constant__ C
             const int i = tid * K + j;
             const unsigned long long key = keys[i];
             const bool valid = key != kKeyInvalid;
-            s_slot[i] = (uint16_t)(key & 0xffffull);
-            s_h[i] = 0.f;
+            const int sl = (int)(key & 0xffffull);
+            s_slot[i] = (uint16_t)sl;
+            s_pl[i] = valid ? (uint16_t)(sl / K) : (uint16_t)0;
+            s_wn[i] = valid ? s_h[sl] : 0.f;
             n_valid += valid;
             n_start += valid && (i == 0 || (prev >> 16) != (key >> 16));
             prev = key;
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(TW *TH) k_tile_accum(const __grid_constant__ C
             if (lane >= o) inc += y;
         }
         if (lane == 31) s_scan[warp] = inc;
-        __syncthreads();
+        __syncthreads();                                  // also: every s_h weight has been read
         uint32_t before = inc - packed;
         for (int w = 0; w < warp; ++w) before += s_scan[w];
         if (tid == B - 1) {
@@ -253,16 +261,18 @@ __global__ void __launch_bounds__(TW *TH) k_tile_accum(const __grid_constant__ C
             s_nu = (int)(tot >> 16);
             s_nvalid = (int)(tot & 0xffffu);
         }
-        uint32_t u = before >> 16;
+        int u = (int)(before >> 16) - 1;
         prev = tid > 0 ? keys[tid * K - 1] : kKeyInvalid;
         for (int j = 0; j < K; ++j) {
             const int i = tid * K + j;
             const unsigned long long key = keys[i];
             if (key != kKeyInvalid && (i == 0 || (prev >> 16) != (key >> 16))) {
+                ++u;
                 s_ustart[u] = (uint16_t)i;
                 s_uid[u] = (uint32_t)(key >> 16);
-                ++u;
             }
+            s_run[i] = (uint16_t)(u < 0 ? 0 : u);
+            s_h[i] = 0.f;
             prev = key;
         }
     }
@@ -271,8 +281,8 @@ __global__ void __launch_bounds__(TW *TH) k_tile_accum(const __grid_constant__ C
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const int nu = s_nu;
-    if (tid == 0) s_ustart[nu] = (uint16_t)s_nvalid;
+    const int nu = s_nu, nvalid = s_nvalid;
+    if (tid == 0) s_ustart[nu] = (uint16_t)nvalid;
     const int n_chunks = (D * ELEM) / kChunkBytes;   // host guarantees an exact multiple
     const long long p_row0 = cam.pix_off + (long long)(ty * TH) * cam.W + tx * TW;
 
@@ -289,7 +299,10 @@ __global__ void __launch_bounds__(TW *TH) k_tile_accum(const __grid_constant__ C
         if (n_chunks > 1) issue(1);
     }
     __syncthreads();
-    const int half = lane >> 4, hl = lane & 15;
+    // balanced split: half-warp hw owns sorted positions [a, b)
+    const int half = lane >> 4, hl = lane & 15, hw = warp * 2 + half;
+    const int R = (nvalid + NH - 1) / NH;
+    const int a = min(hw * R, nvalid), b = min(a + R, nvalid);
     for (int ch = 0; ch < n_chunks; ++ch) {
         const int s = ch % kStages;
         const bool ok = mbar_wait(&bars[s], (uint32_t)((ch / kStages) & 1));
@@ -302,71 +315,95 @@ __global__ void __launch_bounds__(TW *TH) k_tile_accum(const __grid_constant__ C
         }
         const unsigned char *buf = stage + (size_t)s * B * kChunkBytes;
         const int colv = ch * CE + hl * VEC;             // first element of this lane's 16 B
-        for (int u0 = warp * 2; u0 < nu; u0 += 2 * NW) {
-            const int u = u0 + half;
-            const bool live = u < nu;
-            const int i0 = live ? s_ustart[u] : 0, i1 = live ? s_ustart[u + 1] : 0;
-            float f[VEC], acc[VEC];
+        float acc[VEC], f[VEC];
+        int cur = -1, seg0 = a;
+        auto flush = [&](int end) {
+            // segment [seg0, end) of run cur: whole run -> its partial row; cut -> edge buffer
+            const bool cutL = seg0 == a && a > s_ustart[cur];
+            const bool cutR = end == b && b < s_ustart[cur + 1];
+            float *dst = !cutL && !cutR ? rows + (size_t)(rb + cur) * D + colv
+                                        : s_edge + ((size_t)hw * 2 + (cutL ? 0 : 1)) * CE + hl * VEC;
+            float4 *d4 = (float4 *)dst;
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) { f[v] = 0.f; acc[v] = 0.f; }
-            if (live) {
-                const uint4 fv = __ldg((const uint4 *)((const char *)feats + ((size_t)s_uid[u] * D + colv) * ELEM));
-                Ch::cvt(fv, f);
-            }
-            const int n_here = i1 - i0;
-            const int n_max = max(n_here, __shfl_xor_sync(0xffffffffu, n_here, 16));
-            for (int j0 = 0; j0 < n_max; j0 += 8) {
-                float dot[8];
+            for (int v = 0; v < VEC / 4; ++v)
+                d4[v] = make_float4(acc[4 * v], acc[4 * v + 1], acc[4 * v + 2], acc[4 * v + 3]);
+        };
+        for (int j0 = 0; j0 < R; j0 += 8) {
+            float dot[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    dot[q] = 0.f;
-                    if (j0 + q < n_here) {
-                        const int sl = s_slot[i0 + j0 + q];
-                        const int pl = sl / K;
-                        const float wp = s_wn[sl];
-                        const uint4 xv = *(const uint4 *)(buf + (size_t)pl * kChunkBytes + hl * 16);
-                        float x[VEC];
-                        Ch::cvt(xv, x);
+            for (int q = 0; q < 8; ++q) {
+                dot[q] = 0.f;
+                const int i = a + j0 + q;
+                if (i < b) {
+                    const int run = s_run[i];
+                    if (run != cur) {
+                        if (cur >= 0) flush(i);
+                        cur = run;
+                        seg0 = i;
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            acc[v] = fmaf(wp, x[v], acc[v]);
-                            dot[q] = fmaf(x[v], f[v], dot[q]);
-                        }
+                        for (int v = 0; v < VEC; ++v) acc[v] = 0.f;
+                        const uint4 fv = __ldg((const uint4 *)((const char *)feats + ((size_t)s_uid[run] * D + colv) * ELEM));
+                        Ch::cvt(fv, f);
+                    }
+                    const float wp = s_wn[i];
+                    const uint4 xv = *(const uint4 *)(buf + (size_t)s_pl[i] * kChunkBytes + hl * 16);
+                    float x[VEC];
+                    Ch::cvt(xv, x);
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) {
+                        acc[v] = fmaf(wp, x[v], acc[v]);
+                        dot[q] = fmaf(x[v], f[v], dot[q]);
                     }
                 }
-                // reduce-scatter of 8 dots over the 16 lanes of this half-warp:
-                // lane hl ends with dot (hl >> 1) & 7 (lanes hl and hl ^ 1 agree)
-                const bool b3 = hl & 8, b2 = hl & 4, b1 = hl & 2;
-                float a[4], b[2];
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    a[q] = (b3 ? dot[q + 4] : dot[q]) + __shfl_xor_sync(0xffffffffu, b3 ? dot[q] : dot[q + 4], 8);
-#pragma unroll
-                for (int q = 0; q < 2; ++q)
-                    b[q] = (b2 ? a[q + 2] : a[q]) + __shfl_xor_sync(0xffffffffu, b2 ? a[q] : a[q + 2], 4);
-                float d = (b1 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, b1 ? b[0] : b[1], 2);
-                d += __shfl_xor_sync(0xffffffffu, d, 1);
-                const int q = (hl >> 1) & 7;
-                if (!(hl & 1) && j0 + q < n_here) s_h[i0 + j0 + q] += d;
             }
-            if (live) {
-                float4 *d4 = (float4 *)(rows + (size_t)(rb + u) * D + colv);
+            // reduce-scatter of 8 dots over the 16 lanes of this half-warp:
+            // lane hl ends with dot (hl >> 1) & 7 (lanes hl and hl ^ 1 agree)
+            const bool b3 = hl & 8, b2 = hl & 4, b1 = hl & 2;
+            float ra[4], rbv[2];
 #pragma unroll
-                for (int v = 0; v < VEC / 4; ++v)
-                    d4[v] = make_float4(acc[4 * v], acc[4 * v + 1], acc[4 * v + 2], acc[4 * v + 3]);
+            for (int q = 0; q < 4; ++q)
+                ra[q] = (b3 ? dot[q + 4] : dot[q]) + __shfl_xor_sync(0xffffffffu, b3 ? dot[q] : dot[q + 4], 8);
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                rbv[q] = (b2 ? ra[q + 2] : ra[q]) + __shfl_xor_sync(0xffffffffu, b2 ? ra[q] : ra[q + 2], 4);
+            float d = (b1 ? rbv[1] : rbv[0]) + __shfl_xor_sync(0xffffffffu, b1 ? rbv[0] : rbv[1], 2);
+            d += __shfl_xor_sync(0xffffffffu, d, 1);
+            const int q = (hl >> 1) & 7;
+            if (!(hl & 1) && a + j0 + q < b) s_h[a + j0 + q] += d;
+        }
+        if (cur >= 0) flush(b);
+        __syncthreads();                                  // edges written; stage consumed
+        // the half-warp where a cut run starts adds the pieces of the following half-warps
+        if (b > a) {
+            const int last = s_run[b - 1];
+            const bool cutR = b < s_ustart[last + 1];
+            const bool startsHere = s_ustart[last] >= a;
+            if (cutR && startsHere) {
+                const int h_end = (s_ustart[last + 1] - 1) / R;
+                float t[VEC];
+                const float *e = s_edge + ((size_t)hw * 2 + 1) * CE + hl * VEC;
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) t[v] = e[v];
+                for (int h = hw + 1; h <= h_end; ++h) {
+                    const float *e2 = s_edge + ((size_t)h * 2 + 0) * CE + hl * VEC;
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) t[v] += e2[v];
+                }
+                float4 *d4 = (float4 *)(rows + (size_t)(rb + last) * D + colv);
+#pragma unroll
+                for (int v = 0; v < VEC / 4; ++v) d4[v] = make_float4(t[4 * v], t[4 * v + 1], t[4 * v + 2], t[4 * v + 3]);
             }
         }
-        __syncthreads();                                  // every thread is done with this stage
+        __syncthreads();                                  // edges read before the next chunk
         if (tid == 0 && ch + kStages < n_chunks) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             issue(ch + kStages);
         }
     }
     // h per slot, and the (Gaussian, partial row) pairs of the per-Gaussian reduction
-    const int nvalid = s_nvalid;
     for (int i = tid; i < nvalid; i += B) {
         const int sl = s_slot[i];
-        const int pl = sl / K, k = sl - pl * K;
+        const int pl = s_pl[i], k = sl - pl * K;
         const long long p = cam.pix_off + (long long)(ty * TH + pl / TW) * cam.W + tx * TW + pl % TW;
         hbuf[p * K + k] = s_h[i];
     }
@@ -403,8 +440,7 @@ int tile_sort_len(int slots)
 bool tile_grad_supported(int dtype, int D, int K, int tw, int th)
 {
     const int elem = dtype == GS_BF16 ? 2 : 4;
-    return (D * elem) % kChunkBytes == 0 && tw * th * K <= 65535 &&
-           tile_accum_smem(tw * th, K) + 1024 <= 227 * 1024;
+    return (D * elem) % kChunkBytes == 0 && tw * th * K <= 65535 && tile_accum_smem(tw * th, K) <= 227 * 1024;
 }
 
 template <int TW, int TH>
@@ -427,7 +463,7 @@ static bool tile_launch(const CamTable &ct, const WsLayout &L, int dtype, const 
     cudaFuncSetAttribute(k_tile_slots<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     k_tile_slots<TW, TH><<<ct.n_tiles, B, sm1, s>>>(ct, L.K, nsort, topk_idx, err, keys, tile_u);
     exclusive_scan_u32(tile_u, row_base, ct.n_tiles, hdr + 8, aux, s);
-    const size_t sm3 = tile_accum_smem(B, L.K) + 1024;
+    const size_t sm3 = tile_accum_smem(B, L.K);
     if (dtype == GS_BF16) {
         cudaFuncSetAttribute(k_tile_accum<TW, TH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
         k_tile_accum<TW, TH, true><<<ct.n_tiles, B, sm3, s>>>(map, ct, L.K, L.D, topk_w, keys, row_base, tile_u,
