@@ -150,6 +150,8 @@ __global__ void __launch_bounds__(kAccNT, 1) k_tile_accum(CamTable ct, int K, in
     constexpr int B = TW * TH;
     using Rw = Row16<BF16>;
     constexpr int VEC = Rw::VEC;
+    // slots whose rows are in flight together: 32 registers of row data per lane
+    constexpr int DEPTH = CPL * VEC >= 32 ? 1 : 32 / (CPL * VEC);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t s_scan[kAccNW];
     __shared__ int s_nu, s_nvalid;
@@ -267,38 +269,50 @@ __global__ void __launch_bounds__(kAccNT, 1) k_tile_accum(CamTable ct, int K, in
     for (int j0 = 0; j0 < R; j0 += 8) {
         float dot[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            dot[q] = 0.f;
-            const int i = a + j0 + q;
-            if (i < b) {
-                const int run = s_run[i];
-                if (run != cur) {
-                    if (cur >= 0) flush(i);
-                    cur = run;
-                    seg0 = i;
-                    const uint32_t id = s_uid[run];
+        for (int h4 = 0; h4 < 8; h4 += DEPTH) {
+            // issue the row loads of DEPTH slots before any of their arithmetic
+            float x[DEPTH][CPL][VEC];
 #pragma unroll
-                    for (int cc = 0; cc < CPL; ++cc) {
-                        const int ch = lane + 32 * cc;
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) { acc[cc][v] = 0.f; f[cc][v] = 0.f; }
-                        if (ch < nch) Rw::load(feats, (size_t)id * nch + ch, f[cc]);
-                    }
-                }
-                const float wp = s_wn[i];
-                const long long p = pixel_of(s_pl[i]);
+            for (int q = 0; q < DEPTH; ++q) {
+                const int i = a + j0 + h4 + q;
+                const long long p = i < b ? pixel_of(s_pl[i]) : 0;
 #pragma unroll
                 for (int cc = 0; cc < CPL; ++cc) {
                     const int ch = lane + 32 * cc;
-                    if (ch < nch) {
-                        float x[VEC];
-                        Rw::load(dLdF, (size_t)p * nch + ch, x);
+                    if (i < b && ch < nch) Rw::load(dLdF, (size_t)p * nch + ch, x[q][cc]);
+                    else {
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            acc[cc][v] = fmaf(wp, x[v], acc[cc][v]);
-                            dot[q] = fmaf(x[v], f[cc][v], dot[q]);
+                        for (int v = 0; v < VEC; ++v) x[q][cc][v] = 0.f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < DEPTH; ++q) {
+                const int i = a + j0 + h4 + q;
+                dot[h4 + q] = 0.f;
+                if (i < b) {
+                    const int run = s_run[i];
+                    if (run != cur) {
+                        if (cur >= 0) flush(i);
+                        cur = run;
+                        seg0 = i;
+                        const uint32_t id = s_uid[run];
+#pragma unroll
+                        for (int cc = 0; cc < CPL; ++cc) {
+                            const int ch = lane + 32 * cc;
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) { acc[cc][v] = 0.f; f[cc][v] = 0.f; }
+                            if (ch < nch) Rw::load(feats, (size_t)id * nch + ch, f[cc]);
                         }
                     }
+                    const float wp = s_wn[i];
+#pragma unroll
+                    for (int cc = 0; cc < CPL; ++cc)
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) {
+                            acc[cc][v] = fmaf(wp, x[q][cc][v], acc[cc][v]);
+                            dot[h4 + q] = fmaf(x[q][cc][v], f[cc][v], dot[h4 + q]);
+                        }
                 }
             }
         }
@@ -388,11 +402,12 @@ static void accum_launch(int cpl, unsigned grid, size_t sm, cudaStream_t s, cons
                          const void *feats, const void *dLdF, float *rows, uint32_t *pk, uint32_t *pv, float *hbuf,
                          int *err)
 {
+    // (D <= 1024 caps bf16 rows at 4 chunks per lane; float32 rows at 8)
     switch (cpl) {
     case 1: accum_one<TW, TH, BF16, 1>(grid, sm, s, ct, L, tw, keys, rbase, tu, feats, dLdF, rows, pk, pv, hbuf, err); break;
     case 2: accum_one<TW, TH, BF16, 2>(grid, sm, s, ct, L, tw, keys, rbase, tu, feats, dLdF, rows, pk, pv, hbuf, err); break;
     case 4: accum_one<TW, TH, BF16, 4>(grid, sm, s, ct, L, tw, keys, rbase, tu, feats, dLdF, rows, pk, pv, hbuf, err); break;
-    default: accum_one<TW, TH, BF16, 8>(grid, sm, s, ct, L, tw, keys, rbase, tu, feats, dLdF, rows, pk, pv, hbuf, err); break;
+    default: accum_one<TW, TH, BF16, (BF16 ? 4 : 8)>(grid, sm, s, ct, L, tw, keys, rbase, tu, feats, dLdF, rows, pk, pv, hbuf, err); break;
     }
 }
 
