@@ -22,35 +22,6 @@
 
 namespace gs {
 
-// Thread -> pixel: each warp owns a compact 8 x 4 pixel block of the tile, so that a
-// warp can reject a staged Gaussian whose footprint box misses its block with one
-// uniform test (the box is conservative for the per-pixel test, so the rejected
-// Gaussian would fail q <= 9 or alpha >= 1/255 at every pixel of the block).
-template <int TW, int TH>
-__device__ __forceinline__ void warp_block_pixel(int tid, int &lx, int &ly, int &bx0, int &by0)
-{
-    const int lane = tid & 31, warp = tid >> 5;
-    constexpr int WX = TW / 8;
-    bx0 = (warp % WX) * 8;
-    by0 = (warp / WX) * 4;
-    lx = bx0 + (lane & 7);
-    ly = by0 + (lane >> 3);
-}
-
-// Footprint box of a staged Gaussian in pixel-centre coordinates: (x0, x1, y0, y1).
-__device__ __forceinline__ float4 footprint_box(const float4 r0, const float4 r3)
-{
-    float ex, ey;
-    unpack_extent(r3.w, ex, ey);
-    return make_float4(r0.x - ex, r0.x + ex, r0.y - ey, r0.y + ey);
-}
-
-__device__ __forceinline__ bool box_misses(const float4 bb, float bx0f, float by0f)
-{
-    // pixel centres of the block: [bx0 + 0.5, bx0 + 7.5] x [by0 + 0.5, by0 + 3.5]
-    return bb.y < bx0f + 0.5f || bb.x > bx0f + 7.5f || bb.w < by0f + 0.5f || bb.z > by0f + 3.5f;
-}
-
 template <int TW, int TH, int KM>
 __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, const float4 *__restrict__ proj,
                                                      const uint32_t *__restrict__ inst_vals,
@@ -61,7 +32,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
                                                      int *__restrict__ idx_out, float *__restrict__ w_out)
 {
     constexpr int B = TW * TH;
-    __shared__ float4 s_r0[B], s_r1[B], s_r2[B], s_bb[B];
+    __shared__ float4 s_r0[B], s_r1[B], s_r2[B];
     __shared__ int s_g[B];
     const int tid = threadIdx.x;
     const int tile = blockIdx.x;
@@ -69,10 +40,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
     const CamDev &cam = ct.c[c];
     const int lt = tile - cam.tile_off;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    int lx, ly, bx0, by0;
-    warp_block_pixel<TW, TH>(tid, lx, ly, bx0, by0);
-    const int px = tx * TW + lx, py = ty * TH + ly;
-    const float bx0f = (float)(tx * TW + bx0), by0f = (float)(ty * TH + by0);
+    const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
     const bool inside = px < cam.W && py < cam.H;
     int2 rg = ranges[tile];
     if (*err) rg.y = rg.x;
@@ -89,17 +57,14 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
         if (m < rg.y) {
             uint32_t e = inst_elem[inst_vals[m]];
             const float4 *r = proj + 4 * (size_t)e;
-            const float4 r0 = r[0];
-            s_r0[tid] = r0;
+            s_r0[tid] = r[0];
             s_r1[tid] = r[1];
             s_r2[tid] = r[2];
-            s_bb[tid] = footprint_box(r0, r[3]);
             s_g[tid] = (int)e - cN;
         }
         __syncthreads();
         const int cnt = min(B, rg.y - b0);
         for (int j = 0; j < cnt && !done; ++j) {
-            if (box_misses(s_bb[j], bx0f, by0f)) continue;
             float dx, dy;
             const float4 r1 = s_r1[j];
             float q = eval_q(pxf, pyf, s_r0[j], r1, dx, dy);
@@ -154,7 +119,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, 
     constexpr int B = TW * TH;
     constexpr int NW = B / 32;
     constexpr int BB = 64;                       // Gaussians per staged batch
-    __shared__ float4 s_r0[BB], s_r1[BB], s_r2[BB], s_r3[BB], s_bb[BB];
+    __shared__ float4 s_r0[BB], s_r1[BB], s_r2[BB], s_r3[BB];
     __shared__ int s_g[BB];
     __shared__ uint32_t s_o[BB];
     __shared__ float s_red[NW][BB][kGradVals];
@@ -164,10 +129,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, 
     const CamDev &cam = ct.c[c];
     const int lt = tile - cam.tile_off;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    int lx, ly, bx0, by0;
-    warp_block_pixel<TW, TH>(tid, lx, ly, bx0, by0);
-    const int px = tx * TW + lx, py = ty * TH + ly;
-    const float bx0f = (float)(tx * TW + bx0), by0f = (float)(ty * TH + by0);
+    const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
     const bool inside = px < cam.W && py < cam.H;
     int2 rg = ranges[tile];
     if (*err) rg.y = rg.x;
@@ -220,22 +182,16 @@ __global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, 
             uint32_t o = inst_vals[b0 + tid];
             uint32_t e = inst_elem[o];
             const float4 *r = proj + 4 * (size_t)e;
-            const float4 r0 = r[0], r3 = r[3];
-            s_r0[tid] = r0;
+            s_r0[tid] = r[0];
             s_r1[tid] = r[1];
             s_r2[tid] = r[2];
-            s_r3[tid] = r3;
-            s_bb[tid] = footprint_box(r0, r3);
+            s_r3[tid] = r[3];
             s_g[tid] = (int)e - cN;
             s_o[tid] = o;
         }
         __syncthreads();
         const int cnt = min(BB, rg.y - b0);
         for (int j = 0; j < cnt; ++j) {
-            if (box_misses(s_bb[j], bx0f, by0f)) {      // warp-uniform: nothing to reduce
-                if (lane < kGradVals) s_red[warp][j][lane] = 0.f;
-                continue;
-            }
             float v[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = 0.f;
