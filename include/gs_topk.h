@@ -165,6 +165,18 @@ int gs_loss_cos_l1(const gs_config *cfg, int64_t n_pix, const void *F, const voi
                    void *dL_dF, float *dL_dC, float *dL_dD, float *loss,
                    void *scratch, size_t scratch_bytes, void *stream);
 
+/* Training form of a4 + loss in one pass (same results as gs_feature_blend followed
+ * by gs_loss_cos_l1 on the same inputs, without reading F back): pixels are processed
+ * in screen-tile order, so needs the cameras and the workspace of the render (read
+ * only: its error word).  Outputs F_out (P x D) and the loss gradients as
+ * gs_loss_cos_l1; scratch of gs_loss_scratch_size(P) bytes. */
+int gs_feature_blend_loss(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                          const int32_t *topk_idx, const float *topk_w, const void *feats, const void *F_gt,
+                          const float *rgb, const float *rgb_gt, const float *depth, const float *depth_gt,
+                          float w_feat, float w_rgb, float w_depth, void *F_out, void *dL_dF, float *dL_dC,
+                          float *dL_dD, float *loss, void *ws, size_t ws_bytes, void *scratch, size_t scratch_bytes,
+                          void *stream);
+
 /* Same loss as gs_loss_cos_l1, for callers that cannot allocate device memory (code in
  * a real-time loop where cudaMalloc may stall the device, a plug-in inside a host
  * framework that owns all device memory, a component handed only its buffers).  The

@@ -66,6 +66,10 @@ PROTOTYPES = {
     "gs_loss_cos_l1": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.c_int64, vp, vp, vp, vp, vp, vp,
                                       ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, vp, vp, vp, vp,
                                       ctypes.c_size_t, vp]),
+    "gs_feature_blend_loss": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.POINTER(GsCamera), ctypes.c_int32,
+                                             ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_float,
+                                             ctypes.c_float, ctypes.c_float, vp, vp, vp, vp, vp, vp, ctypes.c_size_t,
+                                             vp, ctypes.c_size_t, vp]),
     "gs_loss_cos_l1_noalloc": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.c_int64, vp, vp, vp, vp, vp, vp,
                                               ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, vp, vp, vp, vp]),
     "gs_sync_status": (ctypes.c_int, [vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int64)]),

@@ -315,6 +315,32 @@ int gs_loss_cos_l1(const gs_config *cfg, int64_t n_pix, const void *F, const voi
     return launch_status();
 }
 
+int gs_feature_blend_loss(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                          const int32_t *topk_idx, const float *topk_w, const void *feats, const void *F_gt,
+                          const float *rgb, const float *rgb_gt, const float *depth, const float *depth_gt,
+                          float w_feat, float w_rgb, float w_depth, void *F_out, void *dL_dF, float *dL_dC,
+                          float *dL_dD, float *loss, void *ws, size_t ws_bytes, void *scratch, size_t scratch_bytes,
+                          void *stream)
+{
+    WsLayout L;
+    if (!make_layout(cfg, cams, n_cams, n_gauss, L)) return GS_ERR_ARG;
+    if (!topk_idx || !topk_w || !F_gt || !rgb || !rgb_gt || !depth || !depth_gt || !F_out || !dL_dF || !dL_dC ||
+        !dL_dD || !loss || (n_gauss > 0 && !feats))
+        return GS_ERR_ARG;
+    if (((uintptr_t)feats & 15) || ((uintptr_t)F_gt & 15) || ((uintptr_t)F_out & 15) || ((uintptr_t)dL_dF & 15))
+        return GS_ERR_ARG;
+    int st = ws_check(L, ws, ws_bytes);
+    if (st) return st;
+    if (!scratch || ((uintptr_t)scratch & 15) || scratch_bytes < gs_loss_scratch_size(L.P)) return GS_ERR_WORKSPACE;
+    CamTable ct;
+    make_camtable(cfg, cams, n_cams, ct);
+    if (!launch_blend_loss(ct, cfg->feat_dtype, cfg->K, cfg->D, L.P, topk_idx, topk_w, feats, F_gt, rgb, rgb_gt, depth,
+                           depth_gt, w_feat, w_rgb, w_depth, F_out, dL_dF, dL_dC, dL_dD, loss, (float *)scratch,
+                           ws_ptr<int>(ws, L.header), (cudaStream_t)stream))
+        return GS_ERR_UNSUPPORTED;
+    return launch_status();
+}
+
 int gs_sync_status(const void *ws, size_t ws_bytes, void *stream, int64_t *n_instances)
 {
     if (!ws || ws_bytes < 256) return GS_ERR_WORKSPACE;

@@ -282,6 +282,10 @@ bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N
                          const int *topk_idx, const float *topk_w, const void *feats, const void *dLdF,
                          float *grad_feat, void *ws, cudaStream_t s);
 bool tile_grad_supported(int dtype, int D, int K, int tw, int th);
+bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_pix, const int *idx, const float *w,
+                       const void *feats, const void *Fgt, const float *C, const float *Cgt, const float *Dp,
+                       const float *Dgt, float wf, float wc, float wd, void *F, void *dLdF, float *dLdC, float *dLdD,
+                       float *loss, float *part, const int *err, cudaStream_t s);
 bool launch_loss(int dtype, int D, long long n_pix, const void *F, const void *Fgt, const float *C, const float *Cgt,
                  const float *Dp, const float *Dgt, float wf, float wc, float wd, void *dLdF, float *dLdC,
                  float *dLdD, float *loss, float *part, cudaStream_t s);

@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, 
     __shared__ int s_g[BB];
     __shared__ uint32_t s_o[BB];
     __shared__ float s_red[NW][BB][kGradVals];
+    __shared__ int s_jend[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
     const int c = cam_of_tile(ct, tile);
@@ -191,7 +192,14 @@ __global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, 
         }
         __syncthreads();
         const int cnt = min(BB, rg.y - b0);
+        // a warp whose pixels have all stopped leaves the batch; the per-tile sum below
+        // counts its entries only up to that point
+        int j_end = cnt;
         for (int j = 0; j < cnt; ++j) {
+            if (__all_sync(0xffffffffu, done)) {
+                j_end = j;
+                break;
+            }
             float v[16];
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = 0.f;
@@ -243,12 +251,13 @@ __global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, 
                 s_red[warp][j][lane] = 0.f;
             }
         }
+        if (lane == 0) s_jend[warp] = j_end;
         __syncthreads();
         for (int i = tid; i < cnt * kGradVals; i += B) {
             int j = i / kGradVals, vi = i - j * kGradVals;
             float s = 0.f;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) s += s_red[w][j][vi];
+            for (int w = 0; w < NW; ++w) s += j < s_jend[w] ? s_red[w][j][vi] : 0.f;
             inst_grad[(size_t)kGradVals * s_o[j] + vi] = s;
         }
     }

@@ -125,6 +125,52 @@ class TopKRenderer:
         A.check(L.gs_feature_blend(cfg, self.P, N, _p(o["topk_idx"]), _p(o["topk_w"]), _p(feats), _p(o["F"]), s),
                 "gs_feature_blend")
 
+    def _select_into(self, N, mean3d, cov3d, opacity, rgb, o):
+        """a1-a3 only (projection, binning, Top-K walk)."""
+        L, cfg, s = self.lib, ctypes.byref(self.cfg), self._stream()
+        ws, wsb = _p(self.ws), self.ws.numel()
+        A.check(L.gs_preprocess(cfg, self.cams, self.n_cams, N, _p(mean3d), _p(cov3d), _p(opacity), _p(rgb),
+                                _p(o["proj"]), ws, wsb, s), "gs_preprocess")
+        A.check(L.gs_bin_sort(cfg, self.cams, self.n_cams, N, _p(o["proj"]), ws, wsb, s), "gs_bin_sort")
+        A.check(L.gs_topk_select(cfg, self.cams, self.n_cams, N, _p(o["proj"]), ws, wsb, _p(o["rgb"]),
+                                 _p(o["depth"]), _p(o["T"]), _p(o["n_contrib"]), _p(o["topk_idx"]),
+                                 _p(o["topk_w"]), s), "gs_topk_select")
+
+    def alloc_loss(self):
+        P, dev = self.P, self.device
+        return dict(dL_dF=torch.empty(P, self.D, dtype=self.feat_torch_dtype, device=dev),
+                    dL_dC=torch.empty(P, 3, dtype=torch.float32, device=dev),
+                    dL_dD=torch.empty(P, dtype=torch.float32, device=dev),
+                    loss=torch.empty(1, dtype=torch.float32, device=dev),
+                    scratch=torch.empty(int(self.lib.gs_loss_scratch_size(P)), dtype=torch.uint8, device=dev))
+
+    def blend_loss(self, feats, F_gt, rgb_gt, depth_gt, w_feat=1.0, w_rgb=1.0, w_depth=1.0, lo=None):
+        """Fused gather-blend + loss after a forward (or _select_into): writes out['F']
+        and the loss gradients (gs_feature_blend_loss)."""
+        st = self.state
+        N, o = st["N"], st["out"]
+        lo = lo if lo is not None else self.alloc_loss()
+        A.check(self.lib.gs_feature_blend_loss(
+            ctypes.byref(self.cfg), self.cams, self.n_cams, N, _p(o["topk_idx"]), _p(o["topk_w"]), _p(feats),
+            _p(F_gt), _p(o["rgb"]), _p(rgb_gt), _p(o["depth"]), _p(depth_gt), float(w_feat), float(w_rgb),
+            float(w_depth), _p(o["F"]), _p(lo["dL_dF"]), _p(lo["dL_dC"]), _p(lo["dL_dD"]), _p(lo["loss"]),
+            _p(self.ws), self.ws.numel(), _p(lo["scratch"]), lo["scratch"].numel(), self._stream()),
+            "gs_feature_blend_loss")
+        return lo
+
+    def train_step(self, mean3d, cov3d, opacity, rgb, feats, F_gt, rgb_gt, depth_gt, out=None, lo=None, grads=None,
+                   weights=(1.0, 1.0, 1.0)):
+        """One training step with every buffer supplied (no allocation, no host sync when
+        check_overflow is off): a1-a3, fused a4 + loss, a5."""
+        N = int(mean3d.shape[0])
+        self._ensure_ws(N)
+        o = out if out is not None else self.alloc_outputs(N)
+        self._select_into(N, mean3d, cov3d, opacity, rgb, o)
+        self.state = dict(N=N, mean3d=mean3d, cov3d=cov3d, opacity=opacity, rgb=rgb, feats=feats, out=o)
+        lo = self.blend_loss(feats, F_gt, rgb_gt, depth_gt, *weights, lo=lo)
+        g = self.backward(lo["dL_dF"], lo["dL_dC"], lo["dL_dD"], grads=grads)
+        return o, lo, g
+
     # ------------------------------------------------------------------ backward
     def alloc_grads(self, N: int, with_2d: bool = False):
         dev = self.device

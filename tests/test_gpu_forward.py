@@ -128,3 +128,23 @@ def test_bf16_rows_cosine():
     cos = (Fg[nz] * Fo[nz]).sum(1) / (np.linalg.norm(Fg[nz], axis=1) * np.linalg.norm(Fo[nz], axis=1))
     assert cos.min() >= 0.999, cos.min()
     assert np.array_equal(g["n_contrib"][ok], o["n"][ok])
+
+
+@pytest.mark.parametrize("dtype,D", [("f32", 512), ("f32", 24), ("bf16", 64)])
+def test_fused_blend_loss_matches_separate_calls(dtype, D):
+    """gs_feature_blend_loss gives the same F, loss gradients and loss as
+    gs_feature_blend followed by gs_loss_cos_l1."""
+    sc = S.planes_scene(7, 6000, D) if D >= 64 else S.random_scene_box(7, 3000, D)
+    cams = [S.pinhole(100, 75, 90.0)] if D < 512 else [S.pinhole(160, 120, 131.25)]
+    r, ts, out = U.gpu_forward(sc, cams, 8, (16, 16), feat_dtype=dtype)
+    Fgt, Cgt, Dgt = (torch.from_numpy(a).cuda() for a in S.voronoi_targets(3, cams, D))
+    Fgt = Fgt.to(r.feat_torch_dtype).contiguous()
+    sep = r.loss(out["F"], Fgt, out["rgb"], Cgt, out["depth"], Dgt, 1.0, 0.5, 0.25)
+    F_sep = out["F"].clone()
+    out["F"].zero_()
+    fused = r.blend_loss(ts[4], Fgt, Cgt, Dgt, 1.0, 0.5, 0.25)
+    torch.cuda.synchronize()
+    assert torch.equal(out["F"], F_sep)
+    for k in ("dL_dF", "dL_dC", "dL_dD"):
+        torch.testing.assert_close(fused[k].float(), sep[k].float(), rtol=1e-5, atol=1e-9)
+    torch.testing.assert_close(fused["loss"], sep["loss"], rtol=1e-6, atol=0)
