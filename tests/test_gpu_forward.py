@@ -145,6 +145,8 @@ def test_fused_blend_loss_matches_separate_calls(dtype, D):
     fused = r.blend_loss(ts[4], Fgt, Cgt, Dgt, 1.0, 0.5, 0.25)
     torch.cuda.synchronize()
     assert torch.equal(out["F"], F_sep)
+    # float32 values agree to summation order; bf16-stored dL/dF may round one ulp apart
+    rt = 2.0 ** -7 if dtype == "bf16" else 1e-5
     for k in ("dL_dF", "dL_dC", "dL_dD"):
-        torch.testing.assert_close(fused[k].float(), sep[k].float(), rtol=1e-5, atol=1e-9)
+        torch.testing.assert_close(fused[k].float(), sep[k].float(), rtol=rt if k == "dL_dF" else 1e-5, atol=1e-9)
     torch.testing.assert_close(fused["loss"], sep["loss"], rtol=1e-6, atol=0)
