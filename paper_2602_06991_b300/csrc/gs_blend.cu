@@ -223,152 +223,133 @@ __global__ void __launch_bounds__(1024) k_sum_fixed(const float *__restrict__ in
 }
 
 // ------------------------------------------------------------------------------------
-// Fused training form: gather-blend (Eqs. 3-4) and the loss gradient in one pass, in
-// screen-tile order.  One CTA per tile: the few distinct feature rows a tile selects
-// stay in L1 while its pixels are blended; each warp builds a pixel's F row in
-// registers, reads the target row, reduces |F|^2, F.Fgt, |Fgt|^2 and writes F and dL/dF
-// -- F is not read back.
+// Fused training form: gather-blend (Eqs. 3-4) and the loss gradient in one pass with
+// the k_blend layout (a group of lanes per pixel, many small CTAs): each pixel's F row
+// is built in registers, the target row is read, |F|^2, F.Fgt, |Fgt|^2 are reduced
+// over the pixel's lanes, and F and dL/dF are written -- F is never read back.
 // ------------------------------------------------------------------------------------
-template <int TW, int TH, int KM, bool BF16, int CPL>
-__global__ void __launch_bounds__(256) k_blend_loss(CamTable ct, int K, int D, const int *__restrict__ idx,
-                                                    const float *__restrict__ wts, const void *__restrict__ feats,
-                                                    const void *__restrict__ Fgt, const float *__restrict__ C,
-                                                    const float *__restrict__ Cgt, const float *__restrict__ Dp,
-                                                    const float *__restrict__ Dgt, float wf, float wc, float wd,
-                                                    float invP, void *__restrict__ F, void *__restrict__ dLdF,
-                                                    float *__restrict__ dLdC, float *__restrict__ dLdD,
-                                                    float *__restrict__ part, const int *__restrict__ err)
+template <int KM, bool BF16, int CPL>
+__global__ void __launch_bounds__(256) k_blend_loss(long long n_pix, int K, int nch, int lpp_log2,
+                                                    const int *__restrict__ idx, const float *__restrict__ wts,
+                                                    const void *__restrict__ feats, const void *__restrict__ Fgt,
+                                                    const float *__restrict__ C, const float *__restrict__ Cgt,
+                                                    const float *__restrict__ Dp, const float *__restrict__ Dgt,
+                                                    float wf, float wc, float wd, float invP, void *__restrict__ F,
+                                                    void *__restrict__ dLdF, float *__restrict__ dLdC,
+                                                    float *__restrict__ dLdD, float *__restrict__ part,
+                                                    const int *__restrict__ err)
 {
     using Ch = Chunk<BF16>;
     constexpr int VEC = Ch::VEC;
-    constexpr int B = TW * TH;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tile = blockIdx.x;
-    const int c = cam_of_tile(ct, tile);
-    const CamDev &cam = ct.c[c];
-    const int lt = tile - cam.tile_off;
-    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    const int nch = D / VEC;
+    const int lane = threadIdx.x & 31;
+    const int lpp = 1 << lpp_log2;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long p = warp * (32 >> lpp_log2) + (lane >> lpp_log2);
+    const int sub = lane & (lpp - 1);
+    const bool live = p < n_pix;
+    if (!live) p = n_pix - 1;                      // keep every lane in the shuffles
     const bool bad = *err != 0;
-    for (int pl = warp; pl < B; pl += 8) {
-        const int px = tx * TW + pl % TW, py = ty * TH + pl / TW;
-        if (px >= cam.W || py >= cam.H) continue;                 // warp-uniform
-        const long long p = cam.pix_off + (long long)py * cam.W + px;
-        int ids[KM];
-        float ws[KM], S = 0.f;
+    int ids[KM];
+    float ws[KM], S = 0.f;
 #pragma unroll
-        for (int k = 0; k < KM; ++k) {
-            ids[k] = -1;
-            ws[k] = 0.f;
-            if (k < K && !bad) {
-                ids[k] = __ldg(idx + p * K + k);
-                ws[k] = __ldg(wts + p * K + k);
-                S += ws[k];
-            }
+    for (int k = 0; k < KM; ++k) {
+        ids[k] = -1;
+        ws[k] = 0.f;
+        if (k < K && !bad) {
+            ids[k] = __ldg(idx + p * K + k);
+            ws[k] = __ldg(wts + p * K + k);
+            S += ws[k];
         }
-        const float inv = S > 0.f ? 1.f / S : 0.f;
+    }
+    const float inv = S > 0.f ? 1.f / S : 0.f;
 #pragma unroll
-        for (int k = 0; k < KM; ++k) ws[k] = ids[k] >= 0 ? ws[k] * inv : 0.f;
-        float f[CPL][VEC], g[CPL][VEC];
-        float ff = 0.f, fg = 0.f, gg = 0.f;
+    for (int k = 0; k < KM; ++k) ws[k] = ids[k] >= 0 ? ws[k] * inv : 0.f;
+    float f[CPL][VEC], g[CPL][VEC];
+    float ff = 0.f, fg = 0.f, gg = 0.f;
 #pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) {
-            const int ch = lane + 32 * cc;
+    for (int cc = 0; cc < CPL; ++cc) {
+        const int ch = sub + cc * lpp;
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) { f[cc][v] = 0.f; g[cc][v] = 0.f; }
-            if (ch < nch) {
-                Ch::load(Fgt, (size_t)p * nch + ch, g[cc]);
+        for (int v = 0; v < VEC; ++v) { f[cc][v] = 0.f; g[cc][v] = 0.f; }
+        if (ch < nch) {
+            float x[KM][VEC];
 #pragma unroll
-                for (int k = 0; k < KM; ++k) {
-                    if (ids[k] >= 0) {
-                        float x[VEC];
-                        Ch::load(feats, (size_t)ids[k] * nch + ch, x);
+            for (int k = 0; k < KM; ++k) {
+                if (ids[k] >= 0) Ch::load(feats, (size_t)ids[k] * nch + ch, x[k]);
+                else {
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) f[cc][v] = fmaf(ws[k], x[v], f[cc][v]);
-                    }
-                }
-                Ch::store(F, (size_t)p * nch + ch, f[cc]);
-                if (BF16) {          // the loss sees F as stored
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) f[cc][v] = __bfloat162float(__float2bfloat16(f[cc][v]));
-                }
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) {
-                    ff = fmaf(f[cc][v], f[cc][v], ff);
-                    fg = fmaf(f[cc][v], g[cc][v], fg);
-                    gg = fmaf(g[cc][v], g[cc][v], gg);
+                    for (int v = 0; v < VEC; ++v) x[k][v] = 0.f;
                 }
             }
-        }
+            Ch::load(Fgt, (size_t)p * nch + ch, g[cc]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ff += __shfl_xor_sync(0xffffffffu, ff, o);
-            fg += __shfl_xor_sync(0xffffffffu, fg, o);
-            gg += __shfl_xor_sync(0xffffffffu, gg, o);
-        }
-        const float nf = sqrtf(ff), ng = sqrtf(gg);
-        const bool ok = nf > 0.f && ng > 0.f;
-        const float cosv = ok ? fg / (nf * ng) : 0.f;
-        const float ca = ok ? -wf * invP / (nf * ng) : 0.f;
-        const float cb = ok ? wf * invP * cosv / ff : 0.f;
+            for (int k = 0; k < KM; ++k)
 #pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) {
-            const int ch = lane + 32 * cc;
-            if (ch < nch) {
-                float gdx[VEC];
+                for (int v = 0; v < VEC; ++v) f[cc][v] = fmaf(ws[k], x[k][v], f[cc][v]);
+            if (live) Ch::store(F, (size_t)p * nch + ch, f[cc]);
+            if (BF16) {            // the loss sees F as stored
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) gdx[v] = fmaf(ca, g[cc][v], cb * f[cc][v]);
-                Ch::store(dLdF, (size_t)p * nch + ch, gdx);
+                for (int v = 0; v < VEC; ++v) f[cc][v] = __bfloat162float(__float2bfloat16(f[cc][v]));
+            }
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                ff = fmaf(f[cc][v], f[cc][v], ff);
+                fg = fmaf(f[cc][v], g[cc][v], fg);
+                gg = fmaf(g[cc][v], g[cc][v], gg);
             }
         }
-        if (lane == 0) {
-            float lc = 0.f;
+    }
+    for (int o = 1; o < lpp; o <<= 1) {
+        ff += __shfl_xor_sync(0xffffffffu, ff, o);
+        fg += __shfl_xor_sync(0xffffffffu, fg, o);
+        gg += __shfl_xor_sync(0xffffffffu, gg, o);
+    }
+    if (!live) return;
+    const float nf = sqrtf(ff), ng = sqrtf(gg);
+    const bool ok = nf > 0.f && ng > 0.f;
+    const float cosv = ok ? fg / (nf * ng) : 0.f;
+    const float ca = ok ? -wf * invP / (nf * ng) : 0.f;
+    const float cb = ok ? wf * invP * cosv / ff : 0.f;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                float d = C[3 * p + i] - Cgt[3 * p + i];
-                lc += fabsf(d);
-                dLdC[3 * p + i] = wc * invP / 3.f * (float)((d > 0.f) - (d < 0.f));
-            }
-            float dd = Dp[p] - Dgt[p];
-            dLdD[p] = wd * invP * (float)((dd > 0.f) - (dd < 0.f));
-            part[p] = (wf * (1.f - cosv) + wc * lc / 3.f + wd * fabsf(dd)) * invP;
+    for (int cc = 0; cc < CPL; ++cc) {
+        const int ch = sub + cc * lpp;
+        if (ch < nch) {
+            float gdx[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) gdx[v] = fmaf(ca, g[cc][v], cb * f[cc][v]);
+            Ch::store(dLdF, (size_t)p * nch + ch, gdx);
         }
+    }
+    if (sub == 0) {
+        float lc = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float d = C[3 * p + i] - Cgt[3 * p + i];
+            lc += fabsf(d);
+            dLdC[3 * p + i] = wc * invP / 3.f * (float)((d > 0.f) - (d < 0.f));
+        }
+        float dd = Dp[p] - Dgt[p];
+        dLdD[p] = wd * invP * (float)((dd > 0.f) - (dd < 0.f));
+        part[p] = (wf * (1.f - cosv) + wc * lc / 3.f + wd * fabsf(dd)) * invP;
     }
 }
 
-template <int TW, int TH, int KM, bool BF16>
-static bool blend_loss_cpl(int cpl, const CamTable &ct, int K, int D, const int *idx, const float *w,
-                           const void *feats, const void *Fgt, const float *C, const float *Cgt, const float *Dp,
-                           const float *Dgt, float wf, float wc, float wd, float invP, void *F, void *dLdF,
-                           float *dLdC, float *dLdD, float *part, const int *err, cudaStream_t s)
+template <int KM, bool BF16>
+static bool blend_loss_cpl(int cpl, unsigned blocks, long long n_pix, int K, int nch, int l, const int *idx,
+                           const float *w, const void *feats, const void *Fgt, const float *C, const float *Cgt,
+                           const float *Dp, const float *Dgt, float wf, float wc, float wd, float invP, void *F,
+                           void *dLdF, float *dLdC, float *dLdD, float *part, const int *err, cudaStream_t s)
 {
-#define GS_BL(CP) k_blend_loss<TW, TH, KM, BF16, CP><<<ct.n_tiles, 256, 0, s>>>(ct, K, D, idx, w, feats, Fgt, C, Cgt, \
-                                                                             Dp, Dgt, wf, wc, wd, invP, F, dLdF,     \
-                                                                             dLdC, dLdD, part, err)
+#define GS_BL(CP) k_blend_loss<KM, BF16, CP><<<blocks, 256, 0, s>>>(n_pix, K, nch, l, idx, w, feats, Fgt, C, Cgt, Dp, \
+                                                                   Dgt, wf, wc, wd, invP, F, dLdF, dLdC, dLdD,   \
+                                                                   part, err)
     switch (cpl) {
     case 1: GS_BL(1); return true;
     case 2: GS_BL(2); return true;
     case 4: GS_BL(4); return true;
-    case 8: if (!BF16) { GS_BL(8); return true; } return false;
+    case 8: GS_BL(8); return true;
     }
 #undef GS_BL
-    return false;
-}
-
-template <int TW, int TH>
-static bool blend_loss_tile(int KM, int dtype, int cpl, const CamTable &ct, int K, int D, const int *idx,
-                            const float *w, const void *feats, const void *Fgt, const float *C, const float *Cgt,
-                            const float *Dp, const float *Dgt, float wf, float wc, float wd, float invP, void *F,
-                            void *dLdF, float *dLdC, float *dLdD, float *part, const int *err, cudaStream_t s)
-{
-#define GS_BT(KMV, BF) return blend_loss_cpl<TW, TH, KMV, BF>(cpl, ct, K, D, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, wf, \
-                                                               wc, wd, invP, F, dLdF, dLdC, dLdD, part, err, s)
-    if (dtype == GS_BF16) {
-        switch (KM) { case 4: GS_BT(4, true); case 8: GS_BT(8, true); case 16: GS_BT(16, true); case 32: GS_BT(32, true); }
-    } else {
-        switch (KM) { case 4: GS_BT(4, false); case 8: GS_BT(8, false); case 16: GS_BT(16, false); case 32: GS_BT(32, false); }
-    }
-#undef GS_BT
     return false;
 }
 
@@ -377,16 +358,26 @@ bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_
                        const float *Dgt, float wf, float wc, float wd, void *F, void *dLdF, float *dLdC, float *dLdD,
                        float *loss, float *part, const int *err, cudaStream_t s)
 {
+    (void)ct;
     if (n_pix <= 0) return true;
     const int KM = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
     const int nch = dtype == GS_BF16 ? D / 8 : D / 4;
-    const int cpl = nch <= 32 ? 1 : nch <= 64 ? 2 : nch <= 128 ? 4 : 8;
+    const int l = lpp_log2_for(nch);
+    const int lpp = 1 << l;
+    const int cpl_need = (nch + lpp - 1) / lpp;
+    const int cpl = cpl_need <= 1 ? 1 : cpl_need <= 2 ? 2 : cpl_need <= 4 ? 4 : 8;
+    const long long warps = (n_pix + (32 >> l) - 1) / (32 >> l);
+    const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
     const float invP = 1.f / (float)n_pix;
-    bool ok = false;
-    if (ct.tile_w == 16 && ct.tile_h == 16) ok = blend_loss_tile<16, 16>(KM, dtype, cpl, ct, K, D, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, wf, wc, wd, invP, F, dLdF, dLdC, dLdD, part, err, s);
-    else if (ct.tile_w == 32 && ct.tile_h == 8) ok = blend_loss_tile<32, 8>(KM, dtype, cpl, ct, K, D, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, wf, wc, wd, invP, F, dLdF, dLdC, dLdD, part, err, s);
-    else if (ct.tile_w == 16 && ct.tile_h == 8) ok = blend_loss_tile<16, 8>(KM, dtype, cpl, ct, K, D, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, wf, wc, wd, invP, F, dLdF, dLdC, dLdD, part, err, s);
-    else if (ct.tile_w == 8 && ct.tile_h == 8) ok = blend_loss_tile<8, 8>(KM, dtype, cpl, ct, K, D, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, wf, wc, wd, invP, F, dLdF, dLdC, dLdD, part, err, s);
+    bool ok;
+#define GS_BK(KMV, BF) ok = blend_loss_cpl<KMV, BF>(cpl, blocks, n_pix, K, nch, l, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, \
+                                                    wf, wc, wd, invP, F, dLdF, dLdC, dLdD, part, err, s)
+    if (dtype == GS_BF16) {
+        switch (KM) { case 4: GS_BK(4, true); break; case 8: GS_BK(8, true); break; case 16: GS_BK(16, true); break; default: GS_BK(32, true); }
+    } else {
+        switch (KM) { case 4: GS_BK(4, false); break; case 8: GS_BK(8, false); break; case 16: GS_BK(16, false); break; default: GS_BK(32, false); }
+    }
+#undef GS_BK
     if (!ok) return false;
     float *part2 = part + n_pix;
     k_sum_fixed<<<kSortBlocks, 1024, 0, s>>>(part, n_pix, part2);

@@ -106,18 +106,27 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
     }
 }
 
+// PPT vertically adjacent pixels per thread: a thread sums its pixels' contributions to
+// a staged Gaussian in registers, so each warp-level reduction covers 32 PPT pixels.
+constexpr int kBwdPPT = 2;
+
 template <int TW, int TH, int KM>
-__global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, const float4 *__restrict__ proj,
-                                                     const uint32_t *__restrict__ inst_vals,
-                                                     const uint32_t *__restrict__ inst_elem,
-                                                     const int2 *__restrict__ ranges, const int *__restrict__ err,
-                                                     const float *__restrict__ rgb_out, const float *__restrict__ depth_out,
-                                                     const int *__restrict__ topk_idx, const float *__restrict__ topk_w,
-                                                     const float *__restrict__ hbuf, const float *__restrict__ dLdC,
-                                                     const float *__restrict__ dLdD, float *__restrict__ inst_grad)
+__global__ void __launch_bounds__(TW *TH / kBwdPPT) k_walk_bwd(CamTable ct, int K, int N, const float4 *__restrict__ proj,
+                                                              const uint32_t *__restrict__ inst_vals,
+                                                              const uint32_t *__restrict__ inst_elem,
+                                                              const int2 *__restrict__ ranges, const int *__restrict__ err,
+                                                              const float *__restrict__ rgb_out,
+                                                              const float *__restrict__ depth_out,
+                                                              const int *__restrict__ topk_idx,
+                                                              const float *__restrict__ topk_w,
+                                                              const float *__restrict__ hbuf,
+                                                              const float *__restrict__ dLdC,
+                                                              const float *__restrict__ dLdD,
+                                                              float *__restrict__ inst_grad)
 {
-    constexpr int B = TW * TH;
-    constexpr int NW = B / 32;
+    constexpr int PPT = kBwdPPT;
+    constexpr int NT = TW * TH / PPT;
+    constexpr int NW = NT / 32;
     constexpr int BB = 64;                       // Gaussians per staged batch
     __shared__ float4 s_r0[BB], s_r1[BB], s_r2[BB], s_r3[BB];
     __shared__ int s_g[BB];
@@ -130,65 +139,82 @@ __global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, 
     const CamDev &cam = ct.c[c];
     const int lt = tile - cam.tile_off;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
-    const bool inside = px < cam.W && py < cam.H;
     int2 rg = ranges[tile];
     if (*err) rg.y = rg.x;
-    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
-    const long long p = cam.pix_off + (long long)py * cam.W + px;
+    const int px = tx * TW + (tid % TW);
+    const float pxf = (float)px + 0.5f;
 
-    float dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dD = 0.f, total = 0.f;
-    int kid[KM];
-    float kfp[KM];
+    float pyf[PPT], dC0[PPT], dC1[PPT], dC2[PPT], dD[PPT], total[PPT], T[PPT], prefix[PPT];
+    int kid[PPT][KM];
+    float kfp[PPT][KM];
+    bool pdone[PPT];
 #pragma unroll
-    for (int k = 0; k < KM; ++k) { kid[k] = -2; kfp[k] = 0.f; }
-    if (inside) {
-        dC0 = dLdC[3 * p]; dC1 = dLdC[3 * p + 1]; dC2 = dLdC[3 * p + 2];
-        dD = dLdD[p];
-        total = dC0 * rgb_out[3 * p] + dC1 * rgb_out[3 * p + 1] + dC2 * rgb_out[3 * p + 2] + dD * depth_out[p];
-        float S = 0.f;
+    for (int r = 0; r < PPT; ++r) {
+        const int py = ty * TH + (tid / TW) * PPT + r;
+        pyf[r] = (float)py + 0.5f;
+        const bool inside = px < cam.W && py < cam.H;
+        pdone[r] = !inside;
+        T[r] = 1.f;
+        prefix[r] = 0.f;
+        dC0[r] = dC1[r] = dC2[r] = dD[r] = total[r] = 0.f;
 #pragma unroll
-        for (int k = 0; k < KM; ++k)
-            if (k < K) S += topk_w[p * K + k];
-        float inv = S > 0.f ? 1.f / S : 0.f;
-        float H = 0.f;
+        for (int k = 0; k < KM; ++k) { kid[r][k] = -2; kfp[r][k] = 0.f; }
+        if (inside) {
+            const long long p = cam.pix_off + (long long)py * cam.W + px;
+            dC0[r] = dLdC[3 * p]; dC1[r] = dLdC[3 * p + 1]; dC2[r] = dLdC[3 * p + 2];
+            dD[r] = dLdD[p];
+            total[r] = dC0[r] * rgb_out[3 * p] + dC1[r] * rgb_out[3 * p + 1] + dC2[r] * rgb_out[3 * p + 2] +
+                       dD[r] * depth_out[p];
+            float S = 0.f;
 #pragma unroll
-        for (int k = 0; k < KM; ++k) {
-            if (k < K) {
-                int id = topk_idx[p * K + k];
-                if (id >= 0) {
-                    kid[k] = id;
-                    kfp[k] = hbuf[p * K + k];
-                    H += topk_w[p * K + k] * inv * kfp[k];
+            for (int k = 0; k < KM; ++k)
+                if (k < K) S += topk_w[p * K + k];
+            const float inv = S > 0.f ? 1.f / S : 0.f;
+            float H = 0.f;
+#pragma unroll
+            for (int k = 0; k < KM; ++k) {
+                if (k < K) {
+                    const int id = topk_idx[p * K + k];
+                    if (id >= 0) {
+                        kid[r][k] = id;
+                        kfp[r][k] = hbuf[p * K + k];
+                        H += topk_w[p * K + k] * inv * kfp[r][k];
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int k = 0; k < KM; ++k) kfp[k] = (kfp[k] - H) * inv;
+            for (int k = 0; k < KM; ++k) kfp[r][k] = (kfp[r][k] - H) * inv;
+        }
     }
-    float T = 1.f, prefix = 0.f;
-    bool done = !inside;
+    auto all_done = [&]() {
+        bool d = true;
+#pragma unroll
+        for (int r = 0; r < PPT; ++r) d = d && pdone[r];
+        return d;
+    };
     const int cN = c * N;
     for (int b0 = rg.x; b0 < rg.y; b0 += BB) {
-        if (__syncthreads_count(!done) == 0) {
+        if (__syncthreads_count(!all_done()) == 0) {
             // every pixel stopped: the remaining instances of this tile contribute nothing
-            for (int m = b0 + tid; m < rg.y; m += B) {
+            for (int m = b0 + tid; m < rg.y; m += NT) {
                 float *dst = inst_grad + (size_t)kGradVals * inst_vals[m];
 #pragma unroll
                 for (int v = 0; v < kGradVals; ++v) dst[v] = 0.f;
             }
             break;
         }
-        if (tid < BB && b0 + tid < rg.y) {
-            uint32_t o = inst_vals[b0 + tid];
-            uint32_t e = inst_elem[o];
-            const float4 *r = proj + 4 * (size_t)e;
-            s_r0[tid] = r[0];
-            s_r1[tid] = r[1];
-            s_r2[tid] = r[2];
-            s_r3[tid] = r[3];
-            s_g[tid] = (int)e - cN;
-            s_o[tid] = o;
+        for (int t = tid; t < BB; t += NT) {
+            if (b0 + t < rg.y) {
+                const uint32_t o = inst_vals[b0 + t];
+                const uint32_t e = inst_elem[o];
+                const float4 *rr = proj + 4 * (size_t)e;
+                s_r0[t] = rr[0];
+                s_r1[t] = rr[1];
+                s_r2[t] = rr[2];
+                s_r3[t] = rr[3];
+                s_g[t] = (int)e - cN;
+                s_o[t] = o;
+            }
         }
         __syncthreads();
         const int cnt = min(BB, rg.y - b0);
@@ -196,7 +222,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, 
         // counts its entries only up to that point
         int j_end = cnt;
         for (int j = 0; j < cnt; ++j) {
-            if (__all_sync(0xffffffffu, done)) {
+            if (__all_sync(0xffffffffu, all_done())) {
                 j_end = j;
                 break;
             }
@@ -204,48 +230,48 @@ __global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, 
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = 0.f;
             bool contrib = false;
-            if (!done) {
-                float dx, dy;
-                const float4 r1 = s_r1[j];
-                float q = eval_q(pxf, pyf, s_r0[j], r1, dx, dy);
-                if (q <= kQMax) {
-                    float G, ao;
-                    float alpha = eval_alpha(q, r1.w, G, ao);
-                    if (alpha >= kAlphaMin) {
-                        float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-                        if (test_T < kTStop) {
-                            done = true;
-                        } else {
-                            contrib = true;
-                            float w = __fmul_rn(alpha, T);
-                            const float4 r2 = s_r2[j];
-                            const int gid = s_g[j];
-                            float fp = 0.f;
+            const float4 r0 = s_r0[j], r1 = s_r1[j];
 #pragma unroll
-                            for (int k = 0; k < KM; ++k) fp = (kid[k] == gid) ? kfp[k] : fp;
-                            float gi = dC0 * r2.x + dC1 * r2.y + dC2 * r2.z + dD * r2.w + fp;
-                            prefix = fmaf(gi, w, prefix);
-                            float suffix = total - prefix;
-                            float dalpha = gi * T - suffix / (1.f - alpha);
-                            v[6] = w * dC0; v[7] = w * dC1; v[8] = w * dC2; v[9] = w * dD;
-                            if (ao < kAlphaClamp) {
-                                const float4 r3 = s_r3[j];
-                                v[5] = dalpha * G;
-                                float dq = -0.5f * alpha * dalpha;
-                                v[2] = dq * dx * dx;
-                                v[3] = dq * 2.f * dx * dy;
-                                v[4] = dq * dy * dy;
-                                v[0] = -2.f * dq * (r3.x * dx + r3.y * dy);
-                                v[1] = -2.f * dq * (r3.y * dx + r3.z * dy);
-                            }
-                            T = test_T;
-                        }
-                    }
+            for (int r = 0; r < PPT; ++r) {
+                if (pdone[r]) continue;
+                float dx, dy;
+                const float q = eval_q(pxf, pyf[r], r0, r1, dx, dy);
+                if (q > kQMax) continue;
+                float G, ao;
+                const float alpha = eval_alpha(q, r1.w, G, ao);
+                if (alpha < kAlphaMin) continue;
+                const float test_T = __fmul_rn(T[r], __fsub_rn(1.f, alpha));
+                if (test_T < kTStop) {
+                    pdone[r] = true;
+                    continue;
                 }
+                contrib = true;
+                const float w = __fmul_rn(alpha, T[r]);
+                const float4 r2 = s_r2[j];
+                const int gid = s_g[j];
+                float fp = 0.f;
+#pragma unroll
+                for (int k = 0; k < KM; ++k) fp = (kid[r][k] == gid) ? kfp[r][k] : fp;
+                const float gi = dC0[r] * r2.x + dC1[r] * r2.y + dC2[r] * r2.z + dD[r] * r2.w + fp;
+                prefix[r] = fmaf(gi, w, prefix[r]);
+                const float suffix = total[r] - prefix[r];
+                const float dalpha = gi * T[r] - suffix / (1.f - alpha);
+                v[6] += w * dC0[r]; v[7] += w * dC1[r]; v[8] += w * dC2[r]; v[9] += w * dD[r];
+                if (ao < kAlphaClamp) {
+                    const float4 r3 = s_r3[j];
+                    v[5] += dalpha * G;
+                    const float dq = -0.5f * alpha * dalpha;
+                    v[2] += dq * dx * dx;
+                    v[3] += dq * 2.f * dx * dy;
+                    v[4] += dq * dy * dy;
+                    v[0] += -2.f * dq * (r3.x * dx + r3.y * dy);
+                    v[1] += -2.f * dq * (r3.y * dx + r3.z * dy);
+                }
+                T[r] = test_T;
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                float d = warp_reduce16(v, lane);
-                int vi = (lane >> 1) & 15;
+                const float d = warp_reduce16(v, lane);
+                const int vi = (lane >> 1) & 15;
                 if (!(lane & 1) && vi < kGradVals) s_red[warp][j][vi] = d;
             } else if (lane < kGradVals) {
                 s_red[warp][j][lane] = 0.f;
@@ -253,12 +279,12 @@ __global__ void __launch_bounds__(TW *TH) k_walk_bwd(CamTable ct, int K, int N, 
         }
         if (lane == 0) s_jend[warp] = j_end;
         __syncthreads();
-        for (int i = tid; i < cnt * kGradVals; i += B) {
-            int j = i / kGradVals, vi = i - j * kGradVals;
-            float s = 0.f;
+        for (int i = tid; i < cnt * kGradVals; i += NT) {
+            const int j = i / kGradVals, vi = i - j * kGradVals;
+            float sum = 0.f;
 #pragma unroll
-            for (int w = 0; w < NW; ++w) s += j < s_jend[w] ? s_red[w][j][vi] : 0.f;
-            inst_grad[(size_t)kGradVals * s_o[j] + vi] = s;
+            for (int w = 0; w < NW; ++w) sum += j < s_jend[w] ? s_red[w][j][vi] : 0.f;
+            inst_grad[(size_t)kGradVals * s_o[j] + vi] = sum;
         }
     }
 }
@@ -284,7 +310,7 @@ static bool walk_bwd_k(int KM, dim3 grid, cudaStream_t s, const CamTable &ct, in
                        const float *Dp, const int *ti, const float *tw, const float *h, const float *dC,
                        const float *dD, float *ig)
 {
-    constexpr int B = TW * TH;
+    constexpr int B = TW * TH / kBwdPPT;
     switch (KM) {
     case 4: k_walk_bwd<TW, TH, 4><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig); return true;
     case 8: k_walk_bwd<TW, TH, 8><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig); return true;
