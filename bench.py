@@ -100,19 +100,23 @@ class ClockSampler:
 class Step:
     """All buffers of one training step, resident on the device."""
 
-    def __init__(self, workload, seed=0):
+    def __init__(self, workload, seed=0, tile=None, scene=None):
         import torch
         import gs_scenes as S
         from paper_2602_06991_b300.renderer import TopKRenderer
-        sc, cams, K, tile, fdt = S.make_config(workload, seed)
+        sc, cams, K, tile0, fdt = scene if scene is not None else S.make_config(workload, seed)
+        tile = tuple(tile) if tile is not None else tile0
         self.scene, self.cams, self.K, self.tile, self.fdt = sc, cams, K, tile, fdt
         self.r = TopKRenderer(cams, K=K, D=sc.d, tile=tile, feat_dtype=fdt, check_overflow=True)
         dev = self.r.device
         tdt = self.r.feat_torch_dtype
         t = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(dev).to(dt).contiguous()
         self.inp = [t(sc.mean3d), t(sc.cov3d), t(sc.opacity), t(sc.rgb), t(sc.feats, tdt)]
-        Fgt, Cgt, Dgt = S.voronoi_targets(seed + 100, cams, sc.d)
-        self.tgt = [t(Fgt, tdt), t(Cgt), t(Dgt)]
+        # loss targets: 12 Voronoi cells per view, expanded on the device from labels
+        lab, fv, cv, dv = S.voronoi_sites(seed + 100, cams, sc.d)
+        lab = torch.from_numpy(lab).to(dev).long()
+        self.tgt = [t(fv, tdt)[lab].contiguous(), t(cv)[lab].contiguous(), t(dv)[lab].contiguous()]
+        del lab
         self.N, self.P, self.D = sc.n, self.r.P, sc.d
         # first forward checks the instance capacity once (host sync), then steps run free
         self.out = self.r.forward(*self.inp)
@@ -142,6 +146,28 @@ class Step:
                                     _p(self.inp[4]), _p(o["F"]), self.r._stream())
 
 
+def run_bf16_batched(args):
+    """The BF16 multi-keyframe form: 1M Gaussians, BF16 rows, 8 orbit keyframes of mixed
+    resolution rendered and back-propagated as one step (one launch per stage over all
+    views, the whole step one CUDA graph), tile shape picked by the autotuner."""
+    import torch
+    import gs_scenes as S
+    from paper_2602_06991_b300 import autotune
+    scene = S.make_config("batched", 0)
+    sc, cams, K, tile0, fdt = scene
+    tuned = autotune.tune(cams, sc.n, K, sc.d, fdt, lambda tile: Step("batched", tile=tile, scene=scene).run)
+    torch.cuda.empty_cache()
+    step = Step("batched", tile=tuned["tile"], scene=scene)
+    ms = autotune.time_step(lambda: step.run, reps=max(5, min(args.steps, 20)), warmup=args.warmup)
+    out = {"value": round(step.P / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "ms_per_step": round(ms, 4),
+           "pixels_per_step": step.P, "gaussians": step.N, "views": len(cams), "D": step.D, "K": K,
+           "dtype": "bf16", "tile": list(tuned["tile"]), "autotune_ms": tuned["ms"],
+           "workload": "batched: " + S.CONFIGS["batched"]}
+    del step
+    torch.cuda.empty_cache()
+    return out
+
+
 def blend_algorithmic_bytes(step):
     """Bytes the gather-blend must move: F written (P D s), the Top-K record read
     (P K (4 + 4)), and each distinct selected feature row read once (U D s)."""
@@ -169,6 +195,22 @@ def count_launches(step):
         return n if n > 0 else None
     except Exception:
         return None
+
+
+def aggregate_ranks(ms: float, pixels: int, world: int, device=None):
+    """Whole-job timing of N replicas: the slowest rank's ms per step and the pixels all
+    ranks processed per step (barrier, then all-reduce MAX and SUM).  Every rank gets
+    the same pair.  No data-path collective: only these two scalars are exchanged."""
+    if world <= 1:
+        return ms, pixels
+    import torch
+    import torch.distributed as dist
+    dist.barrier()
+    t_ms = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    t_px = torch.tensor([float(pixels)], dtype=torch.float64, device=device)
+    dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t_px, op=dist.ReduceOp.SUM)
+    return float(t_ms.item()), int(round(t_px.item()))
 
 
 def run_ours(args, rank, world, local_rank):
@@ -224,12 +266,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = t0.elapsed_time(t1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        ms = float(tt.item())
-    value = world * step.P / (ms * 1e-3) / 1e6
+    ms, total_pixels = aggregate_ranks(ms, step.P, world, device="cuda")
+    value = total_pixels / (ms * 1e-3) / 1e6
 
     hbm, peak_kind = peaks()
     ab, uniq = blend_algorithmic_bytes(step)
@@ -253,6 +291,11 @@ def run_ours(args, rank, world, local_rank):
     }
     if rank == 0 and not args.no_e2e:
         res["e2e"] = run_e2e(step, args)
+    if rank == 0 and not args.no_batched:
+        del step
+        torch.cuda.empty_cache()
+        res["bf16_batched"] = run_bf16_batched(args)
+        res["bf16_batched"]["speedup_vs_f32_frame"] = round(res["bf16_batched"]["value"] / res["value"], 3)
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
     return res
@@ -350,6 +393,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-launch-count", action="store_true", help="skip the CUPTI launch count (for ncu runs)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the BF16 multi-keyframe measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))

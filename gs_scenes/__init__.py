@@ -243,6 +243,30 @@ def voronoi_targets(seed, cams: List[Camera], d: int, n_sites=12):
             np.ascontiguousarray(np.concatenate(Dp), f32))
 
 
+def voronoi_sites(seed, cams: List[Camera], d: int, n_sites=12):
+    """The same targets as voronoi_targets in factored form, for large frames: per-pixel
+    cell labels (int32, pixel-major, cameras concatenated, with each camera's cells
+    numbered after the previous camera's) and the per-cell values (unit D-vectors,
+    RGB, depth).  Expand with values[labels]."""
+    rng = np.random.default_rng(seed)
+    labs, F, C, Dp = [], [], [], []
+    base = 0
+    for cam in cams:
+        sites = rng.uniform([0, 0], [cam.width, cam.height], size=(n_sites, 2))
+        fv = _unit_rows(rng, n_sites, d)
+        cv = rng.uniform(0, 1, size=(n_sites, 3))
+        dv = rng.uniform(1, 5, size=n_sites)
+        ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+        px = np.stack([xs.ravel() + 0.5, ys.ravel() + 0.5], axis=1)
+        lab = np.argmin(((px[:, None, :] - sites[None]) ** 2).sum(-1), axis=1)
+        labs.append(lab + base)
+        base += n_sites
+        F.append(fv); C.append(cv); Dp.append(dv)
+    f32 = np.float32
+    return (np.concatenate(labs).astype(np.int32), np.concatenate(F).astype(f32),
+            np.concatenate(C).astype(f32), np.concatenate(Dp).astype(f32))
+
+
 def upstream_grads(seed, n_pix: int, d: int, scale=1.0):
     """Seeded upstream gradients dL/dF (P, D), dL/dC (P, 3), dL/dD (P,)."""
     rng = np.random.default_rng(seed)
