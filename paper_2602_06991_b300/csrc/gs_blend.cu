@@ -105,6 +105,178 @@ __global__ void __launch_bounds__(256) k_blend(long long n_pix, int K, int nch, 
     }
 }
 
+
+// ------------------------------------------------------------------------------------
+// Pixel-group form of the gather-blend.  Neighbouring pixels select mostly the same
+// Gaussians, so a warp takes G consecutive pixels (G K <= 32 (id, w) pairs, one per
+// lane), finds the distinct ids among them with a warp match, and loads each distinct
+// row once for the whole group: every lane holds CPL 16-byte chunks of the row and
+// adds it, with each pixel's renormalised weight (0 where the pixel did not select
+// it), into G register accumulators.  The row traffic from L2 drops from G K rows to
+// the group's distinct rows.  A pixel's terms are summed in the order of first
+// occurrence in the group, so F depends only on the grouping (always G consecutive
+// flat pixels), never on the tile shape; the blend-only and the fused kernels group
+// identically and give bit-identical F.
+// ------------------------------------------------------------------------------------
+template <int KM>
+struct Group {
+    static constexpr int G = KM <= 8 ? 4 : 2;             // pixels per warp (KM <= 16)
+};
+
+struct GroupTable {
+    float w[32][4];                                       // distinct id x pixel
+    int id[32];
+};
+
+// Loads the group's (id, w') pairs, builds the distinct-id table of this warp and
+// returns the number of distinct ids.  Lane l holds pixel l / KM, slot l % KM.
+template <int KM, int G>
+__device__ __forceinline__ int group_table(long long p0, long long n_pix, int K, const int *__restrict__ idx,
+                                           const float *__restrict__ wts, bool bad, int lane, GroupTable &t)
+{
+    const int gl = lane / KM, kl = lane - gl * KM;
+    const long long pl = p0 + gl;
+    int id = -1;
+    float wn = 0.f;
+    if (gl < G && kl < K && pl < n_pix && !bad) {
+        // S in slot order, exactly as the per-pixel kernels sum it
+        float S = 0.f;
+        for (int k = 0; k < K; ++k) S += __ldg(wts + pl * K + k);
+        const float inv = S > 0.f ? 1.f / S : 0.f;
+        id = __ldg(idx + pl * K + kl);
+        wn = id >= 0 ? __ldg(wts + pl * K + kl) * inv : 0.f;
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, id);
+    const int first = __ffs(same) - 1;
+    const unsigned lead = __ballot_sync(0xffffffffu, id >= 0 && first == lane);
+    const int U = __popc(lead);
+    if (lane < U) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) t.w[lane][g] = 0.f;
+    }
+    __syncwarp();
+    if (id >= 0) {
+        const int r = __popc(lead & ((1u << first) - 1u));
+        t.w[r][gl] = wn;
+        if (first == lane) t.id[r] = id;
+    }
+    __syncwarp();
+    return U;
+}
+
+// acc[g] = sum over the distinct rows u of w'[u][g] f_u, for chunks lane + 32 c.
+// Two rows are in flight: the next row's loads are issued before this row's FMAs.
+template <int G, bool BF16, int CPL>
+__device__ __forceinline__ void group_accumulate(int U, int nch, int lane, const void *__restrict__ feats,
+                                                 const GroupTable &t, float (&acc)[G][CPL][Chunk<BF16>::VEC])
+{
+    using Ch = Chunk<BF16>;
+    constexpr int VEC = Ch::VEC;
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) acc[g][c][v] = 0.f;
+    auto load_row = [&](int u, float (&x)[CPL][VEC]) {
+        const size_t base = (size_t)t.id[u] * nch;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int ch = lane + 32 * c;
+            if (ch < nch) Ch::load(feats, base + ch, x[c]);
+            else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) x[c][v] = 0.f;
+            }
+        }
+    };
+    auto add_row = [&](int u, const float (&x)[CPL][VEC]) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float wg = t.w[u][g];
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[g][c][v] = fmaf(wg, x[c][v], acc[g][c][v]);
+        }
+    };
+    float xa[CPL][VEC], xb[CPL][VEC];
+    if (U > 0) load_row(0, xa);
+    for (int u = 0; u < U; u += 2) {
+        if (u + 1 < U) load_row(u + 1, xb);
+        add_row(u, xa);
+        if (u + 1 < U) {
+            if (u + 2 < U) load_row(u + 2, xa);
+            add_row(u + 1, xb);
+        }
+    }
+}
+
+template <int KM, bool BF16, int CPL>
+__global__ void __launch_bounds__(256) k_blend_group(long long n_pix, int K, int nch, const int *__restrict__ idx,
+                                                     const float *__restrict__ wts, const void *__restrict__ feats,
+                                                     void *__restrict__ F, const int *__restrict__ err)
+{
+    using Ch = Chunk<BF16>;
+    constexpr int VEC = Ch::VEC;
+    constexpr int G = Group<KM>::G;
+    __shared__ GroupTable s_t[8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long p0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G;
+    if (p0 >= n_pix) return;                         // whole warp leaves together
+    const bool bad = err && *err;
+    GroupTable &t = s_t[wib];
+    const int U = group_table<KM, G>(p0, n_pix, K, idx, wts, bad, lane, t);
+    float acc[G][CPL][VEC];
+    group_accumulate<G, BF16, CPL>(U, nch, lane, feats, t, acc);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        if (p0 + g >= n_pix) break;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int ch = lane + 32 * c;
+            if (ch < nch) Ch::store(F, (size_t)(p0 + g) * nch + ch, acc[g][c]);
+        }
+    }
+}
+
+// The group form serves K <= 16 and nch >= 32 16-byte chunks while the G accumulator
+// rows fit in 64 registers per lane (G CPL VEC <= 64): float32 rows D 128..512 at
+// K <= 8 and D 128..1024 at K <= 16; bf16 rows D 256..512 at K <= 8 and 256..1024 at
+// K <= 16.  Other widths and K keep the per-pixel kernels.
+template <int KM, bool BF16, int CPL>
+struct GroupFits {
+    static constexpr bool value = Group<KM>::G * CPL * Chunk<BF16>::VEC <= 64;
+};
+
+static int group_cpl(int dtype, int K, int nch)
+{
+    if (K > 16 || nch < 32) return 0;
+    const int need = (nch + 31) / 32;
+    const int cpl = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 16;
+    const int G = K <= 8 ? 4 : 2;
+    const int vec = dtype == GS_BF16 ? 8 : 4;
+    return G * cpl * vec <= 64 ? cpl : 0;
+}
+
+template <int KM, bool BF16>
+static void blend_group_launch(int cpl, unsigned blocks, cudaStream_t s, long long n_pix, int K, int nch,
+                               const int *idx, const float *w, const void *feats, void *F, const int *err)
+{
+    switch (cpl) {
+    case 1: k_blend_group<KM, BF16, 1><<<blocks, 256, 0, s>>>(n_pix, K, nch, idx, w, feats, F, err); break;
+    case 2: k_blend_group<KM, BF16, 2><<<blocks, 256, 0, s>>>(n_pix, K, nch, idx, w, feats, F, err); break;
+    case 4:
+        if constexpr (GroupFits<KM, BF16, 4>::value)
+            k_blend_group<KM, BF16, 4><<<blocks, 256, 0, s>>>(n_pix, K, nch, idx, w, feats, F, err);
+        break;
+    case 8:
+        if constexpr (GroupFits<KM, BF16, 8>::value)
+            k_blend_group<KM, BF16, 8><<<blocks, 256, 0, s>>>(n_pix, K, nch, idx, w, feats, F, err);
+        break;
+    }
+}
+
 static int lpp_log2_for(int nch)
 {
     int l = 0;
@@ -133,8 +305,29 @@ bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, cons
 {
     if (n_pix <= 0) return true;
     int KM = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
-    if (dtype == GS_BF16) return blend_k<true>(KM, K, D / 8, n_pix, idx, w, feats, F, err, s);
-    return blend_k<false>(KM, K, D / 4, n_pix, idx, w, feats, F, err, s);
+    const int nch = dtype == GS_BF16 ? D / 8 : D / 4;
+    const int cpl = group_cpl(dtype, K, nch);
+    if (cpl) {
+        const int G = KM <= 8 ? 4 : 2;
+        const long long warps = (n_pix + G - 1) / G;
+        const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+        if (dtype == GS_BF16) {
+            switch (KM) {
+            case 4: blend_group_launch<4, true>(cpl, blocks, s, n_pix, K, nch, idx, w, feats, F, err); break;
+            case 8: blend_group_launch<8, true>(cpl, blocks, s, n_pix, K, nch, idx, w, feats, F, err); break;
+            default: blend_group_launch<16, true>(cpl, blocks, s, n_pix, K, nch, idx, w, feats, F, err); break;
+            }
+        } else {
+            switch (KM) {
+            case 4: blend_group_launch<4, false>(cpl, blocks, s, n_pix, K, nch, idx, w, feats, F, err); break;
+            case 8: blend_group_launch<8, false>(cpl, blocks, s, n_pix, K, nch, idx, w, feats, F, err); break;
+            default: blend_group_launch<16, false>(cpl, blocks, s, n_pix, K, nch, idx, w, feats, F, err); break;
+            }
+        }
+        return true;
+    }
+    if (dtype == GS_BF16) return blend_k<true>(KM, K, nch, n_pix, idx, w, feats, F, err, s);
+    return blend_k<false>(KM, K, nch, n_pix, idx, w, feats, F, err, s);
 }
 
 // ------------------------------------------------------------------------------------
@@ -334,6 +527,117 @@ __global__ void __launch_bounds__(256) k_blend_loss(long long n_pix, int K, int 
     }
 }
 
+
+// Fused training form in the pixel-group layout: the G rows of F are built in
+// registers as in k_blend_group, then pixel by pixel the target row is read, |F|^2,
+// F.Fgt and |Fgt|^2 are reduced over the warp, and F and dL/dF are written.
+template <int KM, bool BF16, int CPL>
+__global__ void __launch_bounds__(256) k_blend_loss_group(long long n_pix, int K, int nch,
+                                                          const int *__restrict__ idx, const float *__restrict__ wts,
+                                                          const void *__restrict__ feats, const void *__restrict__ Fgt,
+                                                          const float *__restrict__ C, const float *__restrict__ Cgt,
+                                                          const float *__restrict__ Dp, const float *__restrict__ Dgt,
+                                                          float wf, float wc, float wd, float invP,
+                                                          void *__restrict__ F, void *__restrict__ dLdF,
+                                                          float *__restrict__ dLdC, float *__restrict__ dLdD,
+                                                          float *__restrict__ part, const int *__restrict__ err)
+{
+    using Ch = Chunk<BF16>;
+    constexpr int VEC = Ch::VEC;
+    constexpr int G = Group<KM>::G;
+    __shared__ GroupTable s_t[8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long p0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G;
+    if (p0 >= n_pix) return;
+    const bool bad = *err != 0;
+    GroupTable &t = s_t[wib];
+    const int U = group_table<KM, G>(p0, n_pix, K, idx, wts, bad, lane, t);
+    float acc[G][CPL][VEC];
+    group_accumulate<G, BF16, CPL>(U, nch, lane, feats, t, acc);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const long long p = p0 + g;
+        if (p >= n_pix) break;                      // warp-uniform
+        float gt[CPL][VEC];
+        float ff = 0.f, fg = 0.f, gg = 0.f;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int ch = lane + 32 * c;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) gt[c][v] = 0.f;
+            if (ch < nch) {
+                Ch::load(Fgt, (size_t)p * nch + ch, gt[c]);
+                Ch::store(F, (size_t)p * nch + ch, acc[g][c]);
+                if (BF16) {            // the loss sees F as stored
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[g][c][v] = __bfloat162float(__float2bfloat16(acc[g][c][v]));
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                ff = fmaf(acc[g][c][v], acc[g][c][v], ff);
+                fg = fmaf(acc[g][c][v], gt[c][v], fg);
+                gg = fmaf(gt[c][v], gt[c][v], gg);
+            }
+        }
+        for (int o = 1; o < 32; o <<= 1) {
+            ff += __shfl_xor_sync(0xffffffffu, ff, o);
+            fg += __shfl_xor_sync(0xffffffffu, fg, o);
+            gg += __shfl_xor_sync(0xffffffffu, gg, o);
+        }
+        const float nf = sqrtf(ff), ng = sqrtf(gg);
+        const bool ok = nf > 0.f && ng > 0.f;
+        const float cosv = ok ? fg / (nf * ng) : 0.f;
+        const float ca = ok ? -wf * invP / (nf * ng) : 0.f;
+        const float cb = ok ? wf * invP * cosv / ff : 0.f;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int ch = lane + 32 * c;
+            if (ch < nch) {
+                float gdx[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) gdx[v] = fmaf(ca, gt[c][v], cb * acc[g][c][v]);
+                Ch::store(dLdF, (size_t)p * nch + ch, gdx);
+            }
+        }
+        if (lane == g) {
+            float lc = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                float d = C[3 * p + i] - Cgt[3 * p + i];
+                lc += fabsf(d);
+                dLdC[3 * p + i] = wc * invP / 3.f * (float)((d > 0.f) - (d < 0.f));
+            }
+            float dd = Dp[p] - Dgt[p];
+            dLdD[p] = wd * invP * (float)((dd > 0.f) - (dd < 0.f));
+            part[p] = (wf * (1.f - cosv) + wc * lc / 3.f + wd * fabsf(dd)) * invP;
+        }
+    }
+}
+
+template <int KM, bool BF16>
+static void blend_loss_group_launch(int cpl, unsigned blocks, cudaStream_t s, long long n_pix, int K, int nch,
+                                    const int *idx, const float *w, const void *feats, const void *Fgt, const float *C,
+                                    const float *Cgt, const float *Dp, const float *Dgt, float wf, float wc, float wd,
+                                    float invP, void *F, void *dLdF, float *dLdC, float *dLdD, float *part,
+                                    const int *err)
+{
+#define GS_BLGC(CP)                                                                                                   \
+    k_blend_loss_group<KM, BF16, CP><<<blocks, 256, 0, s>>>(n_pix, K, nch, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, wf, wc, \
+                                                            wd, invP, F, dLdF, dLdC, dLdD, part, err)
+    switch (cpl) {
+    case 1: GS_BLGC(1); break;
+    case 2: GS_BLGC(2); break;
+    case 4:
+        if constexpr (GroupFits<KM, BF16, 4>::value) GS_BLGC(4);
+        break;
+    case 8:
+        if constexpr (GroupFits<KM, BF16, 8>::value) GS_BLGC(8);
+        break;
+    }
+#undef GS_BLGC
+}
+
 template <int KM, bool BF16>
 static bool blend_loss_cpl(int cpl, unsigned blocks, long long n_pix, int K, int nch, int l, const int *idx,
                            const float *w, const void *feats, const void *Fgt, const float *C, const float *Cgt,
@@ -369,7 +673,22 @@ bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_
     const long long warps = (n_pix + (32 >> l) - 1) / (32 >> l);
     const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
     const float invP = 1.f / (float)n_pix;
-    bool ok;
+    bool ok = true;
+    const int gcpl = group_cpl(dtype, K, nch);
+    if (gcpl) {
+        const int G = KM <= 8 ? 4 : 2;
+        const long long gw = (n_pix + G - 1) / G;
+        const unsigned gblocks = (unsigned)((gw * 32 + 255) / 256);
+#define GS_BLG(KMV, BF)                                                                                          \
+    blend_loss_group_launch<KMV, BF>(gcpl, gblocks, s, n_pix, K, nch, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, wf, wc, \
+                                     wd, invP, F, dLdF, dLdC, dLdD, part, err)
+        if (dtype == GS_BF16) {
+            switch (KM) { case 4: GS_BLG(4, true); break; case 8: GS_BLG(8, true); break; default: GS_BLG(16, true); }
+        } else {
+            switch (KM) { case 4: GS_BLG(4, false); break; case 8: GS_BLG(8, false); break; default: GS_BLG(16, false); }
+        }
+#undef GS_BLG
+    } else {
 #define GS_BK(KMV, BF) ok = blend_loss_cpl<KMV, BF>(cpl, blocks, n_pix, K, nch, l, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, \
                                                     wf, wc, wd, invP, F, dLdF, dLdC, dLdD, part, err, s)
     if (dtype == GS_BF16) {
@@ -378,6 +697,7 @@ bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_
         switch (KM) { case 4: GS_BK(4, false); break; case 8: GS_BK(8, false); break; case 16: GS_BK(16, false); break; default: GS_BK(32, false); }
     }
 #undef GS_BK
+    }
     if (!ok) return false;
     float *part2 = part + n_pix;
     k_sum_fixed<<<kSortBlocks, 1024, 0, s>>>(part, n_pix, part2);
