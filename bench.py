@@ -118,13 +118,14 @@ class Step:
         self.tgt = [t(fv, tdt)[lab].contiguous(), t(cv)[lab].contiguous(), t(dv)[lab].contiguous()]
         del lab
         self.N, self.P, self.D = sc.n, self.r.P, sc.d
-        # first forward checks the instance capacity once (host sync), then steps run free
+        # the first forward and backward check the instance and partial-row capacities
+        # once (host syncs, growing them if needed), then steps run free
         self.out = self.r.forward(*self.inp)
-        self.r.check_overflow = False
         self.lo = self.r.alloc_loss()
         self.r.blend_loss(self.inp[4], self.tgt[0], self.tgt[1], self.tgt[2], lo=self.lo)
         self.grads = self.r.alloc_grads(self.N)
         self.r.backward(self.lo["dL_dF"], self.lo["dL_dC"], self.lo["dL_dD"], grads=self.grads)
+        self.r.check_overflow = False
         torch.cuda.synchronize()
 
     def run(self, events=None):

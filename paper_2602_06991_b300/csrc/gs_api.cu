@@ -83,10 +83,15 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     if (mcap < 4096) mcap = 4096;
     if (mcap > 0x7fffffffll) mcap = 0x7fffffffll;
     L.Mcap = mcap;
-    L.use_tiles = tile_grad_supported(cfg->feat_dtype, cfg->D, cfg->K, cfg->tile_w, cfg->tile_h);
-    // partial feature-gradient rows: one per (tile, selected Gaussian), itself one of the
-    // instances, so never more than Mcap; sized for 128 per tile or Mcap / 32.
-    L.rows_cap = L.use_tiles ? std::min(mcap, std::max((long long)ct.n_tiles * 128, mcap / 32)) : 0;
+    L.use_tiles = tile_grad_supported(cfg->feat_dtype, cfg->D, cfg->K);
+    CamTable cb;
+    const FgBlock fb = fg_block_shape(cfg->feat_dtype, cfg->D, cfg->K);
+    if (L.use_tiles) retile(ct, fb.bw, fb.bh, cb);
+    L.n_fgblocks = L.use_tiles ? cb.n_tiles : 0;
+    // partial feature-gradient rows: one per (block, selected Gaussian), so never more
+    // than P K; sized for 32 per block or Mcap / 16, growing with max_instances (an
+    // overflow sets the error word and yields no feature gradient).
+    L.rows_cap = L.use_tiles ? std::min(L.PK, std::max((long long)L.n_fgblocks * 32, mcap / 16)) : 0;
     L.n_pairs = N + std::max(L.PK, L.rows_cap);
     if (L.NE > 0x7fffffffll || L.n_pairs > 0x7fffffffll) return false;
     L.max_pieces_rows = N + (L.rows_cap + kPieceLen - 1) / kPieceLen + 1;
@@ -133,9 +138,10 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     L.piece_rows = take(sizeof(float) * (size_t)L.max_multi_rows * cfg->D);
     L.loss_part = 0;
     if (L.use_tiles) {
-        L.tile_keys = take(8 * (size_t)ct.n_tiles * cfg->tile_w * cfg->tile_h * cfg->K);
-        L.tile_u = take(u * ct.n_tiles);
-        L.tile_rowbase = take(u * ct.n_tiles);
+        L.tile_keys = take(8 * (size_t)L.n_fgblocks * fb.bw * fb.bh * cfg->K);
+        L.tile_runs = take((size_t)L.n_fgblocks * tile_runs_bytes(fb.bw * fb.bh, cfg->K));
+        L.tile_u = take(u * L.n_fgblocks);
+        L.tile_rowbase = take(u * L.n_fgblocks);
         L.tile_rows = take(sizeof(float) * (size_t)L.rows_cap * cfg->D);
     }
     L.total = off;

@@ -126,11 +126,12 @@ struct Group {
 struct GroupTable {
     float w[32][4];                                       // distinct id x pixel
     int id[32];
+    signed char slot[32][4];                              // slot of the id in each pixel, -1 if absent
 };
 
 // Loads the group's (id, w') pairs, builds the distinct-id table of this warp and
 // returns the number of distinct ids.  Lane l holds pixel l / KM, slot l % KM.
-template <int KM, int G>
+template <int KM, int G, bool WITH_W = true>
 __device__ __forceinline__ int group_table(long long p0, long long n_pix, int K, const int *__restrict__ idx,
                                            const float *__restrict__ wts, bool bad, int lane, GroupTable &t)
 {
@@ -139,12 +140,14 @@ __device__ __forceinline__ int group_table(long long p0, long long n_pix, int K,
     int id = -1;
     float wn = 0.f;
     if (gl < G && kl < K && pl < n_pix && !bad) {
-        // S in slot order, exactly as the per-pixel kernels sum it
-        float S = 0.f;
-        for (int k = 0; k < K; ++k) S += __ldg(wts + pl * K + k);
-        const float inv = S > 0.f ? 1.f / S : 0.f;
         id = __ldg(idx + pl * K + kl);
-        wn = id >= 0 ? __ldg(wts + pl * K + kl) * inv : 0.f;
+        if (WITH_W) {
+            // S in slot order, exactly as the per-pixel kernels sum it
+            float S = 0.f;
+            for (int k = 0; k < K; ++k) S += __ldg(wts + pl * K + k);
+            const float inv = S > 0.f ? 1.f / S : 0.f;
+            wn = id >= 0 ? __ldg(wts + pl * K + kl) * inv : 0.f;
+        }
     }
     const unsigned same = __match_any_sync(0xffffffffu, id);
     const int first = __ffs(same) - 1;
@@ -152,12 +155,16 @@ __device__ __forceinline__ int group_table(long long p0, long long n_pix, int K,
     const int U = __popc(lead);
     if (lane < U) {
 #pragma unroll
-        for (int g = 0; g < 4; ++g) t.w[lane][g] = 0.f;
+        for (int g = 0; g < 4; ++g) {
+            t.w[lane][g] = 0.f;
+            t.slot[lane][g] = -1;
+        }
     }
     __syncwarp();
     if (id >= 0) {
         const int r = __popc(lead & ((1u << first) - 1u));
         t.w[r][gl] = wn;
+        t.slot[r][gl] = (signed char)kl;
         if (first == lane) t.id[r] = id;
     }
     __syncwarp();
@@ -328,6 +335,162 @@ bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, cons
     }
     if (dtype == GS_BF16) return blend_k<true>(KM, K, nch, n_pix, idx, w, feats, F, err, s);
     return blend_k<false>(KM, K, nch, n_pix, idx, w, feats, F, err, s);
+}
+
+// ------------------------------------------------------------------------------------
+// h_k(p) = dL/dF_p . f_{idx_k(p)} for every Top-K slot (the feature term of dL/dw used
+// by the re-walk of a5).  Pixel-group form: a warp holds the dL/dF rows of its G pixels
+// in registers, loads each distinct selected row once, forms the G partial dot products
+// per lane and reduces them over the warp with one reduce-scatter (lane l ends with the
+// total of pixel (l >> 3) & 3).  Per-pixel form (other widths, K > 16): a group of lanes
+// per pixel, one reduction per slot.
+// ------------------------------------------------------------------------------------
+template <int KM, bool BF16, int CPL>
+__global__ void __launch_bounds__(256) k_h_group(long long n_pix, int K, int nch, const int *__restrict__ idx,
+                                                 const void *__restrict__ feats, const void *__restrict__ dLdF,
+                                                 float *__restrict__ h, const int *__restrict__ err)
+{
+    using Ch = Chunk<BF16>;
+    constexpr int VEC = Ch::VEC;
+    constexpr int G = Group<KM>::G;
+    __shared__ GroupTable s_t[8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long p0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G;
+    if (p0 >= n_pix) return;                         // whole warp leaves together
+    const bool bad = err && *err;
+    GroupTable &t = s_t[wib];
+    const int U = group_table<KM, G, false>(p0, n_pix, K, idx, nullptr, bad, lane, t);
+    float d[G][CPL][VEC];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int ch = lane + 32 * c;
+            if (p0 + g < n_pix && ch < nch) Ch::load(dLdF, (size_t)(p0 + g) * nch + ch, d[g][c]);
+            else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) d[g][c][v] = 0.f;
+            }
+        }
+    auto load_row = [&](int u, float (&x)[CPL][VEC]) {
+        const size_t base = (size_t)t.id[u] * nch;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int ch = lane + 32 * c;
+            if (ch < nch) Ch::load(feats, base + ch, x[c]);
+            else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) x[c][v] = 0.f;
+            }
+        }
+    };
+    auto dot_row = [&](int u, const float (&x)[CPL][VEC]) {
+        float pd[4];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) pd[g] = 0.f;
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) pd[g] = fmaf(d[g][c][v], x[c][v], pd[g]);
+        // reduce-scatter of 4 values: lane l ends with the total of value (l >> 3) & 3
+        const bool b4 = lane & 16, b3 = lane & 8;
+        float a0 = (b4 ? pd[2] : pd[0]) + __shfl_xor_sync(0xffffffffu, b4 ? pd[0] : pd[2], 16);
+        float a1 = (b4 ? pd[3] : pd[1]) + __shfl_xor_sync(0xffffffffu, b4 ? pd[1] : pd[3], 16);
+        float r = (b3 ? a1 : a0) + __shfl_xor_sync(0xffffffffu, b3 ? a0 : a1, 8);
+        r += __shfl_xor_sync(0xffffffffu, r, 4);
+        r += __shfl_xor_sync(0xffffffffu, r, 2);
+        r += __shfl_xor_sync(0xffffffffu, r, 1);
+        const int g = (lane >> 3) & 3;
+        if ((lane & 7) == 0 && g < G) {
+            const int k = t.slot[u][g];
+            if (k >= 0) h[(p0 + g) * K + k] = r;
+        }
+    };
+    float xa[CPL][VEC], xb[CPL][VEC];
+    if (U > 0) load_row(0, xa);
+    for (int u = 0; u < U; u += 2) {
+        if (u + 1 < U) load_row(u + 1, xb);
+        dot_row(u, xa);
+        if (u + 1 < U) {
+            if (u + 2 < U) load_row(u + 2, xa);
+            dot_row(u + 1, xb);
+        }
+    }
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_h_pixel(long long n_pix, int K, int nch, int lpp_log2,
+                                                 const int *__restrict__ idx, const void *__restrict__ feats,
+                                                 const void *__restrict__ dLdF, float *__restrict__ h,
+                                                 const int *__restrict__ err)
+{
+    using Ch = Chunk<BF16>;
+    constexpr int VEC = Ch::VEC;
+    const int lane = threadIdx.x & 31;
+    const int lpp = 1 << lpp_log2;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    long long p = warp * (32 >> lpp_log2) + (lane >> lpp_log2);
+    const int sub = lane & (lpp - 1);
+    const bool live = p < n_pix;
+    if (!live) p = n_pix - 1;                        // keep every lane in the shuffles
+    const bool bad = err && *err;
+    for (int k = 0; k < K; ++k) {
+        const int id = bad ? -1 : __ldg(idx + p * K + k);
+        float part = 0.f;
+        if (id >= 0) {
+            for (int ch = sub; ch < nch; ch += lpp) {
+                float a[VEC], b[VEC];
+                Ch::load(dLdF, (size_t)p * nch + ch, a);
+                Ch::load(feats, (size_t)id * nch + ch, b);
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) part = fmaf(a[v], b[v], part);
+            }
+        }
+        for (int o = 1; o < lpp; o <<= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (live && sub == 0 && id >= 0) h[p * K + k] = part;
+    }
+}
+
+bool launch_h(int dtype, int K, int D, long long n_pix, const int *idx, const void *feats, const void *dLdF,
+              float *h, const int *err, cudaStream_t s)
+{
+    if (n_pix <= 0) return true;
+    const int KM = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
+    const int nch = dtype == GS_BF16 ? D / 8 : D / 4;
+    const int cpl = group_cpl(dtype, K, nch);
+    if (cpl) {
+        const int G = KM <= 8 ? 4 : 2;
+        const long long warps = (n_pix + G - 1) / G;
+        const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+#define GS_HG(KMV, BF)                                                                                            \
+    switch (cpl) {                                                                                                \
+    case 1: k_h_group<KMV, BF, 1><<<blocks, 256, 0, s>>>(n_pix, K, nch, idx, feats, dLdF, h, err); break;          \
+    case 2: k_h_group<KMV, BF, 2><<<blocks, 256, 0, s>>>(n_pix, K, nch, idx, feats, dLdF, h, err); break;          \
+    case 4:                                                                                                       \
+        if constexpr (GroupFits<KMV, BF, 4>::value)                                                                \
+            k_h_group<KMV, BF, 4><<<blocks, 256, 0, s>>>(n_pix, K, nch, idx, feats, dLdF, h, err);                 \
+        break;                                                                                                    \
+    case 8:                                                                                                       \
+        if constexpr (GroupFits<KMV, BF, 8>::value)                                                                \
+            k_h_group<KMV, BF, 8><<<blocks, 256, 0, s>>>(n_pix, K, nch, idx, feats, dLdF, h, err);                 \
+        break;                                                                                                    \
+    }
+        if (dtype == GS_BF16) {
+            switch (KM) { case 4: GS_HG(4, true); break; case 8: GS_HG(8, true); break; default: GS_HG(16, true); }
+        } else {
+            switch (KM) { case 4: GS_HG(4, false); break; case 8: GS_HG(8, false); break; default: GS_HG(16, false); }
+        }
+#undef GS_HG
+        return true;
+    }
+    const int l = lpp_log2_for(nch);
+    const long long warps = (n_pix + (32 >> l) - 1) / (32 >> l);
+    const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+    if (dtype == GS_BF16) k_h_pixel<true><<<blocks, 256, 0, s>>>(n_pix, K, nch, l, idx, feats, dLdF, h, err);
+    else k_h_pixel<false><<<blocks, 256, 0, s>>>(n_pix, K, nch, l, idx, feats, dLdF, h, err);
+    return true;
 }
 
 // ------------------------------------------------------------------------------------

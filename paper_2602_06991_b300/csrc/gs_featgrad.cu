@@ -136,9 +136,13 @@ __global__ void k_markers(int N, uint32_t *keys, uint32_t *vals)
     }
 }
 
-__global__ void k_pair_count(int N, const uint32_t *u_tot, uint32_t rows_cap, uint32_t *n_pairs)
+// Pairs to sort: the N markers and one per partial row.  When the rows overflowed their
+// capacity (or any earlier stage failed) no row is trusted: only the markers are sorted,
+// the feature gradient comes out zero and the error word reports the overflow.
+__global__ void k_pair_count(int N, const uint32_t *u_tot, uint32_t rows_cap, const int *err, uint32_t *n_pairs)
 {
-    *n_pairs = (uint32_t)N + min(*u_tot, rows_cap);
+    const bool ok = *err == 0 && *u_tot <= rows_cap;
+    *n_pairs = (uint32_t)N + (ok ? *u_tot : 0u);
 }
 
 __global__ void k_pieces(int N, const uint32_t *__restrict__ seg_start, const uint32_t *__restrict__ seg_end,
@@ -382,8 +386,7 @@ static bool fgrad_main(int cpl, unsigned blocks, cudaStream_t s, int K, int nch,
 static int cpl_for(int nch) { return nch <= 32 ? 1 : nch <= 64 ? 2 : nch <= 128 ? 4 : 8; }
 
 bool launch_tile_grad(const CamTable &ct, const WsLayout &L, int dtype, const int *topk_idx, const float *topk_w,
-                      const void *feats, const void *dLdF, void *ws, cudaStream_t s);
-bool tile_grad_supported(int dtype, int D, int K, int tw, int th);
+                      const void *dLdF, void *ws, cudaStream_t s);
 
 // Tile-major path: T1-T3 in gs_tilegrad.cu, then the per-Gaussian reduction of the
 // partial rows (row mode of the segmented reduction).
@@ -406,9 +409,12 @@ static bool feature_grad_tiles(const CamTable &ct, const WsLayout &L, int dtype,
     float *trows = ws_ptr<float>(ws, L.tile_rows);
     const unsigned nbN = (unsigned)((N + 255) / 256);
 
-    if (!launch_tile_grad(ct, L, dtype, topk_idx, topk_w, feats, dLdF, ws, s)) return false;
+    // h = dL/dF . f per slot for the re-walk, then the per-block partial rows
+    if (!launch_h(dtype, L.K, L.D, L.P, topk_idx, feats, dLdF, ws_ptr<float>(ws, L.hbuf), (const int *)hdr, s))
+        return false;
+    if (!launch_tile_grad(ct, L, dtype, topk_idx, topk_w, dLdF, ws, s)) return false;
     k_markers<<<nbN, 256, 0, s>>>(N, pk[0], pv[0]);
-    k_pair_count<<<1, 1, 0, s>>>(N, u_tot, (uint32_t)L.rows_cap, n_pairs_dev);
+    k_pair_count<<<1, 1, 0, s>>>(N, u_tot, (uint32_t)L.rows_cap, (const int *)hdr, n_pairs_dev);
     const long long n_host = N + L.rows_cap;
     int pcur = radix_sort_pairs(pk[0], pk[1], pv[0], pv[1], n_host, n_pairs_dev, L.pair_bits, hist, s);
     k_segments<<<(unsigned)((n_host + 255) / 256), 256, 0, s>>>(N, n_host, n_pairs_dev, pk[pcur], pv[pcur], seg_start,

@@ -228,7 +228,8 @@ struct WsLayout {
     size_t piece_rank;         // max_pieces
     size_t piece_rows;         // max_multi_rows x D floats
     size_t loss_part;          // unused (the loss takes caller scratch)
-    size_t tile_keys;          // n_tiles x B K uint64 sorted (Gaussian, slot) keys (tile-major feature gradient)
+    size_t tile_keys;          // n_fgblocks x B K uint2 slot records (pixel | run << 16, w') in sorted order
+    size_t tile_runs;          // n_fgblocks x runs_stride uint2 run tables (first position, Gaussian id)
     size_t tile_u, tile_rowbase; // n_tiles each
     size_t tile_rows;          // rows_cap x D floats: partial feature-gradient rows per (tile, Gaussian)
     size_t total;
@@ -240,6 +241,7 @@ struct WsLayout {
     long long NE, P, PK, Mcap, n_pairs, max_pieces, max_multi_rows;
     long long rows_cap, max_pieces_rows;
     bool use_tiles;
+    long long n_fgblocks;      // feature-gradient pixel blocks (fg_block_shape) over all cameras
     int N, K, D, n_tiles, n_cams;
 };
 
@@ -281,7 +283,17 @@ bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, cons
 bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N, const float *mean3d,
                          const int *topk_idx, const float *topk_w, const void *feats, const void *dLdF,
                          float *grad_feat, void *ws, cudaStream_t s);
-bool tile_grad_supported(int dtype, int D, int K, int tw, int th);
+bool tile_grad_supported(int dtype, int D, int K);
+// Feature-gradient pixel blocks: the largest of 8x8, 8x4, 4x4 whose dL/dF rows fit one
+// 64 KB shared-memory stage ({0, 0}: none).
+struct FgBlock {
+    int bw, bh;
+};
+FgBlock fg_block_shape(int dtype, int D, int K);
+size_t tile_runs_bytes(int B, int K);
+void retile(const CamTable &ct, int bw, int bh, CamTable &out);
+bool launch_h(int dtype, int K, int D, long long n_pix, const int *idx, const void *feats, const void *dLdF,
+              float *h, const int *err, cudaStream_t s);
 bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_pix, const int *idx, const float *w,
                        const void *feats, const void *Fgt, const float *C, const float *Cgt, const float *Dp,
                        const float *Dgt, float wf, float wc, float wd, void *F, void *dLdF, float *dLdC, float *dLdD,

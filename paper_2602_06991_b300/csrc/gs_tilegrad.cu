@@ -1,71 +1,122 @@
-// gs_tilegrad.cu -- feature part of a5, tile-major: every dL/dF row is read from HBM
-// once.
+// gs_tilegrad.cu -- feature part of a5, block-major: every dL/dF row is read from HBM
+// once and re-read only from shared memory.
 //
 //   dL/df_g = sum over (pixel p, slot k) with idx_k(p) = g of w'_k(p) dL/dF_p     (Eqs. 3-4)
-//   h_k(p)  = dL/dF_p . f_{idx_k(p)}     (needed by the re-walk for dL/dw of Top-K members)
 //
-// Stage T1 (k_tile_slots): one CTA per screen tile sorts the tile's (Gaussian, slot)
-//   keys in shared memory (bitonic: deterministic), stores them, and counts the distinct
-//   Gaussians U_t selected in the tile.
-// Stage T2: exclusive scan of U_t over tiles gives every (tile, Gaussian) its partial
-//   row -- deterministic, no atomics.  A (tile, Gaussian) selection is always one of the
-//   binning instances, so the row count is bounded by the instance count.
-// Stage T3 (k_tile_accum): one 512-thread CTA per tile and per SM.  Each warp takes an
-//   equal contiguous share of the tile's sorted slots and processes whole rows (16 B
-//   per lane per 128-column chunk, all chunks of a row at once): it sums w' dL/dF over
-//   the slots of each Gaussian in registers and forms the slot dot products h (one
-//   reduce-scatter per 8 slots).  A Gaussian whose slots straddle warps is finished in
-//   fixed order from shared-memory edge rows.  The tile's dL/dF rows are read from HBM
-//   once and then re-read K times from L2 while the CTA lives: one CTA per SM keeps
-//   148 x 512 KB of rows resident in the 126 MB L2.  (Staging 256-byte column slices in
-//   shared memory with TMA was measured slower: the slices are too narrow to amortise
-//   the per-slot work.)
+// (h_k(p) = dL/dF_p . f_{idx_k(p)}, needed by the re-walk, comes from the pixel-group
+// kernel k_h_group in gs_blend.cu.)
+//
+// The screen is cut into small pixel blocks (8x8, 8x4 or 4x4, the largest whose dL/dF
+// rows fit one 64 KB shared-memory stage with at most 512 slots), independent of the
+// binning tile.
+// Stage T1 (k_tile_slots): one CTA per block sorts the block's (Gaussian, slot) keys in
+//   shared memory (bitonic: deterministic) and writes, in sorted order, one record per
+//   slot (pixel, run, renormalised weight) and one entry per run of equal Gaussians
+//   (first position, id); U_b = the number of runs.
+// Stage T2: exclusive scan of U_b over blocks gives every (block, Gaussian) its partial
+//   row -- deterministic, no atomics.
+// Stage T3 (k_block_accum): a persistent CTA per SM walks blocks.  While it reduces one
+//   block, the dL/dF rows (tensor-map TMA boxes), records and run table (bulk copies) of
+//   its next block stream into the other shared-memory stage, completing on an
+//   mbarrier, so no global round trip sits on the path.  Each warp takes an equal contiguous share of the block's sorted
+//   slots and sums w' dL/dF over the slots of each Gaussian in registers, whole rows at
+//   a time (16 B per lane per 128-column chunk) read from shared memory.  A Gaussian
+//   whose slots straddle warps is finished in fixed order from shared-memory edge rows.
 // Stage T4: the partial rows are reduced per Gaussian by the sort-by-Gaussian segmented
-//   reduction of gs_featgrad.cu in row mode (weight 1, no h).
+//   reduction of gs_featgrad.cu in row mode.
 #include "gs_internal.cuh"
+
+#include <cuda.h>
+#include <mutex>
+#include <string.h>
 
 namespace gs {
 
 constexpr unsigned long long kKeyInvalid = ~0ull;
+constexpr int kStageMax = 64 * 1024;            // bytes of dL/dF rows per block stage
+
+FgBlock fg_block_shape(int dtype, int D, int K)
+{
+    // the rows of a block (in 256-element TMA box rows) fit one 64 KB stage and its slots
+    // number at most 512
+    const int row = (D < 256 ? D : (D + 255) / 256 * 256) * (dtype == GS_BF16 ? 2 : 4);
+    if (64 * row <= kStageMax && 64 * K <= 512) return {8, 8};
+    if (32 * row <= kStageMax && 32 * K <= 512) return {8, 4};
+    if (16 * row <= kStageMax && 16 * K <= 512) return {4, 4};
+    return {0, 0};
+}
+
+void retile(const CamTable &ct, int bw, int bh, CamTable &out)
+{
+    out = ct;
+    out.tile_w = bw;
+    out.tile_h = bh;
+    int off = 0;
+    for (int c = 0; c < ct.n; ++c) {
+        CamDev &d = out.c[c];
+        d.tiles_x = (d.W + bw - 1) / bw;
+        d.tiles_y = (d.H + bh - 1) / bh;
+        d.tile_off = off;
+        off += d.tiles_x * d.tiles_y;
+    }
+    out.n_tiles = off;
+}
 
 // ------------------------------------------------------------------------------------
-// T1: per-tile sort of (Gaussian id << 16 | slot) keys
+// T1: per-block sort of (Gaussian id << 16 | slot) keys, then the block's slot records
+// and run table, so that T3 reads everything it needs as two contiguous arrays.
+//   rec[i]  (sorted position i < B K): x = pixel | run << 16, y = bits of w' (Eq. 3)
+//   runs[u] (u < U_b): x = first sorted position, y = Gaussian id;  runs[U_b].x = the
+//           number of valid positions
 // ------------------------------------------------------------------------------------
-constexpr int kSortNT = 1024;
+static __host__ __device__ __forceinline__ int runs_stride(int nslots) { return (nslots + 2) & ~1; }
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(kSortNT) k_tile_slots(CamTable ct, int K, int nsort, const int *__restrict__ topk_idx,
-                                                        const int *__restrict__ err,
-                                                        unsigned long long *__restrict__ tile_keys,
-                                                        uint32_t *__restrict__ tile_u)
+__global__ void __launch_bounds__(1024) k_tile_slots(CamTable ct, int K, int nsort, const int *__restrict__ topk_idx,
+                                                     const float *__restrict__ topk_w, const int *__restrict__ err,
+                                                     uint2 *__restrict__ rec, uint2 *__restrict__ runs,
+                                                     uint32_t *__restrict__ tile_u)
 {
     constexpr int B = TW * TH;
-    extern __shared__ unsigned long long s_keys[];           // nsort (power of two >= B K)
-    __shared__ uint32_t s_red[kSortNT / 32];
-    const int tid = threadIdx.x;
+    extern __shared__ unsigned long long s_keys[];           // nsort (power of two >= B K), then B K floats
+    __shared__ uint32_t s_red[32];
+    __shared__ uint32_t s_total;
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int nslots = B * K;
+    float *s_w = (float *)(s_keys + nsort);                  // w per slot, then w' in place
     const int tile = blockIdx.x;
     const int c = cam_of_tile(ct, tile);
     const CamDev &cam = ct.c[c];
     const int lt = tile - cam.tile_off;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
     const bool bad = *err != 0;
-    for (int i = tid; i < nsort; i += kSortNT) {
+    for (int i = tid; i < nsort; i += NT) {
         unsigned long long key = kKeyInvalid;
         int pl = i / K, k = i - pl * K;
-        if (i < B * K && !bad) {
+        if (i < nslots) s_w[i] = 0.f;
+        if (i < nslots && !bad) {
             int px = tx * TW + (pl % TW), py = ty * TH + (pl / TW);
             if (px < cam.W && py < cam.H) {
                 long long p = cam.pix_off + (long long)py * cam.W + px;
                 int id = topk_idx[p * K + k];
+                s_w[i] = topk_w[p * K + k];
                 if (id >= 0) key = ((unsigned long long)(uint32_t)id << 16) | (unsigned long long)i;
             }
         }
         s_keys[i] = key;
     }
     __syncthreads();
+    // renormalised weights w' = w / S per pixel (S in slot order)
+    for (int pl = tid; pl < B; pl += NT) {
+        float S = 0.f;
+        for (int k = 0; k < K; ++k) S += s_w[pl * K + k];
+        const float inv = S > 0.f ? 1.f / S : 0.f;
+        for (int k = 0; k < K; ++k) s_w[pl * K + k] *= inv;
+    }
     for (int size = 2; size <= nsort; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = tid; i < nsort / 2; i += kSortNT) {
+            __syncthreads();
+            for (int i = tid; i < nsort / 2; i += NT) {
                 int lo = 2 * i - (i & (stride - 1));
                 int hi = lo + stride;
                 bool up = (lo & size) == 0;
@@ -75,49 +126,134 @@ __global__ void __launch_bounds__(kSortNT) k_tile_slots(CamTable ct, int K, int 
                     s_keys[hi] = a;
                 }
             }
-            __syncthreads();
         }
     }
-    const int nslots = B * K;
+    __syncthreads();
+    // run index of every sorted position: each thread a contiguous group of positions,
+    // a block scan of the run-start counts
+    const int PPT = (nslots + NT - 1) / NT;
+    const int i_lo = min(tid * PPT, nslots), i_hi = min(i_lo + PPT, nslots);
     uint32_t cnt = 0;
-    for (int i = tid; i < nslots; i += kSortNT) {
-        unsigned long long key = s_keys[i];
-        tile_keys[(size_t)tile * nslots + i] = key;
-        if (key != kKeyInvalid && (i == 0 || (s_keys[i - 1] >> 16) != (key >> 16))) ++cnt;
+    for (int i = i_lo; i < i_hi; ++i) {
+        const unsigned long long key = s_keys[i];
+        cnt += key != kKeyInvalid && (i == 0 || (s_keys[i - 1] >> 16) != (key >> 16));
     }
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if ((tid & 31) == 0) s_red[tid >> 5] = cnt;
+    uint32_t inc = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_red[warp] = inc;
     __syncthreads();
     if (tid == 0) {
         uint32_t t = 0;
-        for (int w = 0; w < kSortNT / 32; ++w) t += s_red[w];
-        tile_u[tile] = t;
+        for (int w = 0; w < NT / 32; ++w) {
+            const uint32_t v = s_red[w];
+            s_red[w] = t;
+            t += v;
+        }
+        s_total = t;
+    }
+    __syncthreads();
+    int u = (int)(s_red[warp] + inc - cnt) - 1;               // runs started before i_lo, minus 1
+    uint2 *brec = rec + (size_t)tile * nslots;
+    uint2 *bruns = runs + (size_t)tile * runs_stride(nslots);
+    for (int i = i_lo; i < i_hi; ++i) {
+        const unsigned long long key = s_keys[i];
+        uint2 r = make_uint2(0u, 0u);
+        if (key != kKeyInvalid) {
+            if (i == 0 || (s_keys[i - 1] >> 16) != (key >> 16)) {
+                ++u;
+                bruns[u] = make_uint2((uint32_t)i, (uint32_t)(key >> 16));
+            }
+            const int sl = (int)(key & 0xffffull);
+            r = make_uint2((uint32_t)(sl / K) | ((uint32_t)u << 16), __float_as_uint(s_w[sl]));
+        } else if (i == 0 || s_keys[i - 1] != kKeyInvalid) {
+            bruns[s_total] = make_uint2((uint32_t)i, 0u);      // end of the valid positions
+        }
+        brec[i] = r;
+    }
+    if (tid == 0) {
+        tile_u[tile] = s_total;
+        if (s_keys[nslots - 1] != kKeyInvalid) bruns[s_total] = make_uint2((uint32_t)nslots, 0u);
     }
 }
 
 // ------------------------------------------------------------------------------------
-// T3: per-tile accumulation, whole rows per slot, re-reads served by L2
+// T3: per-block accumulation from shared-memory stages filled by TMA
 // ------------------------------------------------------------------------------------
-constexpr int kAccNT = 512;
-constexpr int kAccNW = kAccNT / 32;
+constexpr int kBlkNT = 256;
+constexpr int kBlkNW = kBlkNT / 32;
+constexpr int kTmaInner = 256;                       // elements per TMA box row (box limit)
+constexpr long long kWaitCycles = 2000000000ll;      // bounded mbarrier wait (~1 s)
+
+struct alignas(64) TmaMaps {
+    CUtensorMap m[GS_MAX_CAMERAS];                   // dL/dF of each camera as [H][W][D]
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Waits for the phase with the given parity to complete; false after kWaitCycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"((unsigned long long)src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
 
 template <bool BF16>
-struct Row16;
+struct SRow;
 template <>
-struct Row16<false> {     // 16 bytes = 4 floats
+struct SRow<false> {      // 16 bytes = 4 floats, from shared memory
     static constexpr int VEC = 4;
-    __device__ __forceinline__ static void load(const void *base, size_t chunk, float (&x)[4])
+    __device__ __forceinline__ static void load(const unsigned char *p, float (&x)[4])
     {
-        float4 v = __ldg((const float4 *)base + chunk);
+        const float4 v = *(const float4 *)p;
         x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
     }
 };
 template <>
-struct Row16<true> {      // 16 bytes = 8 bf16
+struct SRow<true> {       // 16 bytes = 8 bf16
     static constexpr int VEC = 8;
-    __device__ __forceinline__ static void load(const void *base, size_t chunk, float (&x)[8])
+    __device__ __forceinline__ static void load(const unsigned char *p, float (&x)[8])
     {
-        uint4 v = __ldg((const uint4 *)base + chunk);
+        const uint4 v = *(const uint4 *)p;
         const __nv_bfloat162 *h = (const __nv_bfloat162 *)&v;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -128,244 +264,169 @@ struct Row16<true> {      // 16 bytes = 8 bf16
     }
 };
 
-// Dynamic shared memory: edge rows [kAccNW][2][D] f32, then per sorted position (B K):
-// pixel (u16), run (u16), weight (f32), h (f32); per run: start (u16, + 1), id (u32).
-size_t tile_accum_smem(int B, int K, int D)
+// Row geometry of a stage: a block's dL/dF rows arrive as ncol TMA boxes of
+// [TH][TW][inner] elements (inner = min(D, 256)); chunk ch (16 bytes) of pixel pl sits at
+// (ch / cpb) * B * inner * esz + pl * inner * esz + (ch % cpb) * 16, cpb = inner esz / 16.
+static int tma_inner(int D) { return D < kTmaInner ? D : kTmaInner; }
+static int tma_ncol(int D) { return (D + kTmaInner - 1) / kTmaInner; }
+
+// One stage: the rows, the block's records (B K uint2) and run table (runs_stride uint2),
+// 128-byte aligned.  Dynamic shared memory: kStages stages.
+constexpr int kStages = 3;
+
+static size_t stage_bytes(int B, int K, int dtype, int D)
 {
-    size_t n = (size_t)B * K;
-    return (size_t)kAccNW * 2 * D * 4 + 2 * n * 2 + 16 + 4 * n * 2 + 2 * (n + 1) + 16 + 4 * n + 64;
+    const size_t rows = (size_t)tma_ncol(D) * B * tma_inner(D) * (dtype == GS_BF16 ? 2 : 4);
+    const size_t b = rows + 8 * (size_t)B * K + 8 * (size_t)runs_stride(B * K);
+    return (b + 127) & ~(size_t)127;
 }
 
+size_t block_accum_smem(int B, int K, int D, int dtype) { return 128 + kStages * stage_bytes(B, K, dtype, D); }
+
+// Each warp owns whole runs (runs w, w + 8, ...): a run -- one Gaussian's slots in the
+// block, at most B -- is summed by one warp in slot order and written as its partial
+// row, so the result does not depend on the warp count and needs no cross-warp merge.
 template <int TW, int TH, bool BF16, int CPL>
-__global__ void __launch_bounds__(kAccNT, 1) k_tile_accum(CamTable ct, int K, int D, const float *__restrict__ topk_w,
-                                                          const unsigned long long *__restrict__ tile_keys,
-                                                          const uint32_t *__restrict__ row_base,
-                                                          const uint32_t *__restrict__ tile_u, uint32_t rows_cap,
-                                                          const void *__restrict__ feats,
-                                                          const void *__restrict__ dLdF, float *__restrict__ rows,
-                                                          uint32_t *__restrict__ pair_keys,
-                                                          uint32_t *__restrict__ pair_vals, int N,
-                                                          float *__restrict__ hbuf, int *err)
+__global__ void __launch_bounds__(kBlkNT, 1) k_block_accum(const __grid_constant__ TmaMaps maps, CamTable cb, int K,
+                                                           int D, int st_sz, const uint2 *__restrict__ rec,
+                                                           const uint2 *__restrict__ runs,
+                                                           const uint32_t *__restrict__ row_base,
+                                                           const uint32_t *__restrict__ tile_u, uint32_t rows_cap,
+                                                           float *__restrict__ rows, uint32_t *__restrict__ pair_keys,
+                                                           uint32_t *__restrict__ pair_vals, int N, int *err)
 {
     constexpr int B = TW * TH;
-    using Rw = Row16<BF16>;
+    using Rw = SRow<BF16>;
     constexpr int VEC = Rw::VEC;
-    // slots whose rows are in flight together: 32 registers of row data per lane
-    constexpr int DEPTH = CPL * VEC >= 32 ? 1 : 32 / (CPL * VEC);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ uint32_t s_scan[kAccNW];
-    __shared__ int s_nu, s_nvalid;
+    constexpr int ESZ = BF16 ? 2 : 4;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t s_bar[kStages];
     const int nslots = B * K;
+    const int rstride = runs_stride(nslots);
     const int nch = D / VEC;                           // 16-byte chunks per row
-    float *s_edge = (float *)smem_raw;                 // [kAccNW][2][D]
-    uint16_t *s_pl = (uint16_t *)(s_edge + (size_t)kAccNW * 2 * D);
-    uint16_t *s_run = s_pl + nslots;
-    float *s_wn = (float *)(((uintptr_t)(s_run + nslots) + 15) & ~(uintptr_t)15);
-    float *s_h = s_wn + nslots;
-    uint16_t *s_ustart = (uint16_t *)(s_h + nslots);
-    uint32_t *s_uid = (uint32_t *)(((uintptr_t)(s_ustart + nslots + 1) + 15) & ~(uintptr_t)15);
-
+    const int inner = D < kTmaInner ? D : kTmaInner;
+    const int ncol = (D + kTmaInner - 1) / kTmaInner;
+    const int cpb = inner * ESZ / 16;                  // chunks per box row
+    const int pix_bytes = inner * ESZ;
+    const int col_bytes = B * pix_bytes;
+    const int rows_sz = ncol * col_bytes;
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
-    const int c = cam_of_tile(ct, tile);
-    const CamDev &cam = ct.c[c];
-    const int lt = tile - cam.tile_off;
-    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    const uint32_t U = tile_u[tile];
-    const uint32_t rb = row_base[tile];
-    if (*err != 0 || U == 0) return;
-    if (rb + U > rows_cap) {
-        if (tid == 0) atomicOr(err, kErrOverflow);
-        return;
+    const int n_blocks = cb.n_tiles;
+    const int G = gridDim.x;
+    const uint32_t stage_tx = (uint32_t)(rows_sz + 8 * nslots + 8 * rstride);
+
+    if (tid == 0) {
+        for (int i = 0; i < kStages; ++i) mbar_init(&s_bar[i], 1);
+        fence_mbar_init();
     }
-    auto pixel_of = [&](int pl) -> long long {
-        return cam.pix_off + (long long)(ty * TH + pl / TW) * cam.W + tx * TW + pl % TW;
-    };
-    // renormalised weights per slot (Eq. 3), staged in s_h
-    for (int pl = tid; pl < B; pl += kAccNT) {
-        const int px = tx * TW + (pl % TW), py = ty * TH + (pl / TW);
-        if (px < cam.W && py < cam.H) {
-            const long long p = pixel_of(pl);
-            float S = 0.f;
-            for (int k = 0; k < K; ++k) S += topk_w[p * K + k];
-            const float inv = S > 0.f ? 1.f / S : 0.f;
-            for (int k = 0; k < K; ++k) s_h[pl * K + k] = topk_w[p * K + k] * inv;
-        }
-    }
-    __syncthreads();
-    // sorted positions: each thread a contiguous block of PPT positions; run starts by a
-    // block scan of (starts << 16 | valid) counts
-    const int PPT = (nslots + kAccNT - 1) / kAccNT;
-    const int i_lo = min(tid * PPT, nslots), i_hi = min(i_lo + PPT, nslots);
-    const unsigned long long *keys = tile_keys + (size_t)tile * nslots;
-    {
-        uint32_t n_start = 0, n_valid = 0;
-        unsigned long long prev = i_lo > 0 ? keys[i_lo - 1] : kKeyInvalid;
-        for (int i = i_lo; i < i_hi; ++i) {
-            const unsigned long long key = keys[i];
-            const bool valid = key != kKeyInvalid;
-            const int sl = (int)(key & 0xffffull);
-            s_pl[i] = valid ? (uint16_t)(sl / K) : (uint16_t)0;
-            s_wn[i] = valid ? s_h[sl] : 0.f;
-            n_valid += valid;
-            n_start += valid && (i == 0 || (prev >> 16) != (key >> 16));
-            prev = key;
-        }
-        uint32_t packed = (n_start << 16) | n_valid, inc = packed;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) s_scan[warp] = inc;
-        __syncthreads();                                  // also: every staged weight has been read
-        uint32_t before = inc - packed;
-        for (int w = 0; w < warp; ++w) before += s_scan[w];
-        if (tid == kAccNT - 1) {
-            uint32_t tot = before + packed;
-            s_nu = (int)(tot >> 16);
-            s_nvalid = (int)(tot & 0xffffu);
-        }
-        int u = (int)(before >> 16) - 1;
-        prev = i_lo > 0 ? keys[i_lo - 1] : kKeyInvalid;
-        for (int i = i_lo; i < i_hi; ++i) {
-            const unsigned long long key = keys[i];
-            if (key != kKeyInvalid && (i == 0 || (prev >> 16) != (key >> 16))) {
-                ++u;
-                s_ustart[u] = (uint16_t)i;
-                s_uid[u] = (uint32_t)(key >> 16);
-            }
-            s_run[i] = (uint16_t)(u < 0 ? 0 : u);
-            s_h[i] = 0.f;
-            prev = key;
-        }
-    }
-    __syncthreads();
-    const int nu = s_nu, nvalid = s_nvalid;
-    if (tid == 0) s_ustart[nu] = (uint16_t)nvalid;
     __syncthreads();
 
-    // warp w owns sorted positions [a, b)
-    const int R = (nvalid + kAccNW - 1) / kAccNW;
-    const int a = min(warp * R, nvalid), b = min(a + R, nvalid);
-    float acc[CPL][VEC], f[CPL][VEC];
-    int cur = -1, seg0 = a;
-    auto flush = [&](int end) {
-        // segment [seg0, end) of run cur: whole run -> its partial row; cut -> edge row
-        const bool cutL = seg0 == a && a > s_ustart[cur];
-        const bool cutR = end == b && b < s_ustart[cur + 1];
-        float *dst = !cutL && !cutR ? rows + (size_t)(rb + cur) * D
-                                    : s_edge + ((size_t)warp * 2 + (cutL ? 0 : 1)) * D;
-#pragma unroll
-        for (int cc = 0; cc < CPL; ++cc) {
-            const int ch = lane + 32 * cc;
-            if (ch < nch) {
-                float4 *d4 = (float4 *)(dst + (size_t)ch * VEC);
-#pragma unroll
-                for (int v = 0; v < VEC / 4; ++v)
-                    d4[v] = make_float4(acc[cc][4 * v], acc[cc][4 * v + 1], acc[cc][4 * v + 2], acc[cc][4 * v + 3]);
-            }
-        }
+    // thread 0: start the copies of block blk into stage sidx
+    auto issue = [&](int blk, int sidx) {
+        unsigned char *st = base + (size_t)sidx * st_sz;
+        const int c = cam_of_tile(cb, blk);
+        const CamDev &cam = cb.c[c];
+        const int lt = blk - cam.tile_off;
+        const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+        fence_async_shared();
+        mbar_expect_tx(&s_bar[sidx], stage_tx);
+        for (int col = 0; col < ncol; ++col)
+            tma_load_3d(st + (size_t)col * col_bytes, &maps.m[c], col * inner, tx * TW, ty * TH, &s_bar[sidx]);
+        bulk_load(st + rows_sz, rec + (size_t)blk * nslots, 8u * nslots, &s_bar[sidx]);
+        bulk_load(st + rows_sz + 8 * nslots, runs + (size_t)blk * rstride, 8u * rstride, &s_bar[sidx]);
     };
-    for (int j0 = 0; j0 < R; j0 += 8) {
-        float dot[8];
+
+    // blocks of this CTA: blockIdx.x + j G, j = 0, 1, ...; block j lives in stage j % kStages
+    const int my_n = (int)((n_blocks - (int)blockIdx.x + G - 1) / G);
+    uint32_t parity = 0;                             // bit s: parity of stage s's next completion
+    int issued = 0;                                  // blocks whose copies were started
+    uint32_t Uq[kStages], rbq[kStages];              // (U, row base) of the blocks in the stages
+    for (; issued < kStages - 1 && issued < my_n; ++issued) {
+        const int blk = blockIdx.x + issued * G;
+        if (tid == 0) issue(blk, issued % kStages);
+        Uq[issued % kStages] = tile_u[blk];
+        rbq[issued % kStages] = row_base[blk];
+    }
+    int j = 0;
+    bool timed_out = false;
+    for (; j < my_n; ++j) {
+        const int sidx = j % kStages;
+        if (issued < my_n) {                         // keep kStages - 1 blocks in flight
+            const int blk = blockIdx.x + issued * G;
+            if (tid == 0) issue(blk, issued % kStages);
+            Uq[issued % kStages] = tile_u[blk];
+            rbq[issued % kStages] = row_base[blk];
+            ++issued;
+        }
+        const bool ok = mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u);
+        if (ok) parity ^= 1u << sidx;
+        const uint32_t U = Uq[sidx], rb = rbq[sidx];
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(err, kErrTimeout);
+            timed_out = true;
+            break;
+        }
+        const bool over = U > 0 && rb + U > rows_cap;
+        if (over && tid == 0) atomicOr(err, kErrOverflow);
+        const bool skip = __syncthreads_or(*(volatile int *)err != 0) || U == 0 || over;
+        if (!skip) {
+            const unsigned char *st = base + (size_t)sidx * st_sz;
+            const uint2 *s_rec = (const uint2 *)(st + rows_sz);
+            const uint2 *s_runs = (const uint2 *)(st + rows_sz + 8 * nslots);
+            int coff[CPL];                           // stage offset of each lane chunk
 #pragma unroll
-        for (int h4 = 0; h4 < 8; h4 += DEPTH) {
-            // issue the row loads of DEPTH slots before any of their arithmetic
-            float x[DEPTH][CPL][VEC];
+            for (int cc = 0; cc < CPL; ++cc) {
+                const int ch = lane + 32 * cc;
+                coff[cc] = (ch / cpb) * col_bytes + (ch % cpb) * 16;
+            }
+            for (int u = warp; u < (int)U; u += kBlkNW) {
+                const int i0 = (int)s_runs[u].x, i1 = (int)s_runs[u + 1].x;
+                float acc[CPL][VEC];
 #pragma unroll
-            for (int q = 0; q < DEPTH; ++q) {
-                const int i = a + j0 + h4 + q;
-                const long long p = i < b ? pixel_of(s_pl[i]) : 0;
+                for (int cc = 0; cc < CPL; ++cc)
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) acc[cc][v] = 0.f;
+                for (int i = i0; i < i1; ++i) {
+                    const uint2 r = s_rec[i];
+                    const float wp = __uint_as_float(r.y);
+                    const unsigned char *px = st + (size_t)(r.x & 0xffffu) * pix_bytes;
+#pragma unroll
+                    for (int cc = 0; cc < CPL; ++cc) {
+                        if (lane + 32 * cc < nch) {
+                            float x[VEC];
+                            Rw::load(px + coff[cc], x);
+#pragma unroll
+                            for (int v = 0; v < VEC; ++v) acc[cc][v] = fmaf(wp, x[v], acc[cc][v]);
+                        }
+                    }
+                }
+                float *dst = rows + (size_t)(rb + u) * D;
 #pragma unroll
                 for (int cc = 0; cc < CPL; ++cc) {
                     const int ch = lane + 32 * cc;
-                    if (i < b && ch < nch) Rw::load(dLdF, (size_t)p * nch + ch, x[q][cc]);
-                    else {
+                    if (ch < nch) {
+                        float4 *d4 = (float4 *)(dst + (size_t)ch * VEC);
 #pragma unroll
-                        for (int v = 0; v < VEC; ++v) x[q][cc][v] = 0.f;
+                        for (int v = 0; v < VEC / 4; ++v)
+                            d4[v] = make_float4(acc[cc][4 * v], acc[cc][4 * v + 1], acc[cc][4 * v + 2],
+                                                acc[cc][4 * v + 3]);
                     }
                 }
-            }
-#pragma unroll
-            for (int q = 0; q < DEPTH; ++q) {
-                const int i = a + j0 + h4 + q;
-                dot[h4 + q] = 0.f;
-                if (i < b) {
-                    const int run = s_run[i];
-                    if (run != cur) {
-                        if (cur >= 0) flush(i);
-                        cur = run;
-                        seg0 = i;
-                        const uint32_t id = s_uid[run];
-#pragma unroll
-                        for (int cc = 0; cc < CPL; ++cc) {
-                            const int ch = lane + 32 * cc;
-#pragma unroll
-                            for (int v = 0; v < VEC; ++v) { acc[cc][v] = 0.f; f[cc][v] = 0.f; }
-                            if (ch < nch) Rw::load(feats, (size_t)id * nch + ch, f[cc]);
-                        }
-                    }
-                    const float wp = s_wn[i];
-#pragma unroll
-                    for (int cc = 0; cc < CPL; ++cc)
-#pragma unroll
-                        for (int v = 0; v < VEC; ++v) {
-                            acc[cc][v] = fmaf(wp, x[q][cc][v], acc[cc][v]);
-                            dot[h4 + q] = fmaf(x[q][cc][v], f[cc][v], dot[h4 + q]);
-                        }
+                if (lane == 0) {
+                    pair_keys[N + rb + u] = s_runs[u].y;
+                    pair_vals[N + rb + u] = rb + u;
                 }
             }
         }
-        // reduce-scatter of 8 dots over the warp: lane l ends with dot (l >> 2) & 7
-        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-        float ra[4], rbv[2];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            ra[q] = (b4 ? dot[q + 4] : dot[q]) + __shfl_xor_sync(0xffffffffu, b4 ? dot[q] : dot[q + 4], 16);
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-            rbv[q] = (b3 ? ra[q + 2] : ra[q]) + __shfl_xor_sync(0xffffffffu, b3 ? ra[q] : ra[q + 2], 8);
-        float d = (b2 ? rbv[1] : rbv[0]) + __shfl_xor_sync(0xffffffffu, b2 ? rbv[0] : rbv[1], 4);
-        d += __shfl_xor_sync(0xffffffffu, d, 2);
-        d += __shfl_xor_sync(0xffffffffu, d, 1);
-        const int q = (lane >> 2) & 7;
-        if (!(lane & 3) && a + j0 + q < b) s_h[a + j0 + q] = d;
+        __syncthreads();                             // stage sidx is refilled next
     }
-    if (cur >= 0) flush(b);
-    __syncthreads();
-    // the warp where a cut run starts adds the edge rows of the following warps
-    if (b > a) {
-        const int last = s_run[b - 1];
-        const bool cutR = b < s_ustart[last + 1];
-        const bool startsHere = s_ustart[last] >= a;
-        if (cutR && startsHere) {
-            const int w_end = (s_ustart[last + 1] - 1) / R;
-            for (int ch = lane; ch < nch; ch += 32) {
-                float t[VEC];
-                const float *e = s_edge + ((size_t)warp * 2 + 1) * D + (size_t)ch * VEC;
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) t[v] = e[v];
-                for (int w = warp + 1; w <= w_end; ++w) {
-                    const float *e2 = s_edge + ((size_t)w * 2 + 0) * D + (size_t)ch * VEC;
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) t[v] += e2[v];
-                }
-                float4 *d4 = (float4 *)(rows + (size_t)(rb + last) * D + (size_t)ch * VEC);
-#pragma unroll
-                for (int v = 0; v < VEC / 4; ++v) d4[v] = make_float4(t[4 * v], t[4 * v + 1], t[4 * v + 2], t[4 * v + 3]);
-            }
+    // copies still in flight (only after a timed-out wait): wait for them, bounded
+    if (timed_out)
+        for (int jj = j; jj < issued; ++jj) {
+            const int sidx = jj % kStages;
+            if (mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u)) parity ^= 1u << sidx;
         }
-    }
-    // h per slot, and the (Gaussian, partial row) pairs of the per-Gaussian reduction
-    for (int i = tid; i < nvalid; i += kAccNT) {
-        const int sl = (int)(keys[i] & 0xffffull);
-        const int pl = s_pl[i], k = sl - pl * K;
-        hbuf[pixel_of(pl) * K + k] = s_h[i];
-    }
-    for (int u = tid; u < nu; u += kAccNT) {
-        pair_keys[N + rb + u] = s_uid[u];
-        pair_vals[N + rb + u] = rb + u;
-    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -378,81 +439,144 @@ int tile_sort_len(int slots)
     return n;
 }
 
-bool tile_grad_supported(int dtype, int D, int K, int tw, int th)
+bool tile_grad_supported(int dtype, int D, int K)
 {
-    const int nch = D / (dtype == GS_BF16 ? 8 : 4);
-    return nch <= 32 * 8 && tw * th * K <= 65535 && tile_accum_smem(tw * th, K, D) <= 200 * 1024 &&
-           8 * (size_t)tile_sort_len(tw * th * K) <= 200 * 1024;
+    const FgBlock fb = fg_block_shape(dtype, D, K);
+    if (fb.bw == 0) return false;
+    const int B = fb.bw * fb.bh;
+    return B * K <= 65535 && block_accum_smem(B, K, D, dtype) <= 227 * 1024 &&
+           (8 + 4) * (size_t)tile_sort_len(B * K) <= 200 * 1024;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// dL/dF of camera c viewed as [H][W][D], boxes of [bh][bw][min(D, 256)] elements
+static bool make_maps(const CamTable &cb, int dtype, int D, const void *dLdF, TmaMaps &maps)
+{
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const int esz = dtype == GS_BF16 ? 2 : 4;
+    memset(&maps, 0, sizeof(maps));
+    for (int c = 0; c < cb.n; ++c) {
+        const CamDev &cam = cb.c[c];
+        void *gbase = (void *)((const char *)dLdF + (size_t)cam.pix_off * D * esz);
+        const cuuint64_t dims[3] = {(cuuint64_t)D, (cuuint64_t)cam.W, (cuuint64_t)cam.H};
+        const cuuint64_t strides[2] = {(cuuint64_t)D * esz, (cuuint64_t)D * esz * cam.W};
+        const cuuint32_t box[3] = {(cuuint32_t)tma_inner(D), (cuuint32_t)cb.tile_w, (cuuint32_t)cb.tile_h};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        const CUresult r = enc(&maps.m[c], dtype == GS_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                               3, gbase, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
 }
 
 template <int TW, int TH, bool BF16, int CPLV>
-static void accum_one(unsigned grid, size_t sm, cudaStream_t s, const CamTable &ct, const WsLayout &L,
-                      const float *tw, const unsigned long long *keys, const uint32_t *rbase, const uint32_t *tu,
-                      const void *feats, const void *dLdF, float *rows, uint32_t *pk, uint32_t *pv, float *hbuf,
-                      int *err)
+static void accum_one(unsigned grid, size_t sm, cudaStream_t s, const TmaMaps &maps, const CamTable &cb,
+                      const WsLayout &L, int st_sz, const uint2 *rec, const uint2 *runs, const uint32_t *rbase,
+                      const uint32_t *tu, float *rows, uint32_t *pk, uint32_t *pv, int *err)
 {
-    cudaFuncSetAttribute(k_tile_accum<TW, TH, BF16, CPLV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_tile_accum<TW, TH, BF16, CPLV><<<grid, kAccNT, sm, s>>>(ct, L.K, L.D, tw, keys, rbase, tu, (uint32_t)L.rows_cap,
-                                                              feats, dLdF, rows, pk, pv, L.N, hbuf, err);
+    cudaFuncSetAttribute(k_block_accum<TW, TH, BF16, CPLV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_block_accum<TW, TH, BF16, CPLV><<<grid, kBlkNT, sm, s>>>(maps, cb, L.K, L.D, st_sz, rec, runs, rbase, tu,
+                                                               (uint32_t)L.rows_cap, rows, pk, pv, L.N, err);
 }
 
 template <int TW, int TH, bool BF16>
-static void accum_launch(int cpl, unsigned grid, size_t sm, cudaStream_t s, const CamTable &ct, const WsLayout &L,
-                         const float *tw, const unsigned long long *keys, const uint32_t *rbase, const uint32_t *tu,
-                         const void *feats, const void *dLdF, float *rows, uint32_t *pk, uint32_t *pv, float *hbuf,
-                         int *err)
+static void accum_launch(int cpl, unsigned grid, size_t sm, cudaStream_t s, const TmaMaps &maps, const CamTable &cb,
+                         const WsLayout &L, int st_sz, const uint2 *rec, const uint2 *runs, const uint32_t *rbase,
+                         const uint32_t *tu, float *rows, uint32_t *pk, uint32_t *pv, int *err)
 {
     // (D <= 1024 caps bf16 rows at 4 chunks per lane; float32 rows at 8)
     switch (cpl) {
-    case 1: accum_one<TW, TH, BF16, 1>(grid, sm, s, ct, L, tw, keys, rbase, tu, feats, dLdF, rows, pk, pv, hbuf, err); break;
-    case 2: accum_one<TW, TH, BF16, 2>(grid, sm, s, ct, L, tw, keys, rbase, tu, feats, dLdF, rows, pk, pv, hbuf, err); break;
-    case 4: accum_one<TW, TH, BF16, 4>(grid, sm, s, ct, L, tw, keys, rbase, tu, feats, dLdF, rows, pk, pv, hbuf, err); break;
-    default: accum_one<TW, TH, BF16, (BF16 ? 4 : 8)>(grid, sm, s, ct, L, tw, keys, rbase, tu, feats, dLdF, rows, pk, pv, hbuf, err); break;
+    case 1: accum_one<TW, TH, BF16, 1>(grid, sm, s, maps, cb, L, st_sz, rec, runs, rbase, tu, rows, pk, pv, err); break;
+    case 2: accum_one<TW, TH, BF16, 2>(grid, sm, s, maps, cb, L, st_sz, rec, runs, rbase, tu, rows, pk, pv, err); break;
+    case 4: accum_one<TW, TH, BF16, 4>(grid, sm, s, maps, cb, L, st_sz, rec, runs, rbase, tu, rows, pk, pv, err); break;
+    default:
+        accum_one<TW, TH, BF16, (BF16 ? 4 : 8)>(grid, sm, s, maps, cb, L, st_sz, rec, runs, rbase, tu, rows, pk, pv,
+                                                 err);
+        break;
     }
 }
 
+static int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 148;
+    return n;
+}
+
 template <int TW, int TH>
-static bool tile_launch(const CamTable &ct, const WsLayout &L, int dtype, const int *topk_idx, const float *topk_w,
-                        const void *feats, const void *dLdF, void *ws, cudaStream_t s)
+static bool tile_launch(const CamTable &cb, const WsLayout &L, int dtype, const int *topk_idx, const float *topk_w,
+                        const void *dLdF, void *ws, cudaStream_t s)
 {
     constexpr int B = TW * TH;
+    TmaMaps maps;
+    if (!make_maps(cb, dtype, L.D, dLdF, maps)) return false;
     uint32_t *hdr = ws_ptr<uint32_t>(ws, L.header);
     int *err = (int *)hdr;
-    unsigned long long *keys = ws_ptr<unsigned long long>(ws, L.tile_keys);
+    uint2 *rec = ws_ptr<uint2>(ws, L.tile_keys);
+    uint2 *runs = ws_ptr<uint2>(ws, L.tile_runs);
     uint32_t *tile_u = ws_ptr<uint32_t>(ws, L.tile_u);
     uint32_t *row_base = ws_ptr<uint32_t>(ws, L.tile_rowbase);
     float *rows = ws_ptr<float>(ws, L.tile_rows);
     uint32_t *pk = ws_ptr<uint32_t>(ws, L.pair_keys[0]);
     uint32_t *pv = ws_ptr<uint32_t>(ws, L.pair_vals[0]);
-    float *hbuf = ws_ptr<float>(ws, L.hbuf);
     uint32_t *aux = ws_ptr<uint32_t>(ws, L.scan_aux);
     const int nsort = tile_sort_len(B * L.K);
-    const size_t sm1 = sizeof(unsigned long long) * nsort;
+    const size_t sm1 = (sizeof(unsigned long long) + sizeof(float)) * nsort;
+    const int nt1 = std::min(1024, std::max(32, nsort / 2));
     cudaFuncSetAttribute(k_tile_slots<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-    k_tile_slots<TW, TH><<<ct.n_tiles, kSortNT, sm1, s>>>(ct, L.K, nsort, topk_idx, err, keys, tile_u);
-    exclusive_scan_u32(tile_u, row_base, ct.n_tiles, hdr + 8, aux, s);
-    const size_t sm3 = tile_accum_smem(B, L.K, L.D);
+    k_tile_slots<TW, TH><<<cb.n_tiles, nt1, sm1, s>>>(cb, L.K, nsort, topk_idx, topk_w, err, rec, runs, tile_u);
+    exclusive_scan_u32(tile_u, row_base, cb.n_tiles, hdr + 8, aux, s);
+    const size_t sm3 = block_accum_smem(B, L.K, L.D, dtype);
+    const int st_sz = (int)stage_bytes(B, L.K, dtype, L.D);
     const int nch = L.D / (dtype == GS_BF16 ? 8 : 4);
     const int cpl = nch <= 32 ? 1 : nch <= 64 ? 2 : nch <= 128 ? 4 : 8;
+    const unsigned grid = (unsigned)std::max(1, std::min(cb.n_tiles, sm_count()));
     if (dtype == GS_BF16)
-        accum_launch<TW, TH, true>(cpl, ct.n_tiles, sm3, s, ct, L, topk_w, keys, row_base, tile_u, feats, dLdF, rows,
-                                   pk, pv, hbuf, err);
+        accum_launch<TW, TH, true>(cpl, grid, sm3, s, maps, cb, L, st_sz, rec, runs, row_base, tile_u, rows, pk, pv,
+                                   err);
     else
-        accum_launch<TW, TH, false>(cpl, ct.n_tiles, sm3, s, ct, L, topk_w, keys, row_base, tile_u, feats, dLdF, rows,
-                                    pk, pv, hbuf, err);
+        accum_launch<TW, TH, false>(cpl, grid, sm3, s, maps, cb, L, st_sz, rec, runs, row_base, tile_u, rows, pk, pv,
+                                    err);
     return true;
 }
 
-// Stages T1-T3; leaves the (Gaussian, row) pairs after N marker slots in pair buffer 0,
-// the partial rows, hbuf, and U_tot in header word 8.
+// Stages T1-T3 on the feature-gradient blocks of ct's cameras; leaves the (Gaussian,
+// row) pairs after N marker slots in pair buffer 0, the partial rows, and U_tot in
+// header word 8.
 bool launch_tile_grad(const CamTable &ct, const WsLayout &L, int dtype, const int *topk_idx, const float *topk_w,
-                      const void *feats, const void *dLdF, void *ws, cudaStream_t s)
+                      const void *dLdF, void *ws, cudaStream_t s)
 {
-    if (ct.tile_w == 16 && ct.tile_h == 16) return tile_launch<16, 16>(ct, L, dtype, topk_idx, topk_w, feats, dLdF, ws, s);
-    if (ct.tile_w == 32 && ct.tile_h == 8) return tile_launch<32, 8>(ct, L, dtype, topk_idx, topk_w, feats, dLdF, ws, s);
-    if (ct.tile_w == 16 && ct.tile_h == 8) return tile_launch<16, 8>(ct, L, dtype, topk_idx, topk_w, feats, dLdF, ws, s);
-    if (ct.tile_w == 8 && ct.tile_h == 8) return tile_launch<8, 8>(ct, L, dtype, topk_idx, topk_w, feats, dLdF, ws, s);
+    const FgBlock fb = fg_block_shape(dtype, L.D, L.K);
+    CamTable cb;
+    retile(ct, fb.bw, fb.bh, cb);
+    if (fb.bw == 8 && fb.bh == 8) return tile_launch<8, 8>(cb, L, dtype, topk_idx, topk_w, dLdF, ws, s);
+    if (fb.bw == 8 && fb.bh == 4) return tile_launch<8, 4>(cb, L, dtype, topk_idx, topk_w, dLdF, ws, s);
+    if (fb.bw == 4 && fb.bh == 4) return tile_launch<4, 4>(cb, L, dtype, topk_idx, topk_w, dLdF, ws, s);
     return false;
 }
+
+size_t tile_runs_bytes(int B, int K) { return 8 * (size_t)runs_stride(B * K); }
 
 }  // namespace gs

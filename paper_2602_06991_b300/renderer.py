@@ -196,11 +196,30 @@ class TopKRenderer:
         gg = A.GsGrads(g["feat"].data_ptr(), g["opacity"].data_ptr(), g["rgb"].data_ptr(), g["mean3d"].data_ptr(),
                        g["cov3d"].data_ptr(), g["mean2d"].data_ptr() if "mean2d" in g else None,
                        g["conic"].data_ptr() if "conic" in g else None)
-        A.check(self.lib.gs_backward(ctypes.byref(self.cfg), self.cams, self.n_cams, N, _p(st["mean3d"]),
-                                     _p(st["cov3d"]), _p(st["opacity"]), _p(st["rgb"]), _p(st["feats"]),
-                                     _p(o["proj"]), _p(o["rgb"]), _p(o["depth"]), _p(o["topk_idx"]),
-                                     _p(o["topk_w"]), _p(dL_dF), _p(dL_dC), _p(dL_dD), ctypes.byref(gg),
-                                     _p(self.ws), self.ws.numel(), self._stream()), "gs_backward")
+        def run():
+            A.check(self.lib.gs_backward(ctypes.byref(self.cfg), self.cams, self.n_cams, N, _p(st["mean3d"]),
+                                         _p(st["cov3d"]), _p(st["opacity"]), _p(st["rgb"]), _p(st["feats"]),
+                                         _p(o["proj"]), _p(o["rgb"]), _p(o["depth"]), _p(o["topk_idx"]),
+                                         _p(o["topk_w"]), _p(dL_dF), _p(dL_dC), _p(dL_dD), ctypes.byref(gg),
+                                         _p(self.ws), self.ws.numel(), self._stream()), "gs_backward")
+
+        run()
+        if self.check_overflow:
+            # the per-block partial feature rows have a capacity that grows with
+            # max_instances: on overflow, grow it, redo a1-a3 into the new workspace (same
+            # Top-K, deterministic) and the adjoint
+            code, _ = self.sync_status()
+            while code == A.GS_ERR_OVERFLOW:
+                cur = self.cfg.max_instances if self.cfg.max_instances > 0 else 32 * self.n_cams * N
+                if cur >= 2 ** 31 - 1:
+                    break
+                self.cfg.max_instances = int(min(2 ** 31 - 1, 2 * cur))
+                self.ws = None
+                self._ensure_ws(N)
+                self._select_into(N, st["mean3d"], st["cov3d"], st["opacity"], st["rgb"], o)
+                run()
+                code, _ = self.sync_status()
+            A.check(code, "backward")
         return g
 
     # ------------------------------------------------------------------ loss

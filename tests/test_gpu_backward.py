@@ -145,3 +145,37 @@ def test_autograd_function_matches_direct_calls():
     g = r2.backward(dF, dC, dD)
     for t, k in zip(ts, ["mean3d", "cov3d", "opacity", "rgb", "feat"]):
         assert torch.equal(t.grad, g[k]), k
+
+
+@pytest.mark.parametrize("D,K,dtype", [(1024, 5, "f32"), (768, 16, "bf16"), (136, 32, "f32")])
+def test_backward_feature_block_shapes(D, K, dtype):
+    """Feature-gradient blocks of every shape and TMA column count: float32 D=1024
+    (4x4 blocks, four 256-column boxes), bf16 D=768 K=16 (8x4 blocks, three boxes), and
+    D=136 K=32 (a box narrower than 256 columns); two ragged cameras whose blocks run
+    past the image edges.  Against the oracle gradient (bf16: the oracle takes the
+    bf16-rounded rows and upstream feature gradients)."""
+    sc = S.random_scene_box(12, 1500, D, box=((-1, 1), (-1, 1), (2, 4)))
+    cams = S.orbit_cameras(13, [(45, 29, 50.0), (38, 31, 45.0)], radius=3.0)
+    r, ts, out = U.gpu_forward(sc, cams, K, (16, 16), feat_dtype=dtype)
+    feats = None
+    if dtype == "bf16":
+        feats = torch.from_numpy(sc.feats).to(torch.bfloat16).float().numpy()
+    o = U.oracle_forward(sc, cams, K, feats=feats)
+    dF, dC, dD = _upstream(cams, sc.d, 14, o["flags"])
+    dF_t = torch.from_numpy(dF).cuda().to(r.feat_torch_dtype)
+    dF_exact = dF_t.float().cpu().numpy().astype(np.float64)
+    gg = r.backward(dF_t, torch.from_numpy(dC).cuda(), torch.from_numpy(dD).cuda())
+    torch.cuda.synchronize()
+    tot = None
+    for i, (cam, off) in enumerate(U.cam_slices(cams)):
+        sl = slice(off, off + cam.n_pix)
+        g = oracle.backward(sc, cam, K, dF_exact[sl], dC[sl], dD[sl], feats=feats)
+        if tot is None:
+            tot = {k: v.copy() for k, v in g.items()}
+        else:
+            for k in ("feat", "opac", "rgb", "mean3d", "cov3d"):
+                tot[k] += g[k]
+    errs = {gk: U.rel_l2(gg[gk].cpu().numpy(), tot[ok]) for gk, ok in GROUPS}
+    print("block shapes", D, K, dtype, errs)
+    for k, e in errs.items():
+        assert e <= U.GRAD_TOL, (k, e, errs)
