@@ -142,6 +142,34 @@ __device__ __forceinline__ float eval_alpha(float q, float o, float &G, float &a
     return fminf(kAlphaClamp, ao);
 }
 
+// Whether a Gaussian (centre r0, Cholesky-form conic and opacity r1) can take part at
+// any pixel centre of the rectangle [x0, x1] x [y0, y1]: the minimum of
+// q = (dx s1)^2 + ((dy - m dx) s2)^2 over the rectangle (on its boundary when the centre
+// is outside; the edge minima in closed form) against min(9, 2 ln(255 o)), the bound
+// beyond which alpha < 1/255, with margins above the binning's for float32 slack.  A
+// false answer is exact: no pixel in the rectangle would accept the Gaussian.
+__device__ __forceinline__ bool touches_rect(const float4 r0, const float4 r1, float x0, float x1, float y0, float y1)
+{
+    const float u = r0.x + r0.z, v = r0.y + r0.w;
+    const float s1 = r1.x, m = r1.y, s2 = r1.z;
+    const float dx0 = x0 - u, dx1 = x1 - u, dy0 = y0 - v, dy1 = y1 - v;
+    float qmin = 0.f;
+    if (!(dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f)) {
+        auto qf = [&](float dx, float dy) {
+            const float y1v = dx * s1, y2v = (dy - m * dx) * s2;
+            return y1v * y1v + y2v * y2v;
+        };
+        const float s22 = s2 * s2;
+        const float ax = s1 * s1 + m * m * s22;
+        auto on_vertical = [&](float dx) { return qf(dx, fminf(fmaxf(m * dx, dy0), dy1)); };
+        auto on_horizontal = [&](float dy) { return qf(fminf(fmaxf(m * s22 * dy / ax, dx0), dx1), dy); };
+        qmin = fminf(fminf(on_vertical(dx0), on_vertical(dx1)), fminf(on_horizontal(dy0), on_horizontal(dy1)));
+    }
+    float qb = fminf(kQMax, 2.0f * logf(255.0f * r1.w));
+    qb = fmaxf(qb, 0.0f) * 1.004f + 0.02f;
+    return qmin <= qb;
+}
+
 // Sum 16 per-lane values over the warp with 16 shuffles (reduce-scatter): on return
 // lane l holds the total of value index (l >> 1) & 15; lanes l and l ^ 1 agree.
 __device__ __forceinline__ float warp_reduce16(const float (&v)[16], int lane)

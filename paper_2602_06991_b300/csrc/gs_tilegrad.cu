@@ -283,24 +283,37 @@ static size_t stage_bytes(int B, int K, int dtype, int D)
 
 size_t block_accum_smem(int B, int K, int D, int dtype) { return 128 + kStages * stage_bytes(B, K, dtype, D); }
 
-// Each warp owns whole runs (runs w, w + 8, ...): a run -- one Gaussian's slots in the
-// block, at most B -- is summed by one warp in slot order and written as its partial
-// row, so the result does not depend on the warp count and needs no cross-warp merge.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp-specialised pipeline: warp kBlkNW (the producer) fills the kStages stages with
+// TMA and bulk copies, one block after another, once the consumers have released a
+// stage; warps 0..kBlkNW-1 (the consumers) each own whole runs (runs w, w + kBlkNW, ...)
+// of the block in a full stage: a run -- one Gaussian's slots in the block, at most B --
+// is summed by one warp in slot order and written as its partial row, so the result does
+// not depend on the warp count and needs no cross-warp merge; no CTA-wide barrier sits
+// between blocks.
 template <int TW, int TH, bool BF16, int CPL>
-__global__ void __launch_bounds__(kBlkNT, 1) k_block_accum(const __grid_constant__ TmaMaps maps, CamTable cb, int K,
-                                                           int D, int st_sz, const uint2 *__restrict__ rec,
-                                                           const uint2 *__restrict__ runs,
-                                                           const uint32_t *__restrict__ row_base,
-                                                           const uint32_t *__restrict__ tile_u, uint32_t rows_cap,
-                                                           float *__restrict__ rows, uint32_t *__restrict__ pair_keys,
-                                                           uint32_t *__restrict__ pair_vals, int N, int *err)
+__global__ void __launch_bounds__(kBlkNT + 32, 1) k_block_accum(const __grid_constant__ TmaMaps maps, CamTable cb,
+                                                                int K, int D, int st_sz,
+                                                                const uint2 *__restrict__ rec,
+                                                                const uint2 *__restrict__ runs,
+                                                                const uint32_t *__restrict__ row_base,
+                                                                const uint32_t *__restrict__ tile_u,
+                                                                uint32_t rows_cap, float *__restrict__ rows,
+                                                                uint32_t *__restrict__ pair_keys,
+                                                                uint32_t *__restrict__ pair_vals, int N, int *err)
 {
     constexpr int B = TW * TH;
     using Rw = SRow<BF16>;
     constexpr int VEC = Rw::VEC;
     constexpr int ESZ = BF16 ? 2 : 4;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t s_bar[kStages];
+    __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages];
+    __shared__ uint32_t s_meta[kStages][2];          // (U, row base) of the block in each stage
+    __shared__ int s_bad, s_issued, s_done[kBlkNW];
     const int nslots = B * K;
     const int rstride = runs_stride(nslots);
     const int nch = D / VEC;                           // 16-byte chunks per row
@@ -310,123 +323,138 @@ __global__ void __launch_bounds__(kBlkNT, 1) k_block_accum(const __grid_constant
     const int pix_bytes = inner * ESZ;
     const int col_bytes = B * pix_bytes;
     const int rows_sz = ncol * col_bytes;
-    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    // 128-byte aligned base, offset within the shared array (the pointer stays a
+    // shared-memory pointer, so the stage reads compile to shared loads)
+    unsigned char *base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n_blocks = cb.n_tiles;
     const int G = gridDim.x;
+    const int my_n = (int)((n_blocks - (int)blockIdx.x + G - 1) / G);
     const uint32_t stage_tx = (uint32_t)(rows_sz + 8 * nslots + 8 * rstride);
 
     if (tid == 0) {
-        for (int i = 0; i < kStages; ++i) mbar_init(&s_bar[i], 1);
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&s_full[i], 1);
+            mbar_init(&s_empty[i], kBlkNW);
+        }
         fence_mbar_init();
+        s_bad = *err != 0;
+        s_issued = 0;
     }
+    if (tid < kBlkNW) s_done[tid] = 0;
     __syncthreads();
+    const bool bad = s_bad != 0;
 
-    // thread 0: start the copies of block blk into stage sidx
-    auto issue = [&](int blk, int sidx) {
-        unsigned char *st = base + (size_t)sidx * st_sz;
-        const int c = cam_of_tile(cb, blk);
-        const CamDev &cam = cb.c[c];
-        const int lt = blk - cam.tile_off;
-        const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-        fence_async_shared();
-        mbar_expect_tx(&s_bar[sidx], stage_tx);
-        for (int col = 0; col < ncol; ++col)
-            tma_load_3d(st + (size_t)col * col_bytes, &maps.m[c], col * inner, tx * TW, ty * TH, &s_bar[sidx]);
-        bulk_load(st + rows_sz, rec + (size_t)blk * nslots, 8u * nslots, &s_bar[sidx]);
-        bulk_load(st + rows_sz + 8 * nslots, runs + (size_t)blk * rstride, 8u * rstride, &s_bar[sidx]);
-    };
-
-    // blocks of this CTA: blockIdx.x + j G, j = 0, 1, ...; block j lives in stage j % kStages
-    const int my_n = (int)((n_blocks - (int)blockIdx.x + G - 1) / G);
-    uint32_t parity = 0;                             // bit s: parity of stage s's next completion
-    int issued = 0;                                  // blocks whose copies were started
-    uint32_t Uq[kStages], rbq[kStages];              // (U, row base) of the blocks in the stages
-    for (; issued < kStages - 1 && issued < my_n; ++issued) {
-        const int blk = blockIdx.x + issued * G;
-        if (tid == 0) issue(blk, issued % kStages);
-        Uq[issued % kStages] = tile_u[blk];
-        rbq[issued % kStages] = row_base[blk];
-    }
-    int j = 0;
-    bool timed_out = false;
-    for (; j < my_n; ++j) {
-        const int sidx = j % kStages;
-        if (issued < my_n) {                         // keep kStages - 1 blocks in flight
-            const int blk = blockIdx.x + issued * G;
-            if (tid == 0) issue(blk, issued % kStages);
-            Uq[issued % kStages] = tile_u[blk];
-            rbq[issued % kStages] = row_base[blk];
-            ++issued;
-        }
-        const bool ok = mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u);
-        if (ok) parity ^= 1u << sidx;
-        const uint32_t U = Uq[sidx], rb = rbq[sidx];
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(err, kErrTimeout);
-            timed_out = true;
-            break;
-        }
-        const bool over = U > 0 && rb + U > rows_cap;
-        if (over && tid == 0) atomicOr(err, kErrOverflow);
-        const bool skip = __syncthreads_or(*(volatile int *)err != 0) || U == 0 || over;
-        if (!skip) {
-            const unsigned char *st = base + (size_t)sidx * st_sz;
-            const uint2 *s_rec = (const uint2 *)(st + rows_sz);
-            const uint2 *s_runs = (const uint2 *)(st + rows_sz + 8 * nslots);
-            int coff[CPL];                           // stage offset of each lane chunk
-#pragma unroll
-            for (int cc = 0; cc < CPL; ++cc) {
-                const int ch = lane + 32 * cc;
-                coff[cc] = (ch / cpb) * col_bytes + (ch % cpb) * 16;
+    if (warp == kBlkNW) {
+        // producer
+        if (lane == 0 && !bad) {
+            // (U, row base) of the next two blocks are loaded ahead, so no global round
+            // trip delays a copy
+            uint32_t U0 = 0, rb0 = 0, U1 = 0, rb1 = 0;
+            if (my_n > 0) { U0 = tile_u[blockIdx.x]; rb0 = row_base[blockIdx.x]; }
+            if (my_n > 1) { U1 = tile_u[blockIdx.x + G]; rb1 = row_base[blockIdx.x + G]; }
+            int j = 0;
+            for (; j < my_n; ++j) {
+                const int sidx = j % kStages;
+                const int blk = blockIdx.x + j * G;
+                uint32_t U2 = 0, rb2 = 0;
+                if (j + 2 < my_n) { U2 = tile_u[blk + 2 * G]; rb2 = row_base[blk + 2 * G]; }
+                if (j >= kStages && !mbar_wait(&s_empty[sidx], ((j / kStages) - 1) & 1)) {
+                    atomicOr(err, kErrTimeout);
+                    break;
+                }
+                s_meta[sidx][0] = U0;
+                s_meta[sidx][1] = rb0;
+                U0 = U1; rb0 = rb1; U1 = U2; rb1 = rb2;
+                unsigned char *st = base + (size_t)sidx * st_sz;
+                const int c = cam_of_tile(cb, blk);
+                const CamDev &cam = cb.c[c];
+                const int lt = blk - cam.tile_off;
+                const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+                fence_async_shared();
+                mbar_expect_tx(&s_full[sidx], stage_tx);
+                for (int col = 0; col < ncol; ++col)
+                    tma_load_3d(st + (size_t)col * col_bytes, &maps.m[c], col * inner, tx * TW, ty * TH,
+                                &s_full[sidx]);
+                bulk_load(st + rows_sz, rec + (size_t)blk * nslots, 8u * nslots, &s_full[sidx]);
+                bulk_load(st + rows_sz + 8 * nslots, runs + (size_t)blk * rstride, 8u * rstride, &s_full[sidx]);
             }
-            for (int u = warp; u < (int)U; u += kBlkNW) {
-                const int i0 = (int)s_runs[u].x, i1 = (int)s_runs[u + 1].x;
-                float acc[CPL][VEC];
+            s_issued = j;
+        }
+    } else if (!bad) {
+        // consumers
+        int coff[CPL];                               // stage offset of each lane chunk
 #pragma unroll
-                for (int cc = 0; cc < CPL; ++cc)
+        for (int cc = 0; cc < CPL; ++cc) {
+            const int ch = lane + 32 * cc;
+            coff[cc] = (ch / cpb) * col_bytes + (ch % cpb) * 16;
+        }
+        int j = 0;
+        for (; j < my_n; ++j) {
+            const int sidx = j % kStages;
+            if (!mbar_wait(&s_full[sidx], (j / kStages) & 1)) {
+                if (lane == 0) atomicOr(err, kErrTimeout);
+                break;
+            }
+            const uint32_t U = s_meta[sidx][0], rb = s_meta[sidx][1];
+            const bool over = U > 0 && rb + U > rows_cap;
+            if (over && warp == 0 && lane == 0) atomicOr(err, kErrOverflow);
+            if (!over) {
+                const unsigned char *st = base + (size_t)sidx * st_sz;
+                const uint2 *s_rec = (const uint2 *)(st + rows_sz);
+                const uint2 *s_runs = (const uint2 *)(st + rows_sz + 8 * nslots);
+                for (int u = warp; u < (int)U; u += kBlkNW) {
+                    const int i0 = (int)s_runs[u].x, i1 = (int)s_runs[u + 1].x;
+                    float acc[CPL][VEC];
 #pragma unroll
-                    for (int v = 0; v < VEC; ++v) acc[cc][v] = 0.f;
-                for (int i = i0; i < i1; ++i) {
-                    const uint2 r = s_rec[i];
-                    const float wp = __uint_as_float(r.y);
-                    const unsigned char *px = st + (size_t)(r.x & 0xffffu) * pix_bytes;
+                    for (int cc = 0; cc < CPL; ++cc)
 #pragma unroll
-                    for (int cc = 0; cc < CPL; ++cc) {
-                        if (lane + 32 * cc < nch) {
-                            float x[VEC];
-                            Rw::load(px + coff[cc], x);
+                        for (int v = 0; v < VEC; ++v) acc[cc][v] = 0.f;
+                    for (int i = i0; i < i1; ++i) {
+                        const uint2 r = s_rec[i];
+                        const float wp = __uint_as_float(r.y);
+                        const unsigned char *px = st + (size_t)(r.x & 0xffffu) * pix_bytes;
 #pragma unroll
-                            for (int v = 0; v < VEC; ++v) acc[cc][v] = fmaf(wp, x[v], acc[cc][v]);
+                        for (int cc = 0; cc < CPL; ++cc) {
+                            if (lane + 32 * cc < nch) {
+                                float x[VEC];
+                                Rw::load(px + coff[cc], x);
+#pragma unroll
+                                for (int v = 0; v < VEC; ++v) acc[cc][v] = fmaf(wp, x[v], acc[cc][v]);
+                            }
                         }
                     }
-                }
-                float *dst = rows + (size_t)(rb + u) * D;
+                    float *dst = rows + (size_t)(rb + u) * D;
 #pragma unroll
-                for (int cc = 0; cc < CPL; ++cc) {
-                    const int ch = lane + 32 * cc;
-                    if (ch < nch) {
-                        float4 *d4 = (float4 *)(dst + (size_t)ch * VEC);
+                    for (int cc = 0; cc < CPL; ++cc) {
+                        const int ch = lane + 32 * cc;
+                        if (ch < nch) {
+                            float4 *d4 = (float4 *)(dst + (size_t)ch * VEC);
 #pragma unroll
-                        for (int v = 0; v < VEC / 4; ++v)
-                            d4[v] = make_float4(acc[cc][4 * v], acc[cc][4 * v + 1], acc[cc][4 * v + 2],
-                                                acc[cc][4 * v + 3]);
+                            for (int v = 0; v < VEC / 4; ++v)
+                                d4[v] = make_float4(acc[cc][4 * v], acc[cc][4 * v + 1], acc[cc][4 * v + 2],
+                                                    acc[cc][4 * v + 3]);
+                        }
+                    }
+                    if (lane == 0) {
+                        pair_keys[N + rb + u] = s_runs[u].y;
+                        pair_vals[N + rb + u] = rb + u;
                     }
                 }
-                if (lane == 0) {
-                    pair_keys[N + rb + u] = s_runs[u].y;
-                    pair_vals[N + rb + u] = rb + u;
-                }
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_empty[sidx]);   // this warp is done with the stage
         }
-        __syncthreads();                             // stage sidx is refilled next
+        if (lane == 0) s_done[warp] = j;
     }
+    __syncthreads();
     // copies still in flight (only after a timed-out wait): wait for them, bounded
-    if (timed_out)
-        for (int jj = j; jj < issued; ++jj) {
-            const int sidx = jj % kStages;
-            if (mbar_wait(&s_bar[sidx], (parity >> sidx) & 1u)) parity ^= 1u << sidx;
-        }
+    if (tid == 0) {
+        int done = my_n;
+        for (int w = 0; w < kBlkNW; ++w) done = min(done, s_done[w]);
+        if (bad) done = 0;
+        for (int jj = done; jj < s_issued; ++jj) mbar_wait(&s_full[jj % kStages], (jj / kStages) & 1);
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -496,7 +524,7 @@ static void accum_one(unsigned grid, size_t sm, cudaStream_t s, const TmaMaps &m
                       const uint32_t *tu, float *rows, uint32_t *pk, uint32_t *pv, int *err)
 {
     cudaFuncSetAttribute(k_block_accum<TW, TH, BF16, CPLV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_block_accum<TW, TH, BF16, CPLV><<<grid, kBlkNT, sm, s>>>(maps, cb, L.K, L.D, st_sz, rec, runs, rbase, tu,
+    k_block_accum<TW, TH, BF16, CPLV><<<grid, kBlkNT + 32, sm, s>>>(maps, cb, L.K, L.D, st_sz, rec, runs, rbase, tu,
                                                                (uint32_t)L.rows_cap, rows, pk, pv, L.N, err);
 }
 

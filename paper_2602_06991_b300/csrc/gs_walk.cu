@@ -42,6 +42,11 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
     const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
     const bool inside = px < cam.W && py < cam.H;
+    // pixel-centre rectangle of this warp: all TW columns, its 32 / TW rows
+    const int lane = tid & 31;
+    const float wx0 = (float)(tx * TW) + 0.5f, wx1 = (float)(tx * TW + TW) - 0.5f;
+    const float wy0 = (float)(ty * TH + (tid - lane) / TW) + 0.5f;
+    const float wy1 = wy0 + (float)(32 / TW - 1);
     int2 rg = ranges[tile];
     if (*err) rg.y = rg.x;
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
@@ -64,7 +69,13 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
         }
         __syncthreads();
         const int cnt = min(B, rg.y - b0);
-        for (int j = 0; j < cnt && !done; ++j) {
+        for (int jc = 0; jc < cnt && __any_sync(0xffffffffu, !done); jc += 32) {
+            // Gaussians of this chunk that can reach a pixel of this warp's rows
+            const int jl = jc + lane;
+            unsigned live = __ballot_sync(0xffffffffu, jl < cnt && touches_rect(s_r0[jl], s_r1[jl], wx0, wx1, wy0, wy1));
+            while (live && !done) {
+            const int j = jc + __ffs(live) - 1;
+            live &= live - 1;
             float dx, dy;
             const float4 r1 = s_r1[j];
             float q = eval_q(pxf, pyf, s_r0[j], r1, dx, dy);
@@ -86,6 +97,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
             T = test_T;
             ++nc;
             tk.insert(w, s_g[j]);
+            }
         }
     }
     if (!inside) return;
