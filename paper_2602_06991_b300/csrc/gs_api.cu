@@ -92,15 +92,13 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     // than P K; sized for 32 per block or Mcap / 16, growing with max_instances (an
     // overflow sets the error word and yields no feature gradient).
     L.rows_cap = L.use_tiles ? std::min(L.PK, std::max((long long)L.n_fgblocks * 32, mcap / 16)) : 0;
-    L.n_pairs = N + std::max(L.PK, L.rows_cap);
+    L.n_pairs = N + L.rows_cap;
     if (L.NE > 0x7fffffffll || L.n_pairs > 0x7fffffffll) return false;
     L.max_pieces_rows = N + (L.rows_cap + kPieceLen - 1) / kPieceLen + 1;
-    L.max_pieces = N + (L.PK + kPieceLen - 1) / kPieceLen + 1;
-    L.max_multi_rows = 2 * ((std::max(L.PK, L.rows_cap) + kPieceLen - 1) / kPieceLen) + 1;
+    L.max_multi_rows = 2 * ((L.rows_cap + kPieceLen - 1) / kPieceLen) + 1;
     L.inst_sorted = sorted_buffer(bits_for(L.n_tiles));
     L.pair_bits = bits_for((long long)N + 1);
     L.pair_sorted = sorted_buffer(L.pair_bits);
-    L.rank_sorted = sorted_buffer(30);
 
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes > 0 ? bytes : 1); return o; };
@@ -119,13 +117,9 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     L.scan_aux = take(u * (kSortBlocks + 32));
     L.inst_grad = take(sizeof(float) * kGradVals * L.Mcap);
     L.elem_grad = take(sizeof(float) * kGradVals * L.NE);
-    for (int i = 0; i < 2; ++i) L.rank_keys[i] = take(u * N);
-    for (int i = 0; i < 2; ++i) L.rank_vals[i] = take(u * N);
-    L.grank = take(u * N);
     for (int i = 0; i < 2; ++i) L.pair_keys[i] = take(u * L.n_pairs);
     for (int i = 0; i < 2; ++i) L.pair_vals[i] = take(u * L.n_pairs);
     L.hbuf = take(sizeof(float) * L.PK);
-    L.wnorm = take(sizeof(float) * L.PK);
     L.seg_start = take(u * N);
     L.seg_end = take(u * N);
     L.pieces = take(u * N);
@@ -134,7 +128,7 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     L.multi_off = take(u * N);
     L.mflag = take(u * N);
     L.mlist = take(u * N);
-    L.piece_rank = take(u * L.max_pieces);
+    L.piece_rank = take(u * L.max_pieces_rows);
     L.piece_rows = take(sizeof(float) * (size_t)L.max_multi_rows * cfg->D);
     L.loss_part = 0;
     if (L.use_tiles) {
@@ -288,7 +282,7 @@ int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int
     cudaStream_t s = (cudaStream_t)stream;
     CamTable ct;
     make_camtable(cfg, cams, n_cams, ct);
-    if (!launch_feature_grad(ct, L, cfg->feat_dtype, n_gauss, mean3d, topk_idx, topk_w, feats, dL_dF, grads->feat, ws,
+    if (!launch_feature_grad(ct, L, cfg->feat_dtype, n_gauss, topk_idx, topk_w, feats, dL_dF, grads->feat, ws,
                              s))
         return GS_ERR_UNSUPPORTED;
     if (!launch_walk_bwd(ct, L, cfg->K, n_gauss, proj, ws, rgb_out, depth_out, topk_idx, topk_w, dL_dC, dL_dD, s))

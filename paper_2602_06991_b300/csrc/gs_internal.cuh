@@ -244,16 +244,13 @@ struct WsLayout {
     size_t scan_aux;           // scan block sums
     size_t inst_grad;          // Mcap x kGradVals floats (per-instance partial 2D gradients)
     size_t elem_grad;          // NE x kGradVals floats (per-element sums of the instance partials)
-    size_t rank_keys[2], rank_vals[2];     // N (Gaussians in 3D Morton order)
-    size_t grank;              // N: Morton rank of each Gaussian
     size_t pair_keys[2], pair_vals[2];     // N + P K
     size_t hbuf;               // P K floats: dL/dF_p . f_{idx_k}
-    size_t wnorm;              // P K floats: renormalised Top-K weights w / S
     size_t seg_start, seg_end; // N each
     size_t pieces, piece_off;  // N each
     size_t multi, multi_off;   // N each
     size_t mflag, mlist;       // N each: ranks with a multi-piece segment (flag scan, compact list)
-    size_t piece_rank;         // max_pieces
+    size_t piece_rank;         // max_pieces_rows
     size_t piece_rows;         // max_multi_rows x D floats
     size_t loss_part;          // unused (the loss takes caller scratch)
     size_t tile_keys;          // n_fgblocks x B K uint2 slot records (pixel | run << 16, w') in sorted order
@@ -263,10 +260,9 @@ struct WsLayout {
     size_t total;
     int inst_sorted;           // buffer (0/1) holding the tile-sorted instances
     int pair_sorted;           // buffer (0/1) holding the sorted feature-gradient pairs
-    int rank_sorted;           // buffer (0/1) holding the Morton-ordered Gaussians
     int pair_bits;
 
-    long long NE, P, PK, Mcap, n_pairs, max_pieces, max_multi_rows;
+    long long NE, P, PK, Mcap, n_pairs, max_multi_rows;
     long long rows_cap, max_pieces_rows;
     bool use_tiles;
     long long n_fgblocks;      // feature-gradient pixel blocks (fg_block_shape) over all cameras
@@ -308,9 +304,9 @@ bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const 
                      const float *dLdC, const float *dLdD, cudaStream_t s);
 bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, const float *w, const void *feats,
                   void *F, const int *err, cudaStream_t s);
-bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N, const float *mean3d,
-                         const int *topk_idx, const float *topk_w, const void *feats, const void *dLdF,
-                         float *grad_feat, void *ws, cudaStream_t s);
+bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N, const int *topk_idx,
+                         const float *topk_w, const void *feats, const void *dLdF, float *grad_feat, void *ws,
+                         cudaStream_t s);
 bool tile_grad_supported(int dtype, int D, int K);
 // Feature-gradient pixel blocks: the largest of 8x8, 8x4, 4x4 whose dL/dF rows fit one
 // 64 KB shared-memory stage ({0, 0}: none).
