@@ -26,7 +26,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 elements per tile
 constexpr int kSortBlocks = 296;                       // 2 per SM on a 148-SM B300
-constexpr int kPieceLen = 128;                         // pairs per feature-gradient work piece
+constexpr int kPieceLen = 16;                          // partial rows per feature-gradient work piece
 constexpr int kGradVals = 10;                          // per-instance partial 2D gradient
 
 // Error word bits (in the workspace header).
@@ -192,6 +192,46 @@ __device__ __forceinline__ float warp_reduce16(const float (&v)[16], int lane)
         c2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
     }
     float d = (b1 ? c2[1] : c2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? c2[0] : c2[1], 2);
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    return d;
+}
+
+// Sum 10 per-lane values over the warp with 12 shuffles (a reduce-scatter that halves
+// 10 -> 5 -> 3 -> 2 -> 1 values per lane on lane bits 4, 3, 2, 1, padding with zeros):
+// on return lane l holds the total of value vidx10(l), or of a padding slot when
+// vidx10(l) < 0; lanes l and l ^ 1 agree.
+__device__ __forceinline__ int vidx10(int lane)
+{
+    const int b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1, b1 = (lane >> 1) & 1;
+    const bool real = b3 ? b2 == 0 : !(b2 && b1);
+    return real ? 5 * b4 + 3 * b3 + 2 * b2 + b1 : -1;
+}
+__device__ __forceinline__ float warp_reduce10(const float (&v)[10], int lane)
+{
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float a[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float send = b4 ? v[i] : v[i + 5], keep = b4 ? v[i + 5] : v[i];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    // a[0..4] of half b4; pad to 6: halves {0,1,2} and {3,4,-}
+    float b[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float lo = a[i], hi = i + 3 < 5 ? a[i + 3] : 0.f;
+        const float send = b3 ? lo : hi, keep = b3 ? hi : lo;
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    // b[0..2]; pad to 4: halves {0,1} and {2,-}
+    float c[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float lo = b[i], hi = i + 2 < 3 ? b[i + 2] : 0.f;
+        const float send = b2 ? lo : hi, keep = b2 ? hi : lo;
+        c[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    float d = (b1 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, b1 ? c[0] : c[1], 2);
     d += __shfl_xor_sync(0xffffffffu, d, 1);
     return d;
 }

@@ -238,9 +238,9 @@ __global__ void __launch_bounds__(TW *TH / kBwdPPT) k_walk_bwd(CamTable ct, int 
                 j_end = j;
                 break;
             }
-            float v[16];
+            float v[kGradVals];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+            for (int i = 0; i < kGradVals; ++i) v[i] = 0.f;
             bool contrib = false;
             const float4 r0 = s_r0[j], r1 = s_r1[j];
 #pragma unroll
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(TW *TH / kBwdPPT) k_walk_bwd(CamTable ct, int 
                 const float gi = dC0[r] * r2.x + dC1[r] * r2.y + dC2[r] * r2.z + dD[r] * r2.w + fp;
                 prefix[r] = fmaf(gi, w, prefix[r]);
                 const float suffix = total[r] - prefix[r];
-                const float dalpha = gi * T[r] - suffix / (1.f - alpha);
+                const float dalpha = gi * T[r] - __fdividef(suffix, 1.f - alpha);
                 v[6] += w * dC0[r]; v[7] += w * dC1[r]; v[8] += w * dC2[r]; v[9] += w * dD[r];
                 if (ao < kAlphaClamp) {
                     const float4 r3 = s_r3[j];
@@ -282,9 +282,9 @@ __global__ void __launch_bounds__(TW *TH / kBwdPPT) k_walk_bwd(CamTable ct, int 
                 T[r] = test_T;
             }
             if (__any_sync(0xffffffffu, contrib)) {
-                const float d = warp_reduce16(v, lane);
-                const int vi = (lane >> 1) & 15;
-                if (!(lane & 1) && vi < kGradVals) s_red[warp][j][vi] = d;
+                const float d = warp_reduce10(v, lane);
+                const int vi = vidx10(lane);
+                if (!(lane & 1) && vi >= 0) s_red[warp][j][vi] = d;
             } else if (lane < kGradVals) {
                 s_red[warp][j][lane] = 0.f;
             }
