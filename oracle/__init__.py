@@ -12,6 +12,10 @@ Functions follow the paper's definitions:
   backward  -- the adjoint of the above (no counterpart in the paper; written out from
                Eqs. 1-4 by the chain rule), chained through the projection to the 3D
                mean and covariance.
+  prune_stats  -- Sec. 3.3: Top-K participation count and the geometric importance
+               S_i = max w_i (Eq. 8) of every Gaussian over a view's pixels
+  prune_select -- Sec. 3.3: the candidate set (low Top-K participation) and the weighted
+               survival sampling of Eq. 9
 """
 from __future__ import annotations
 
@@ -64,6 +68,7 @@ def _L():
                                     dp, dp, dp, dp, dp, dp]
         lib.or_backward_project.argtypes = [i, dp, dp, dp, dp, dp, dp, dp, dp]
         lib.or_pixel_walk.argtypes = [i, dp, dp, ctypes.c_double, ctypes.c_double, dp, i, ip, dp, dp, ip]
+        lib.or_prune_stats.argtypes = [i, dp, dp, i, i, dp, dp, ctypes.POINTER(ctypes.c_longlong), dp, ip]
         _lib = lib
         global PROJ_LEN, CAM_LEN
         PROJ_LEN = lib.or_proj_len()
@@ -190,3 +195,51 @@ def backward(scene, cam, K, dF, dC, dD, pixels=None, proj=None, margins=DEFAULT_
     gc, pgc = _d(np.zeros((n, 6)))
     L.or_backward_project(n, pcov, pca, ppr, pg2, pgq, pgz, pgm, pgc)
     return dict(mean2d=g2, conic=gq, opac=go, rgb=gr, depth=gz, feat=gf, mean3d=gm, cov3d=gc)
+
+
+def prune_stats(scene, cam, K, pixels=None, proj=None, margins=DEFAULT_MARGINS, count=None, maxw=None):
+    """Sec. 3.3 statistics over one view's pixels (default: all), accumulated into count
+    (int64, n) and maxw (float64, n) when given: Top-K participation and S_i = max w_i
+    (Eq. 8).  Returns dict(count, maxw, flags)."""
+    L = _L()
+    if proj is None:
+        proj = project(scene, cam)
+    n = scene.n
+    pxy, ppx = _d(pixel_centres(cam, pixels))
+    P = pxy.shape[0]
+    pr, ppr = _d(proj)
+    op, pop = _d(scene.opacity)
+    mg, pmg = _d(np.asarray(margins, dtype=np.float64))
+    cnt = np.zeros(n, dtype=np.int64) if count is None else count
+    mw = np.zeros(n, dtype=np.float64) if maxw is None else maxw
+    assert cnt.dtype == np.int64 and cnt.flags.c_contiguous and mw.dtype == np.float64 and mw.flags.c_contiguous
+    fl, pfl = _i(np.zeros(P))
+    L.or_prune_stats(n, ppr, pop, K, P, ppx, pmg, cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                     mw.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pfl)
+    return dict(count=cnt, maxw=mw, flags=fl)
+
+
+def prune_select(count, S, tau, ratio, expo):
+    """Sec. 3.3, Eq. 9.  Candidates G_prune: Gaussians with Top-K participation count < tau.
+    Within G_prune, m = floor(ratio |G_prune| + 1/2) Gaussians survive, drawn by weighted
+    sampling without replacement with probability proportional to S_i (Eq. 9): each
+    draw picks candidate i with probability S_i / sum of the remaining S.  The draws are
+    realised as an exponential race -- candidate i finishes at e_i / S_i with the given
+    e_i ~ Exp(1), the m earliest survive (the first finisher is i with probability
+    S_i / sum S); S_i = 0 never finishes, equal times go to the smaller id.  The times
+    are formed in float32 (as the kernel does), so both sides take the same decision.
+    Returns keep (bool, n): every non-candidate is kept."""
+    count = np.asarray(count)
+    S32 = np.asarray(S, dtype=np.float32)
+    e32 = np.asarray(expo, dtype=np.float32)
+    n = count.shape[0]
+    cand = np.nonzero(count < tau)[0]
+    m = int(np.floor(ratio * cand.size + 0.5))
+    t = np.full(cand.size, np.inf, dtype=np.float32)
+    pos = S32[cand] > 0
+    t[pos] = e32[cand][pos] / S32[cand][pos]
+    order = np.lexsort((cand, t))          # by time, then id
+    keep = np.ones(n, dtype=bool)
+    keep[cand] = False
+    keep[cand[order[:m]]] = True
+    return keep

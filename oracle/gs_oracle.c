@@ -443,3 +443,33 @@ int or_backward_project(int n, const double *cov3d, const double *cam, const dou
     }
     return 0;
 }
+
+/* ---------------------------------------------------------------------------------
+ * Consistency-pruning statistics (Sec. 3.3), accumulated over the given pixels of one
+ * view, for every Gaussian g:
+ *   count[g] += the number of pixels whose Top-K set (Eq. 2) holds g
+ *               (the Top-K participation that selects the candidate set G_prune);
+ *   maxw[g]   = max(maxw[g], w_g(r)) over every pixel r where g is a contributor --
+ *               the geometric importance S_g of Eq. 8, a maximum of the alpha-blending
+ *               weight of Eq. 1 over all rays, selected or not.
+ * flags as in or_render.
+ * ------------------------------------------------------------------------------- */
+int or_prune_stats(int n, const double *proj, const double *opac, int K, int npix, const double *pxy,
+                   const double *margin, long long *count, double *maxw, int *flags)
+{
+    contrib_t *cand = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)(n > 0 ? n : 1));
+    contrib_t *walk = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)(n > 0 ? n : 1));
+    int *pos = (int *)malloc(sizeof(int) * (size_t)(K > 0 ? K : 1));
+    for (int p = 0; p < npix; ++p) {
+        int fl = 0;
+        double Tf;
+        int nc = pixel_walk(n, proj, opac, pxy[2 * p], pxy[2 * p + 1], margin, cand, walk, &Tf, &fl);
+        for (int i = 0; i < nc; ++i)
+            if (walk[i].w > maxw[walk[i].g]) maxw[walk[i].g] = walk[i].w;
+        int m = topk_positions(walk, nc, K, pos, margin[3], &fl);
+        for (int k = 0; k < m; ++k) count[walk[pos[k]].g] += 1;
+        flags[p] = fl;
+    }
+    free(cand); free(walk); free(pos);
+    return 0;
+}

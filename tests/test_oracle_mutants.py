@@ -34,6 +34,10 @@ MUTANTS = {
     "bwd_dT_factor": ("dT[i][j] = 2.0 * acc;", "dT[i][j] = acc;"),
     "bwd_feature_term": ("acc += dFp[d] * (f[d] - Fp[d]);", "acc += dFp[d] * f[d];"),
     "bwd_jacobian_z": ("dpz += dJ[0][0] * (-fx / (z * z));", "dpz += dJ[0][0] * (fx / (z * z));"),
+    "prune_counts_all_contributors": ("for (int k = 0; k < m; ++k) count[walk[pos[k]].g] += 1;",
+                                      "for (int k = 0; k < nc; ++k) count[walk[k].g] += 1;"),
+    "prune_importance_is_alpha": ("if (walk[i].w > maxw[walk[i].g]) maxw[walk[i].g] = walk[i].w;",
+                                  "if (walk[i].alpha > maxw[walk[i].g]) maxw[walk[i].g] = walk[i].alpha;"),
 }
 
 
@@ -50,6 +54,7 @@ def test_pins_catch_mutant(name):
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", c, "-o", so, "-lm"])
         env = dict(os.environ, GS_ORACLE_LIB=so)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                            os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_prune.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
