@@ -290,6 +290,8 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
         "launches_per_step": launches_per_step,
     }
+    if rank == 0:
+        res["prune"] = run_prune(step)
     if rank == 0 and not args.no_e2e:
         res["e2e"] = run_e2e(step, args)
     if rank == 0 and not args.no_batched:
@@ -300,6 +302,39 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
     return res
+
+
+def run_prune(step, reps=20):
+    """Consistency-pruning statistics of the step's view (Sec. 3.3, Eq. 8: Top-K count and
+    S = max w, one re-walk) and the survival selection over all Gaussians (Eq. 9), each
+    timed with CUDA events on the launching stream."""
+    import torch
+    from paper_2602_06991_b300.renderer import prune_select
+    acc = step.r.alloc_prune_stats(step.N)
+    for _ in range(3):
+        step.r.prune_stats(acc)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        step.r.prune_stats(acc)
+    e1.record()
+    torch.cuda.synchronize()
+    stats_ms = e0.elapsed_time(e1) / reps
+    acc = step.r.prune_stats(step.r.alloc_prune_stats(step.N))
+    expo = torch.empty(step.N, device="cuda").exponential_()
+    for _ in range(3):
+        prune_select(acc["count"], acc["S"], 1, 0.5, expo)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        keep = prune_select(acc["count"], acc["S"], 1, 0.5, expo)
+    e1.record()
+    torch.cuda.synchronize()
+    sel_ms = e0.elapsed_time(e1) / reps
+    return {"stats_ms": round(stats_ms, 4), "select_ms": round(sel_ms, 4),
+            "candidates": int((acc["count"] < 1).sum().item()), "kept": int(keep.sum().item()),
+            "note": "per view: Top-K count + S = max w re-walk; selection: tau = 1, ratio 0.5, over all Gaussians"}
 
 
 def run_e2e(step, args):

@@ -193,6 +193,30 @@ int gs_loss_cos_l1_noalloc(const gs_config *cfg, int64_t n_pix, const void *F, c
                            float w_feat, float w_rgb, float w_depth,
                            void *dL_dF, float *dL_dC, float *dL_dD, float *loss, void *stream);
 
+/* Consistency-pruning statistics of one rendered view (Sec. 3.3), accumulated into
+ * caller-owned per-Gaussian arrays that the caller zeroes at the start of a pruning
+ * window and passes for every view of it:
+ *   topk_count[g] += the number of pixels whose Top-K set (Eq. 2) holds g (int32, N);
+ *   S[g] = max(S[g], w) over every pixel where g contributes, w the alpha-blending
+ *          weight of Eq. 1 -- the geometric importance of Eq. 8 (float32, N, >= 0).
+ * Call after gs_topk_select on the same workspace (it re-walks the binned tile lists)
+ * with that call's topk_idx.  Exact: integer counts, and the maximum of float32
+ * weights taken with the walk's own contributor rule. */
+int gs_prune_stats(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss, const float *proj,
+                   const int32_t *topk_idx, void *ws, size_t ws_bytes, int32_t *topk_count, float *S, void *stream);
+
+/* Survival selection of Sec. 3.3 (Eq. 9).  Candidates G_prune: Gaussians with
+ * topk_count < tau.  m = floor(ratio |G_prune| + 1/2) candidates survive, drawn by
+ * weighted sampling without replacement with probability S_i / sum S over the remaining
+ * candidates, realised as an exponential race: candidate i finishes at expo[i] / S[i]
+ * (float32 division), expo[i] ~ Exp(1) supplied by the caller (the random numbers of
+ * the method are inputs); S = 0 never finishes; equal times go to the smaller id.
+ * keep[g] (uint8, N) = 1 for survivors and every non-candidate, 0 for the pruned.
+ * Device workspace of gs_prune_select_workspace_size(n_gauss) bytes, 256-aligned. */
+size_t gs_prune_select_workspace_size(int32_t n_gauss);
+int gs_prune_select(int32_t n_gauss, const int32_t *topk_count, const float *S, int32_t tau, double ratio,
+                    const float *expo, uint8_t *keep, void *ws, size_t ws_bytes, void *stream);
+
 /* Synchronises `stream` and returns the workspace error word as a status (GS_OK if
  * clear).  If n_instances is not NULL it receives the instance count of the last
  * gs_bin_sort. */

@@ -72,6 +72,11 @@ PROTOTYPES = {
                                              vp, ctypes.c_size_t, vp]),
     "gs_loss_cos_l1_noalloc": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.c_int64, vp, vp, vp, vp, vp, vp,
                                               ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, vp, vp, vp, vp]),
+    "gs_prune_stats": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.POINTER(GsCamera), ctypes.c_int32,
+                                      ctypes.c_int32, vp, vp, vp, ctypes.c_size_t, vp, vp, vp]),
+    "gs_prune_select_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),
+    "gs_prune_select": (ctypes.c_int, [ctypes.c_int32, vp, vp, ctypes.c_int32, ctypes.c_double, vp, vp, vp,
+                                       ctypes.c_size_t, vp]),
     "gs_sync_status": (ctypes.c_int, [vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int64)]),
 }
 

@@ -341,6 +341,39 @@ int gs_feature_blend_loss(const gs_config *cfg, const gs_camera *cams, int32_t n
     return launch_status();
 }
 
+int gs_prune_stats(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss, const float *proj,
+                   const int32_t *topk_idx, void *ws, size_t ws_bytes, int32_t *topk_count, float *S, void *stream)
+{
+    WsLayout L;
+    if (!make_layout(cfg, cams, n_cams, n_gauss, L)) return GS_ERR_ARG;
+    if ((n_gauss > 0 && (!proj || !topk_count || !S)) || (L.PK > 0 && !topk_idx)) return GS_ERR_ARG;
+    int st = ws_check(L, ws, ws_bytes);
+    if (st) return st;
+    CamTable ct;
+    make_camtable(cfg, cams, n_cams, ct);
+    if (!launch_prune_stats(ct, L, n_gauss, proj, topk_idx, ws, topk_count, S, (cudaStream_t)stream))
+        return GS_ERR_UNSUPPORTED;
+    return launch_status();
+}
+
+size_t gs_prune_select_workspace_size(int32_t n_gauss)
+{
+    if (n_gauss < 0) return 0;
+    return prune_select_ws(n_gauss);
+}
+
+int gs_prune_select(int32_t n_gauss, const int32_t *topk_count, const float *S, int32_t tau, double ratio,
+                    const float *expo, uint8_t *keep, void *ws, size_t ws_bytes, void *stream)
+{
+    if (n_gauss < 0 || !(ratio >= 0.0 && ratio <= 1.0)) return GS_ERR_ARG;
+    if (n_gauss == 0) return GS_OK;
+    if (!topk_count || !S || !expo || !keep) return GS_ERR_ARG;
+    if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < prune_select_ws(n_gauss)) return GS_ERR_WORKSPACE;
+    if (!launch_prune_select(n_gauss, topk_count, S, tau, ratio, expo, keep, ws, (cudaStream_t)stream))
+        return GS_ERR_UNSUPPORTED;
+    return launch_status();
+}
+
 int gs_sync_status(const void *ws, size_t ws_bytes, void *stream, int64_t *n_instances)
 {
     if (!ws || ws_bytes < 256) return GS_ERR_WORKSPACE;

@@ -320,6 +320,11 @@ __host__ __device__ __forceinline__ T *ws_ptr(void *ws, size_t off) { return (T 
 // ------------------------------------------------------------------------------------
 // Host-side launchers implemented in the .cu files
 // ------------------------------------------------------------------------------------
+bool launch_prune_stats(const CamTable &ct, const WsLayout &L, int N, const float *proj, const int *topk_idx,
+                        void *ws, int *count, float *S, cudaStream_t s);
+size_t prune_select_ws(int N);
+bool launch_prune_select(int N, const int *count, const float *S, int tau, double ratio, const float *expo,
+                         uint8_t *keep, void *ws, cudaStream_t s);
 // LSD radix sort of (key, value) uint32 pairs on key bits [0, n_bits); stable.  The
 // element count is n_host, or *n_dev clamped to n_host if n_dev is non-null.
 // Returns the index (0/1) of the buffer pair holding the sorted result.

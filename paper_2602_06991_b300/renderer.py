@@ -222,6 +222,26 @@ class TopKRenderer:
             A.check(code, "backward")
         return g
 
+    # ------------------------------------------------------------------ pruning (Sec. 3.3)
+    def alloc_prune_stats(self, N: int):
+        """Zeroed accumulators for a pruning window: Top-K count (int32) and S (float32)."""
+        return dict(count=torch.zeros(N, dtype=torch.int32, device=self.device),
+                    S=torch.zeros(N, dtype=torch.float32, device=self.device))
+
+    def prune_stats(self, acc):
+        """Accumulate the statistics of the last forward's views into acc (gs_prune_stats):
+        acc['count'] += Top-K participation, acc['S'] = max(acc['S'], max w) (Eq. 8)."""
+        st = self.state
+        if st is None:
+            raise RuntimeError("prune_stats before forward")
+        N, o = st["N"], st["out"]
+        _need(acc["count"], torch.int32, (N,), "count")
+        _need(acc["S"], torch.float32, (N,), "S")
+        A.check(self.lib.gs_prune_stats(ctypes.byref(self.cfg), self.cams, self.n_cams, N, _p(o["proj"]),
+                                        _p(o["topk_idx"]), _p(self.ws), self.ws.numel(), _p(acc["count"]),
+                                        _p(acc["S"]), self._stream()), "gs_prune_stats")
+        return acc
+
     # ------------------------------------------------------------------ loss
     def loss(self, F, F_gt, rgb, rgb_gt, depth, depth_gt, w_feat=1.0, w_rgb=1.0, w_depth=1.0, out=None):
         P = self.P
@@ -259,3 +279,22 @@ class _TopKRenderFn(torch.autograd.Function):
 def render(renderer: TopKRenderer, mean3d, cov3d, opacity, rgb, feats):
     """Differentiable Top-K render: returns (F, rgb, depth) with gradients to every input."""
     return _TopKRenderFn.apply(renderer, mean3d, cov3d, opacity, rgb, feats)
+
+
+def prune_select(count, S, tau: int, ratio: float, expo):
+    """Survival selection of Sec. 3.3 (Eq. 9) on the device (gs_prune_select): candidates
+    have count < tau; floor(ratio |candidates| + 1/2) of them survive by weighted
+    sampling without replacement with probability proportional to S, drawn as an
+    exponential race with the given Exp(1) variates expo.  Returns keep (uint8, N)."""
+    lib = A.load()
+    N = int(count.shape[0])
+    dev = count.device
+    _need(count, torch.int32, (N,), "count")
+    _need(S, torch.float32, (N,), "S")
+    _need(expo, torch.float32, (N,), "expo")
+    keep = torch.empty(N, dtype=torch.uint8, device=dev)
+    ws = torch.empty(max(1, int(lib.gs_prune_select_workspace_size(N))), dtype=torch.uint8, device=dev)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    A.check(lib.gs_prune_select(N, _p(count), _p(S), int(tau), float(ratio), _p(expo), _p(keep), _p(ws), ws.numel(),
+                                stream), "gs_prune_select")
+    return keep
