@@ -16,6 +16,8 @@ Functions follow the paper's definitions:
                S_i = max w_i (Eq. 8) of every Gaussian over a view's pixels
   prune_select -- Sec. 3.3: the candidate set (low Top-K participation) and the weighted
                survival sampling of Eq. 9
+  render_vanilla -- the full alpha-blending feature baseline (Sec. 3.2, Tab. 4):
+               F = sum over all contributors of w_i f_i
 """
 from __future__ import annotations
 
@@ -69,6 +71,7 @@ def _L():
         lib.or_backward_project.argtypes = [i, dp, dp, dp, dp, dp, dp, dp, dp]
         lib.or_pixel_walk.argtypes = [i, dp, dp, ctypes.c_double, ctypes.c_double, dp, i, ip, dp, dp, ip]
         lib.or_prune_stats.argtypes = [i, dp, dp, i, i, dp, dp, ctypes.POINTER(ctypes.c_longlong), dp, ip]
+        lib.or_render_vanilla.argtypes = [i, dp, dp, dp, i, i, dp, dp, dp, ip]
         _lib = lib
         global PROJ_LEN, CAM_LEN
         PROJ_LEN = lib.or_proj_len()
@@ -243,3 +246,23 @@ def prune_select(count, S, tau, ratio, expo):
     keep[cand] = False
     keep[cand[order[:m]]] = True
     return keep
+
+
+def render_vanilla(scene, cam, pixels=None, proj=None, margins=DEFAULT_MARGINS, feats=None):
+    """Full alpha-blended feature (Eq. 1 on the feature rows, every contributor, no
+    renormalisation) at the given pixels.  Returns dict(F, flags)."""
+    L = _L()
+    if proj is None:
+        proj = project(scene, cam)
+    feats = scene.feats if feats is None else feats
+    n, D = scene.n, feats.shape[1]
+    pxy, ppx = _d(pixel_centres(cam, pixels))
+    P = pxy.shape[0]
+    pr, ppr = _d(proj)
+    op, pop = _d(scene.opacity)
+    ft, pft = _d(feats)
+    mg, pmg = _d(np.asarray(margins, dtype=np.float64))
+    F, pF = _d(np.zeros((P, D)))
+    fl, pfl = _i(np.zeros(P))
+    L.or_render_vanilla(n, ppr, pop, pft, D, P, ppx, pmg, pF, pfl)
+    return dict(F=F, flags=fl)

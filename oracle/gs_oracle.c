@@ -473,3 +473,29 @@ int or_prune_stats(int n, const double *proj, const double *opac, int K, int npi
     free(cand); free(walk); free(pos);
     return 0;
 }
+
+/* ---------------------------------------------------------------------------------
+ * Vanilla feature render (the full alpha-blending baseline of Sec. 3.2 / Tab. 4, as
+ * Feature3DGS renders features): F(p) = sum over every contributor i of w_i f_i --
+ * Eq. 1 applied to the feature rows, no Top-K, no renormalisation.
+ * ------------------------------------------------------------------------------- */
+int or_render_vanilla(int n, const double *proj, const double *opac, const double *feat, int D, int npix,
+                      const double *pxy, const double *margin, double *F, int *flags)
+{
+    contrib_t *cand = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)(n > 0 ? n : 1));
+    contrib_t *walk = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)(n > 0 ? n : 1));
+    for (int p = 0; p < npix; ++p) {
+        int fl = 0;
+        double Tf;
+        int nc = pixel_walk(n, proj, opac, pxy[2 * p], pxy[2 * p + 1], margin, cand, walk, &Tf, &fl);
+        double *Fp = F + (size_t)p * D;
+        for (int d = 0; d < D; ++d) Fp[d] = 0.0;
+        for (int i = 0; i < nc; ++i) {
+            const double *f = feat + (size_t)walk[i].g * D;
+            for (int d = 0; d < D; ++d) Fp[d] += walk[i].w * f[d];
+        }
+        flags[p] = fl;
+    }
+    free(cand); free(walk);
+    return 0;
+}

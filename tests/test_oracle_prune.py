@@ -129,3 +129,32 @@ def test_survival_selection_rules():
         pos = cand & (S_ > 0)
         if m <= pos.sum():
             assert not (keep & cand & (S_ == 0)).any()
+
+
+# ----------------------------------------------------------------------------------
+# vanilla (full alpha-blending) feature render
+# ----------------------------------------------------------------------------------
+def test_vanilla_two_stacked_closed_form():
+    """Front A over back B on the axis: F = w_A f_A + w_B f_B with w_A = o_A and
+    w_B = o_B (1 - o_A) -- unnormalised, unlike Top-K's Eq. 3."""
+    cam = axis_cam()
+    oa, ob = 0.3, 0.9
+    fa, fb = np.array([1.0, 0.0, 0.5]), np.array([0.0, 1.0, -0.5])
+    sc = scene_from([[0, 0, 1.5], [0, 0, 2.5]], [iso(0.05)] * 2, [oa, ob], [[1, 0, 0]] * 2, [fa, fb])
+    c = [(cam.height // 2) * cam.width + cam.width // 2]
+    r = oracle.render_vanilla(sc, cam, pixels=c)
+    np.testing.assert_allclose(r["F"][0], oa * fa + ob * (1 - oa) * fb, rtol=1e-14)
+
+
+def test_vanilla_is_scaled_full_topk():
+    """With K at least the contributor count, Top-K renormalises the full blend:
+    F_topK = F_vanilla / (1 - T_final), pixel by pixel (and F_vanilla = 0 where nothing
+    contributes)."""
+    sc = S.random_scene_box(22, 300, 6, box=((-1, 1), (-1, 1), (1.5, 4)), log_scale_mu=-2.5)
+    cam = S.pinhole(32, 24, 40.0)
+    v = oracle.render_vanilla(sc, cam)
+    t = oracle.render(sc, cam, K=400)
+    assert t["n"].max() < 400
+    has = t["n"] > 0
+    np.testing.assert_allclose(v["F"][has], t["F"][has] * (1 - t["T"][has, None]), rtol=1e-12, atol=1e-14)
+    np.testing.assert_array_equal(v["F"][~has], 0.0)
