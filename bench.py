@@ -292,6 +292,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if rank == 0:
         res["prune"] = run_prune(step)
+        res["vanilla"] = run_vanilla(step)
     if rank == 0 and not args.no_e2e:
         res["e2e"] = run_e2e(step, args)
     if rank == 0 and not args.no_batched:
@@ -302,6 +303,37 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
     return res
+
+
+def run_vanilla(step, reps=5):
+    """The full alpha-blending feature render (Tab. 4 'vanilla') of the step's view against
+    the Top-K forward (a1-a3 + a4) on the same inputs, both timed with CUDA events."""
+    import torch
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    F = torch.empty_like(step.out["F"])
+
+    def topk_forward():
+        step.r._select_into(step.N, *step.inp[:4], step.out)
+        step.run_blend_only()
+
+    topk_ms = timed(topk_forward, 10)
+    van_ms = timed(lambda: step.r.forward_vanilla(step.inp[4], F), reps) + timed(
+        lambda: step.r._select_into(step.N, *step.inp[:4], step.out), 10)
+    return {"forward_ms": round(van_ms, 3), "topk_forward_ms": round(topk_ms, 3),
+            "slowdown_vs_topk": round(van_ms / topk_ms, 2),
+            "note": "vanilla = a1-a3 + full alpha-blended D-wide feature over every contributor; "
+                    "topk = a1-a3 + Top-K gather-blend"}
 
 
 def run_prune(step, reps=20):

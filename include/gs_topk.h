@@ -193,6 +193,15 @@ int gs_loss_cos_l1_noalloc(const gs_config *cfg, int64_t n_pix, const void *F, c
                            float w_feat, float w_rgb, float w_depth,
                            void *dL_dF, float *dL_dC, float *dL_dD, float *loss, void *stream);
 
+/* The full alpha-blending feature baseline (Sec. 3.2, Tab. 4 "vanilla"; Feature3DGS's
+ * way of rendering features): F_out[p] = sum over every contributor i of w_i f_i -- Eq. 1
+ * applied to the feature rows, with the walk's own contributor rule, no Top-K and no
+ * renormalisation.  F_out: P x D of cfg->feat_dtype (float32 accumulation).  Call after
+ * gs_bin_sort on the same workspace (it walks the binned tile lists). */
+int gs_feature_blend_vanilla(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                             const float *proj, const void *feats, void *F_out, void *ws, size_t ws_bytes,
+                             void *stream);
+
 /* Consistency-pruning statistics of one rendered view (Sec. 3.3), accumulated into
  * caller-owned per-Gaussian arrays that the caller zeroes at the start of a pruning
  * window and passes for every view of it:

@@ -72,6 +72,8 @@ PROTOTYPES = {
                                              vp, ctypes.c_size_t, vp]),
     "gs_loss_cos_l1_noalloc": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.c_int64, vp, vp, vp, vp, vp, vp,
                                               ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, vp, vp, vp, vp]),
+    "gs_feature_blend_vanilla": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.POINTER(GsCamera), ctypes.c_int32,
+                                                ctypes.c_int32, vp, vp, vp, vp, ctypes.c_size_t, vp]),
     "gs_prune_stats": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.POINTER(GsCamera), ctypes.c_int32,
                                       ctypes.c_int32, vp, vp, vp, ctypes.c_size_t, vp, vp, vp]),
     "gs_prune_select_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),

@@ -341,6 +341,23 @@ int gs_feature_blend_loss(const gs_config *cfg, const gs_camera *cams, int32_t n
     return launch_status();
 }
 
+int gs_feature_blend_vanilla(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                             const float *proj, const void *feats, void *F_out, void *ws, size_t ws_bytes,
+                             void *stream)
+{
+    WsLayout L;
+    if (!make_layout(cfg, cams, n_cams, n_gauss, L)) return GS_ERR_ARG;
+    if ((n_gauss > 0 && (!proj || !feats)) || (L.P > 0 && !F_out)) return GS_ERR_ARG;
+    if (((uintptr_t)feats & 15) != 0 || ((uintptr_t)F_out & 15) != 0) return GS_ERR_ARG;
+    int st = ws_check(L, ws, ws_bytes);
+    if (st) return st;
+    CamTable ct;
+    make_camtable(cfg, cams, n_cams, ct);
+    if (!launch_vanilla(cfg->feat_dtype, ct, L, n_gauss, proj, ws, feats, F_out, (cudaStream_t)stream))
+        return GS_ERR_UNSUPPORTED;
+    return launch_status();
+}
+
 int gs_prune_stats(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss, const float *proj,
                    const int32_t *topk_idx, void *ws, size_t ws_bytes, int32_t *topk_count, float *S, void *stream)
 {

@@ -320,6 +320,8 @@ __host__ __device__ __forceinline__ T *ws_ptr(void *ws, size_t off) { return (T 
 // ------------------------------------------------------------------------------------
 // Host-side launchers implemented in the .cu files
 // ------------------------------------------------------------------------------------
+bool launch_vanilla(int dtype, const CamTable &ct, const WsLayout &L, int N, const float *proj, void *ws,
+                    const void *feats, void *F, cudaStream_t s);
 bool launch_prune_stats(const CamTable &ct, const WsLayout &L, int N, const float *proj, const int *topk_idx,
                         void *ws, int *count, float *S, cudaStream_t s);
 size_t prune_select_ws(int N);

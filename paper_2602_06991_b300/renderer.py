@@ -222,6 +222,21 @@ class TopKRenderer:
             A.check(code, "backward")
         return g
 
+    # ------------------------------------------------------------------ vanilla baseline
+    def forward_vanilla(self, feats, F=None):
+        """Full alpha-blended feature of the last forward's views (gs_feature_blend_vanilla):
+        F = sum over all contributors of w_i f_i -- the baseline Top-K rendering replaces."""
+        st = self.state
+        if st is None:
+            raise RuntimeError("forward_vanilla before forward")
+        N, o = st["N"], st["out"]
+        _need(feats, self.feat_torch_dtype, (N, self.D), "feats")
+        F = F if F is not None else torch.empty(self.P, self.D, dtype=self.feat_torch_dtype, device=self.device)
+        A.check(self.lib.gs_feature_blend_vanilla(ctypes.byref(self.cfg), self.cams, self.n_cams, N, _p(o["proj"]),
+                                                  _p(feats), _p(F), _p(self.ws), self.ws.numel(), self._stream()),
+                "gs_feature_blend_vanilla")
+        return F
+
     # ------------------------------------------------------------------ pruning (Sec. 3.3)
     def alloc_prune_stats(self, N: int):
         """Zeroed accumulators for a pruning window: Top-K count (int32) and S (float32)."""
