@@ -291,6 +291,7 @@ def run_ours(args, rank, world, local_rank):
         "launches_per_step": launches_per_step,
     }
     if rank == 0:
+        res["hybrid"] = run_hybrid(step, ms)
         res["prune"] = run_prune(step)
         res["vanilla"] = run_vanilla(step)
     if rank == 0 and not args.no_e2e:
@@ -303,6 +304,47 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
     return res
+
+
+def run_hybrid(step, full_ms, semantic_every=4):
+    """Hybrid field optimisation (Sec. 3.4): the geometry-only iteration (a1-a3, colour/
+    depth loss, adjoint without its feature part) replayed as a graph, the schedule's
+    mean step time with semantics every `semantic_every` iterations, and the fused Adam
+    step over every parameter tensor of the workload."""
+    import torch
+    from paper_2602_06991_b300 import autotune
+    from paper_2602_06991_b300.hybrid import AdamState, adam_step
+    r = step.r
+    lo = r.loss_geo(step.out["rgb"], step.tgt[1], step.out["depth"], step.tgt[2])
+
+    def geo():
+        r._select_into(step.N, *step.inp[:4], step.out)
+        r.loss_geo(step.out["rgb"], step.tgt[1], step.out["depth"], step.tgt[2], out=lo)
+        r.backward(None, lo["dL_dC"], lo["dL_dD"], grads=step.grads)
+
+    geo_ms = autotune.time_step(lambda: geo, reps=20)
+    avg = ((semantic_every - 1) * geo_ms + full_ms) / semantic_every
+    params = {"mean3d": step.inp[0], "cov3d": step.inp[1], "opacity": step.inp[2], "rgb": step.inp[3]}
+    if step.fdt == "f32":
+        params["feat"] = step.inp[4]
+    st = AdamState(params)
+    grads = {"mean3d": step.grads["mean3d"], "cov3d": step.grads["cov3d"], "opacity": step.grads["opacity"],
+             "rgb": step.grads["rgb"], "feat": step.grads["feat"]}
+    lr = {k: 0.0 for k in params}                     # timing only: parameters unchanged
+    adam_step(params, grads, st, lr)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        adam_step(params, grads, st, lr)
+    e1.record()
+    torch.cuda.synchronize()
+    adam_ms = e0.elapsed_time(e1) / 20
+    n_el = sum(v.numel() for v in params.values())
+    return {"geometry_step_ms": round(geo_ms, 4), "full_step_ms": round(full_ms, 4), "semantic_every": semantic_every,
+            "schedule_mean_step_ms": round(avg, 4), "schedule_Mpix_s": round(step.P / (avg * 1e-3) / 1e6, 3),
+            "adam_ms": round(adam_ms, 4), "adam_elements": n_el,
+            "adam_GBps": round(n_el * 4 * 7 / (adam_ms * 1e-3) / 1e9, 1)}
 
 
 def run_vanilla(step, reps=5):

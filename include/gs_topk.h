@@ -140,7 +140,9 @@ int gs_feature_blend(const gs_config *cfg, int64_t n_pix, int32_t n_gauss, const
 
 /* a5. Adjoint of a1-a4.  Takes the forward inputs and outputs and the upstream
  * gradients dL_dF (P x D, cfg->feat_dtype), dL_dC (P x 3), dL_dD (P), and writes
- * every gradient in `grads`.  The walk is recomputed, not stored; feature gradients
+ * every gradient in `grads`.  dL_dF == NULL is the geometry-only adjoint of the hybrid
+ * schedule (Sec. 3.4): no feature loss, so no feature gradient (feats and grads->feat
+ * are not used and may be NULL) and no feature term in dL/dw.  The walk is recomputed, not stored; feature gradients
  * are reduced per Gaussian after a sort of the Top-K (pixel, slot) pairs by
  * Gaussian, and geometry gradients per (Gaussian, tile) instance, without atomics,
  * so the results are deterministic. */
@@ -192,6 +194,31 @@ int gs_loss_cos_l1_noalloc(const gs_config *cfg, int64_t n_pix, const void *F, c
                            const float *rgb, const float *rgb_gt, const float *depth, const float *depth_gt,
                            float w_feat, float w_rgb, float w_depth,
                            void *dL_dF, float *dL_dC, float *dL_dD, float *loss, void *stream);
+
+/* Geometric reconstruction loss of the hybrid schedule's geometry-only iterations
+ * (Sec. 3.4, Eq. 6 read as in gs_loss_cos_l1 without the feature term): mean over pixels
+ * of w_rgb |C - C_gt|_1 / 3 + w_depth |D - D_gt|, with its gradients dL_dC (P x 3) and
+ * dL_dD (P); loss (1 float, device) summed in a fixed order.  Scratch as gs_loss_cos_l1. */
+int gs_loss_geo_l1(int64_t n_pix, const float *rgb, const float *rgb_gt, const float *depth, const float *depth_gt,
+                   float w_rgb, float w_depth, float *dL_dC, float *dL_dD, float *loss, void *scratch,
+                   size_t scratch_bytes, void *stream);
+
+/* One Adam step over up to GS_ADAM_MAX_TENSORS float32 parameter tensors in a single
+ * launch (the optimiser of the mapping iterations; the paper leaves it to 3DGS):
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps),
+ * element-wise; param, exp_avg (m) and exp_avg_sq (v) are updated in place, step >= 1. */
+#define GS_ADAM_MAX_TENSORS 16
+typedef struct {
+    float *param;
+    const float *grad;
+    float *exp_avg;
+    float *exp_avg_sq;
+    int64_t n;
+    float lr;
+} gs_adam_tensor;
+int gs_adam_step(const gs_adam_tensor *tensors, int32_t n_tensors, int32_t step, float beta1, float beta2, float eps,
+                 void *stream);
 
 /* The full alpha-blending feature baseline (Sec. 3.2, Tab. 4 "vanilla"; Feature3DGS's
  * way of rendering features): F_out[p] = sum over every contributor i of w_i f_i -- Eq. 1

@@ -18,6 +18,9 @@ Functions follow the paper's definitions:
                survival sampling of Eq. 9
   render_vanilla -- the full alpha-blending feature baseline (Sec. 3.2, Tab. 4):
                F = sum over all contributors of w_i f_i
+  adam_step  -- the Adam update (Kingma and Ba, with bias correction) of the mapping
+               iterations, FP64
+  loss_geo   -- the colour/depth L1 loss of the geometry-only iterations and its gradient
 """
 from __future__ import annotations
 
@@ -266,3 +269,23 @@ def render_vanilla(scene, cam, pixels=None, proj=None, margins=DEFAULT_MARGINS, 
     fl, pfl = _i(np.zeros(P))
     L.or_render_vanilla(n, ppr, pop, pft, D, P, ppx, pmg, pF, pfl)
     return dict(F=F, flags=fl)
+
+
+def adam_step(p, g, m, v, lr, beta1, beta2, eps, step):
+    """One Adam step in FP64 (Kingma and Ba, Algorithm 1 with bias correction): returns
+    the new (p, m, v)."""
+    p, g, m, v = (np.asarray(a, np.float64) for a in (p, g, m, v))
+    m = beta1 * m + (1 - beta1) * g
+    v = beta2 * v + (1 - beta2) * g * g
+    mh = m / (1 - beta1 ** step)
+    vh = v / (1 - beta2 ** step)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def loss_geo(C, Cgt, D, Dgt, w_rgb, w_depth):
+    """Mean over pixels of w_rgb |C - C_gt|_1 / 3 + w_depth |D - D_gt| (Eq. 6's L1 terms)
+    and its gradient (sign convention: 0 at equality).  Returns (loss, dC, dD)."""
+    C, Cgt, D, Dgt = (np.asarray(a, np.float64) for a in (C, Cgt, D, Dgt))
+    P = D.shape[0]
+    loss = (w_rgb * np.abs(C - Cgt).sum(1) / 3 + w_depth * np.abs(D - Dgt)).sum() / P
+    return loss, w_rgb / (3 * P) * np.sign(C - Cgt), w_depth / P * np.sign(D - Dgt)

@@ -38,6 +38,14 @@ class GsGrads(ctypes.Structure):
                 ("mean2d", vp), ("conic", vp)]
 
 
+class GsAdamTensor(ctypes.Structure):
+    _fields_ = [("param", vp), ("grad", vp), ("exp_avg", vp), ("exp_avg_sq", vp), ("n", ctypes.c_int64),
+                ("lr", ctypes.c_float)]
+
+
+GS_ADAM_MAX_TENSORS = 16
+
+
 class GsError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -72,6 +80,10 @@ PROTOTYPES = {
                                              vp, ctypes.c_size_t, vp]),
     "gs_loss_cos_l1_noalloc": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.c_int64, vp, vp, vp, vp, vp, vp,
                                               ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, vp, vp, vp, vp]),
+    "gs_loss_geo_l1": (ctypes.c_int, [ctypes.c_int64, vp, vp, vp, vp, ctypes.c_float, ctypes.c_float, vp, vp, vp, vp,
+                                      ctypes.c_size_t, vp]),
+    "gs_adam_step": (ctypes.c_int, [ctypes.POINTER(GsAdamTensor), ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, vp]),
     "gs_feature_blend_vanilla": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.POINTER(GsCamera), ctypes.c_int32,
                                                 ctypes.c_int32, vp, vp, vp, vp, ctypes.c_size_t, vp]),
     "gs_prune_stats": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.POINTER(GsCamera), ctypes.c_int32,

@@ -270,11 +270,15 @@ int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int
 {
     WsLayout L;
     if (!make_layout(cfg, cams, n_cams, n_gauss, L)) return GS_ERR_ARG;
-    if (!grads || !rgb_out || !depth_out || !topk_idx || !topk_w || !dL_dF || !dL_dC || !dL_dD) return GS_ERR_ARG;
-    if (n_gauss > 0 && (!mean3d || !cov3d || !opacity || !rgb || !feats || !proj || !grads->feat ||
-                        !grads->opacity || !grads->rgb || !grads->mean3d || !grads->cov3d))
+    // dL_dF == NULL: geometry-only adjoint (no feature loss): no feature gradient, no
+    // feature term in dL/dw; feats and grads->feat are then not used
+    const bool with_feature = dL_dF != nullptr;
+    if (!grads || !rgb_out || !depth_out || !topk_idx || !topk_w || !dL_dC || !dL_dD) return GS_ERR_ARG;
+    if (n_gauss > 0 && (!mean3d || !cov3d || !opacity || !rgb || !proj || !grads->opacity || !grads->rgb ||
+                        !grads->mean3d || !grads->cov3d || (with_feature && (!feats || !grads->feat))))
         return GS_ERR_ARG;
-    if (((uintptr_t)feats & 15) != 0 || ((uintptr_t)dL_dF & 15) != 0 || ((uintptr_t)grads->feat & 15) != 0)
+    if (with_feature &&
+        (((uintptr_t)feats & 15) != 0 || ((uintptr_t)dL_dF & 15) != 0 || ((uintptr_t)grads->feat & 15) != 0))
         return GS_ERR_ARG;
     int st = ws_check(L, ws, ws_bytes);
     if (st) return st;
@@ -282,10 +286,11 @@ int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int
     cudaStream_t s = (cudaStream_t)stream;
     CamTable ct;
     make_camtable(cfg, cams, n_cams, ct);
-    if (!launch_feature_grad(ct, L, cfg->feat_dtype, n_gauss, topk_idx, topk_w, feats, dL_dF, grads->feat, ws,
-                             s))
+    if (with_feature && !launch_feature_grad(ct, L, cfg->feat_dtype, n_gauss, topk_idx, topk_w, feats, dL_dF,
+                                             grads->feat, ws, s))
         return GS_ERR_UNSUPPORTED;
-    if (!launch_walk_bwd(ct, L, cfg->K, n_gauss, proj, ws, rgb_out, depth_out, topk_idx, topk_w, dL_dC, dL_dD, s))
+    if (!launch_walk_bwd(ct, L, cfg->K, n_gauss, proj, ws, rgb_out, depth_out, topk_idx, topk_w, dL_dC, dL_dD,
+                         with_feature, s))
         return GS_ERR_UNSUPPORTED;
     launch_project_backward(ct, n_gauss, mean3d, cov3d, proj, ws_ptr<uint32_t>(ws, L.elem_off),
                             ws_ptr<uint32_t>(ws, L.elem_cnt), ws_ptr<float>(ws, L.inst_grad),
@@ -338,6 +343,37 @@ int gs_feature_blend_loss(const gs_config *cfg, const gs_camera *cams, int32_t n
                            depth_gt, w_feat, w_rgb, w_depth, F_out, dL_dF, dL_dC, dL_dD, loss, (float *)scratch,
                            ws_ptr<int>(ws, L.header), (cudaStream_t)stream))
         return GS_ERR_UNSUPPORTED;
+    return launch_status();
+}
+
+int gs_loss_geo_l1(int64_t n_pix, const float *rgb, const float *rgb_gt, const float *depth, const float *depth_gt,
+                   float w_rgb, float w_depth, float *dL_dC, float *dL_dD, float *loss, void *scratch,
+                   size_t scratch_bytes, void *stream)
+{
+    if (n_pix < 1 || !rgb || !rgb_gt || !depth || !depth_gt || !dL_dC || !dL_dD || !loss) return GS_ERR_ARG;
+    if (!scratch || ((uintptr_t)scratch & 15) || scratch_bytes < gs_loss_scratch_size(n_pix)) return GS_ERR_WORKSPACE;
+    launch_loss_geo(n_pix, rgb, rgb_gt, depth, depth_gt, w_rgb, w_depth, dL_dC, dL_dD, loss, (float *)scratch,
+                    (cudaStream_t)stream);
+    return launch_status();
+}
+
+int gs_adam_step(const gs_adam_tensor *tensors, int32_t n_tensors, int32_t step, float beta1, float beta2, float eps,
+                 void *stream)
+{
+    if (n_tensors < 0 || n_tensors > GS_ADAM_MAX_TENSORS || step < 1) return GS_ERR_ARG;
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f)) return GS_ERR_ARG;
+    if (n_tensors > 0 && !tensors) return GS_ERR_ARG;
+    AdamTensor t[kAdamMaxTensors];
+    int nt = 0;
+    for (int i = 0; i < n_tensors; ++i) {
+        const gs_adam_tensor &a = tensors[i];
+        if (a.n < 0) return GS_ERR_ARG;
+        if (a.n == 0) continue;
+        if (!a.param || !a.grad || !a.exp_avg || !a.exp_avg_sq) return GS_ERR_ARG;
+        t[nt++] = AdamTensor{a.param, a.grad, a.exp_avg, a.exp_avg_sq, (long long)a.n, a.lr};
+    }
+    if (nt == 0) return GS_OK;
+    launch_adam(t, nt, step, beta1, beta2, eps, (cudaStream_t)stream);
     return launch_status();
 }
 

@@ -322,6 +322,17 @@ __host__ __device__ __forceinline__ T *ws_ptr(void *ws, size_t off) { return (T 
 // ------------------------------------------------------------------------------------
 bool launch_vanilla(int dtype, const CamTable &ct, const WsLayout &L, int N, const float *proj, void *ws,
                     const void *feats, void *F, cudaStream_t s);
+bool launch_loss_geo(long long n_pix, const float *C, const float *Cgt, const float *Dp, const float *Dgt, float wc,
+                     float wd, float *dLdC, float *dLdD, float *loss, float *part, cudaStream_t s);
+struct AdamTensor {
+    float *param;
+    const float *grad;
+    float *m, *v;
+    long long n;
+    float lr;
+};
+constexpr int kAdamMaxTensors = 16;
+bool launch_adam(const AdamTensor *t, int n_tensors, int step, float beta1, float beta2, float eps, cudaStream_t s);
 bool launch_prune_stats(const CamTable &ct, const WsLayout &L, int N, const float *proj, const int *topk_idx,
                         void *ws, int *count, float *S, cudaStream_t s);
 size_t prune_select_ws(int N);
@@ -348,7 +359,7 @@ bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int N, const 
                      cudaStream_t s);
 bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj, void *ws,
                      const float *rgb_out, const float *depth_out, const int *topk_idx, const float *topk_w,
-                     const float *dLdC, const float *dLdD, cudaStream_t s);
+                     const float *dLdC, const float *dLdD, bool with_feature, cudaStream_t s);
 bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, const float *w, const void *feats,
                   void *F, const int *err, cudaStream_t s);
 bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N, const int *topk_idx,

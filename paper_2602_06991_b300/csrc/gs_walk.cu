@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(TW *TH / kBwdPPT) k_walk_bwd(CamTable ct, int 
                     const int id = topk_idx[p * K + k];
                     if (id >= 0) {
                         kid[r][k] = id;
-                        kfp[r][k] = hbuf[p * K + k];
+                        kfp[r][k] = hbuf ? hbuf[p * K + k] : 0.f;    // no feature loss: no term
                         H += topk_w[p * K + k] * inv * kfp[r][k];
                     }
                 }
@@ -354,14 +354,14 @@ bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int N, const 
 
 bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj_f, void *ws,
                      const float *rgb_out, const float *depth_out, const int *topk_idx, const float *topk_w,
-                     const float *dLdC, const float *dLdD, cudaStream_t s)
+                     const float *dLdC, const float *dLdD, bool with_feature, cudaStream_t s)
 {
     const float4 *proj = (const float4 *)proj_f;
     const int *err = ws_ptr<int>(ws, L.header);
     const uint32_t *iv = ws_ptr<uint32_t>(ws, L.inst_vals[L.inst_sorted]);
     const uint32_t *ie = ws_ptr<uint32_t>(ws, L.inst_elem);
     const int2 *rg = ws_ptr<int2>(ws, L.tile_range);
-    const float *h = ws_ptr<float>(ws, L.hbuf);
+    const float *h = with_feature ? ws_ptr<float>(ws, L.hbuf) : nullptr;
     float *ig = ws_ptr<float>(ws, L.inst_grad);
     dim3 grid(ct.n_tiles);
     int KM = k_bucket(K);

@@ -185,15 +185,19 @@ class TopKRenderer:
         return g
 
     def backward(self, dL_dF, dL_dC, dL_dD, grads=None, with_2d=False):
+        """The adjoint (gs_backward).  dL_dF = None is the geometry-only adjoint of the
+        hybrid schedule: no feature loss, so grads['feat'] is left as it is."""
         st = self.state
         if st is None:
             raise RuntimeError("backward before forward")
         N, o = st["N"], st["out"]
-        _need(dL_dF, self.feat_torch_dtype, (self.P, self.D), "dL_dF")
+        if dL_dF is not None:
+            _need(dL_dF, self.feat_torch_dtype, (self.P, self.D), "dL_dF")
         _need(dL_dC, torch.float32, (self.P, 3), "dL_dC")
         _need(dL_dD, torch.float32, (self.P,), "dL_dD")
         g = grads if grads is not None else self.alloc_grads(N, with_2d)
-        gg = A.GsGrads(g["feat"].data_ptr(), g["opacity"].data_ptr(), g["rgb"].data_ptr(), g["mean3d"].data_ptr(),
+        gg = A.GsGrads(g["feat"].data_ptr() if dL_dF is not None else None, g["opacity"].data_ptr(),
+                       g["rgb"].data_ptr(), g["mean3d"].data_ptr(),
                        g["cov3d"].data_ptr(), g["mean2d"].data_ptr() if "mean2d" in g else None,
                        g["conic"].data_ptr() if "conic" in g else None)
         def run():
@@ -221,6 +225,34 @@ class TopKRenderer:
                 code, _ = self.sync_status()
             A.check(code, "backward")
         return g
+
+    # ------------------------------------------------------------------ hybrid schedule (Sec. 3.4)
+    def loss_geo(self, rgb, rgb_gt, depth, depth_gt, w_rgb=1.0, w_depth=1.0, out=None):
+        """Geometric loss of the geometry-only iterations (gs_loss_geo_l1)."""
+        P = self.P
+        o = out if out is not None else dict(
+            dL_dC=torch.empty(P, 3, dtype=torch.float32, device=self.device),
+            dL_dD=torch.empty(P, dtype=torch.float32, device=self.device),
+            loss=torch.empty(1, dtype=torch.float32, device=self.device),
+            scratch=torch.empty(int(self.lib.gs_loss_scratch_size(P)), dtype=torch.uint8, device=self.device))
+        A.check(self.lib.gs_loss_geo_l1(P, _p(rgb), _p(rgb_gt), _p(depth), _p(depth_gt), float(w_rgb), float(w_depth),
+                                        _p(o["dL_dC"]), _p(o["dL_dD"]), _p(o["loss"]), _p(o["scratch"]),
+                                        o["scratch"].numel(), self._stream()), "gs_loss_geo_l1")
+        return o
+
+    def train_step_geometry(self, mean3d, cov3d, opacity, rgb, rgb_gt, depth_gt, out=None, lo=None, grads=None,
+                            weights=(1.0, 1.0)):
+        """A geometry-only iteration: a1-a3, the colour/depth loss, the adjoint without its
+        feature part (the feature gradient is left untouched)."""
+        N = int(mean3d.shape[0])
+        self._ensure_ws(N)
+        o = out if out is not None else self.alloc_outputs(N)
+        self._select_into(N, mean3d, cov3d, opacity, rgb, o)
+        feats = self.state["feats"] if self.state is not None else None
+        self.state = dict(N=N, mean3d=mean3d, cov3d=cov3d, opacity=opacity, rgb=rgb, feats=feats, out=o)
+        lo = self.loss_geo(o["rgb"], rgb_gt, o["depth"], depth_gt, *weights, out=lo)
+        g = self.backward(None, lo["dL_dC"], lo["dL_dD"], grads=grads)
+        return o, lo, g
 
     # ------------------------------------------------------------------ vanilla baseline
     def forward_vanilla(self, feats, F=None):
