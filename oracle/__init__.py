@@ -71,7 +71,7 @@ def _L():
         lib.or_render.argtypes = [i, dp, dp, dp, dp, i, i, i, dp, dp, dp, dp, dp, ip, ip, dp, dp, ip]
         lib.or_backward.argtypes = [i, dp, dp, dp, dp, i, i, i, dp, dp, dp, dp, dp,
                                     dp, dp, dp, dp, dp, dp]
-        lib.or_backward_project.argtypes = [i, dp, dp, dp, dp, dp, dp, dp, dp]
+        lib.or_backward_project.argtypes = [i, dp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         lib.or_pixel_walk.argtypes = [i, dp, dp, ctypes.c_double, ctypes.c_double, dp, i, ip, dp, dp, ip]
         lib.or_prune_stats.argtypes = [i, dp, dp, i, i, dp, dp, ctypes.POINTER(ctypes.c_longlong), dp, ip]
         lib.or_render_vanilla.argtypes = [i, dp, dp, dp, i, i, dp, dp, dp, ip]
@@ -114,12 +114,14 @@ def pixel_centres(cam, pixels=None) -> np.ndarray:
     return np.stack([pixels % cam.width + 0.5, pixels // cam.width + 0.5], axis=1).astype(np.float64)
 
 
-def project(scene, cam) -> np.ndarray:
+def project(scene, cam, cam_arr=None) -> np.ndarray:
+    """EWA projection of every Gaussian; cam_arr (float64, cam_array's layout) overrides
+    the camera -- e.g. a perturbed pose for finite differences."""
     L = _L()
     n = scene.n
     mean, pm = _d(scene.mean3d)
     cov, pc = _d(scene.cov3d)
-    ca, pca = _d(cam_array(cam))
+    ca, pca = _d(cam_array(cam) if cam_arr is None else np.asarray(cam_arr, np.float64))
     out, po = _d(np.zeros((n, PROJ_LEN)))
     L.or_project(n, pm, pc, pca, po)
     return out
@@ -169,13 +171,15 @@ def pixel_walk(scene, cam, px, py, proj=None, margins=DEFAULT_MARGINS, cap=4096)
     return g[:m].copy(), awt[:m, 0].copy(), awt[:m, 1].copy(), awt[:m, 2].copy(), float(Tf[0]), int(fl[0])
 
 
-def backward(scene, cam, K, dF, dC, dD, pixels=None, proj=None, margins=DEFAULT_MARGINS, feats=None):
+def backward(scene, cam, K, dF, dC, dD, pixels=None, proj=None, margins=DEFAULT_MARGINS, feats=None, cam_arr=None):
     """Gradients of L with upstream dL/dF (P, D), dL/dC (P, 3), dL/dD (P,) at the given
     pixels.  Returns per-Gaussian FP64 arrays: mean2d (n,2), conic (n,3), opac (n),
-    rgb (n,3), depth (n), feat (n,D), mean3d (n,3), cov3d (n,6)."""
+    rgb (n,3), depth (n), feat (n,D), mean3d (n,3), cov3d (n,6), and viewmat (3,4): the
+    gradient with respect to the camera's world-to-camera [R | t].  cam_arr overrides
+    the camera array (float64, as cam_array lays it out)."""
     L = _L()
     if proj is None:
-        proj = project(scene, cam)
+        proj = project(scene, cam, cam_arr=cam_arr)
     feats = scene.feats if feats is None else feats
     n, D = scene.n, feats.shape[1]
     pxy, ppx = _d(pixel_centres(cam, pixels))
@@ -195,12 +199,14 @@ def backward(scene, cam, K, dF, dC, dD, pixels=None, proj=None, margins=DEFAULT_
     gz, pgz = _d(np.zeros(n))
     gf, pgf = _d(np.zeros((n, D)))
     L.or_backward(n, ppr, pop, prgb, pft, D, K, P, ppx, pmg, pdF, pdC, pdD, pg2, pgq, pgo, pgr, pgz, pgf)
+    mean, pmean = _d(scene.mean3d)
     cov, pcov = _d(scene.cov3d)
-    ca, pca = _d(cam_array(cam))
+    ca, pca = _d(cam_array(cam) if cam_arr is None else cam_arr)
     gm, pgm = _d(np.zeros((n, 3)))
     gc, pgc = _d(np.zeros((n, 6)))
-    L.or_backward_project(n, pcov, pca, ppr, pg2, pgq, pgz, pgm, pgc)
-    return dict(mean2d=g2, conic=gq, opac=go, rgb=gr, depth=gz, feat=gf, mean3d=gm, cov3d=gc)
+    gv, pgv = _d(np.zeros((3, 4)))
+    L.or_backward_project(n, pmean, pcov, pca, ppr, pg2, pgq, pgz, pgm, pgc, pgv)
+    return dict(mean2d=g2, conic=gq, opac=go, rgb=gr, depth=gz, feat=gf, mean3d=gm, cov3d=gc, viewmat=gv)
 
 
 def prune_stats(scene, cam, K, pixels=None, proj=None, margins=DEFAULT_MARGINS, count=None, maxw=None):

@@ -366,10 +366,12 @@ int or_backward(int n, const double *proj, const double *opac, const double *rgb
 
 /* Chain the 2D gradients back through the projection to the 3D mean and the
  * 3D covariance (6 entries xx, xy, xz, yy, yz, zz; an off-diagonal entry stands for
- * both symmetric positions). */
-int or_backward_project(int n, const double *cov3d, const double *cam, const double *proj,
+ * both symmetric positions), and to the camera: g_view (12, accumulated +=) is the
+ * gradient with respect to the world-to-camera matrix [R | t] (row-major 3 x 4), through
+ * p = R mu + t and through T = J R -- the rendering-loss gradient of a pose refinement. */
+int or_backward_project(int n, const double *mean3d, const double *cov3d, const double *cam, const double *proj,
                         const double *g_mean2d, const double *g_conic, const double *g_depth,
-                        double *g_mean3d, double *g_cov3d)
+                        double *g_mean3d, double *g_cov3d, double *g_view)
 {
     const double *R = cam + CAM_R;
     double fx = cam[CAM_FX], fy = cam[CAM_FY];
@@ -440,6 +442,14 @@ int or_backward_project(int n, const double *cov3d, const double *cam, const dou
         dpz += g_depth[g];
         /* p = R mu + t */
         for (int j = 0; j < 3; ++j) gm[j] = R[0 * 3 + j] * dpx + R[1 * 3 + j] * dpy + R[2 * 3 + j] * dpz;
+        /* the camera: dL/dR_ij = dL/dp_i mu_j + (J^T dL/dT)_ij, dL/dt_i = dL/dp_i */
+        const double dp[3] = {dpx, dpy, dpz};
+        const double *mu = mean3d + 3 * (size_t)g;
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j)
+                g_view[4 * i + j] += dp[i] * mu[j] + J[0][i] * dT[0][j] + J[1][i] * dT[1][j];
+            g_view[4 * i + 3] += dp[i];
+        }
     }
     return 0;
 }

@@ -36,6 +36,9 @@ MUTANTS = {
     "bwd_jacobian_z": ("dpz += dJ[0][0] * (-fx / (z * z));", "dpz += dJ[0][0] * (fx / (z * z));"),
     "prune_counts_all_contributors": ("for (int k = 0; k < m; ++k) count[walk[pos[k]].g] += 1;",
                                       "for (int k = 0; k < nc; ++k) count[walk[k].g] += 1;"),
+    "pose_no_covariance_term": ("g_view[4 * i + j] += dp[i] * mu[j] + J[0][i] * dT[0][j] + J[1][i] * dT[1][j];",
+                                "g_view[4 * i + j] += dp[i] * mu[j];"),
+    "pose_translation_sign": ("g_view[4 * i + 3] += dp[i];", "g_view[4 * i + 3] -= dp[i];"),
     "vanilla_uses_alpha": ("for (int d = 0; d < D; ++d) Fp[d] += walk[i].w * f[d];",
                            "for (int d = 0; d < D; ++d) Fp[d] += walk[i].alpha * f[d];"),
     "prune_importance_is_alpha": ("if (walk[i].w > maxw[walk[i].g]) maxw[walk[i].g] = walk[i].w;",
