@@ -91,6 +91,9 @@ typedef struct {
     float *cov3d;              /* N x 6 (xx, xy, xz, yy, yz, zz); an off-diagonal entry stands for both symmetric entries */
     float *mean2d;             /* n_cams x N x 2, or NULL */
     float *conic;              /* n_cams x N x 3, or NULL */
+    float *viewmat;            /* n_cams x 12, or NULL: the gradient with respect to each camera's world-to-camera
+                                  [R | t] (row-major 3 x 4; through p = R mu + t and the EWA Jacobian term J R),
+                                  summed over the Gaussians in a fixed order -- for rendering-loss pose refinement */
 } gs_grads;
 
 /* Human-readable name of a status code (static string). */

@@ -35,7 +35,7 @@ class GsConfig(ctypes.Structure):
 
 class GsGrads(ctypes.Structure):
     _fields_ = [("feat", vp), ("opacity", vp), ("rgb", vp), ("mean3d", vp), ("cov3d", vp),
-                ("mean2d", vp), ("conic", vp)]
+                ("mean2d", vp), ("conic", vp), ("viewmat", vp)]
 
 
 class GsAdamTensor(ctypes.Structure):

@@ -284,6 +284,7 @@ struct WsLayout {
     size_t scan_aux;           // scan block sums
     size_t inst_grad;          // Mcap x kGradVals floats (per-instance partial 2D gradients)
     size_t elem_grad;          // NE x kGradVals floats (per-element sums of the instance partials)
+    size_t pose_part;          // NE x 12 floats (per-element partial pose gradients)
     size_t pair_keys[2], pair_vals[2];     // N + P K
     size_t hbuf;               // P K floats: dL/dF_p . f_{idx_k}
     size_t seg_start, seg_end; // N each
@@ -352,7 +353,7 @@ void launch_preprocess(const CamTable &ct, int N, const float *mean3d, const flo
                        const float *rgb, float *proj, cudaStream_t s);
 void launch_project_backward(const CamTable &ct, int N, const float *mean3d, const float *cov3d, const float *proj,
                              const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad,
-                             float *elem_grad, const int *err, const gs_grads *gr, cudaStream_t s);
+                             float *elem_grad, const int *err, const gs_grads *gr, float *pose_part, cudaStream_t s);
 void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *proj, void *ws, cudaStream_t s);
 bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj, void *ws,
                      float *rgb_out, float *depth_out, float *T_out, int *n_out, int *idx_out, float *w_out,

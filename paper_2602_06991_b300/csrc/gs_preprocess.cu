@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_project_backward(CamTable ct, int N, co
                                                           const float *__restrict__ cov3d, const float4 *__restrict__ proj,
                                                           const float *__restrict__ elem_grad, const int *err,
                                                           float *g_opac, float *g_rgb, float *g_mean3d, float *g_cov3d,
-                                                          float *g_mean2d, float *g_conic)
+                                                          float *g_mean2d, float *g_conic, float *pose_part)
 {
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= N) return;
@@ -212,7 +212,13 @@ __global__ void __launch_bounds__(256) k_project_backward(CamTable ct, int N, co
             g_conic[3 * e + 1] = acc[3];
             g_conic[3 * e + 2] = acc[4];
         }
-        if (!live) continue;
+        if (!live) {
+            if (pose_part) {
+#pragma unroll
+                for (int k = 0; k < 12; ++k) pose_part[12 * e + k] = 0.f;
+            }
+            continue;
+        }
         go += acc[5];
         gr[0] += acc[6]; gr[1] += acc[7]; gr[2] += acc[8];
         float mu[3] = {mean3d[3 * (size_t)g], mean3d[3 * (size_t)g + 1], mean3d[3 * (size_t)g + 2]};
@@ -276,6 +282,18 @@ __global__ void __launch_bounds__(256) k_project_backward(CamTable ct, int N, co
         dpz += acc[9];
 #pragma unroll
         for (int j = 0; j < 3; ++j) gm[j] += cam.R[0 * 3 + j] * dpx + cam.R[1 * 3 + j] * dpy + cam.R[2 * 3 + j] * dpz;
+        if (pose_part) {
+            // the camera: dL/dR_ij = dL/dp_i mu_j + (J^T dL/dT)_ij, dL/dt_i = dL/dp_i
+            const float J[2][3] = {{cam.fx * iz, 0.f, -cam.fx * geo.rx * iz}, {0.f, cam.fy * iz, -cam.fy * geo.ry * iz}};
+            const float dp[3] = {dpx, dpy, dpz};
+            float *pp = pose_part + 12 * e;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) pp[4 * i + j] = dp[i] * mu[j] + J[0][i] * dT[0][j] + J[1][i] * dT[1][j];
+                pp[4 * i + 3] = dp[i];
+            }
+        }
     }
     g_opac[g] = go;
 #pragma unroll
@@ -295,16 +313,37 @@ void launch_preprocess(const CamTable &ct, int N, const float *mean3d, const flo
     k_preprocess<<<(unsigned)((NE + 255) / 256), 256, 0, s>>>(ct, N, mean3d, cov3d, opac, rgb, (float4 *)proj);
 }
 
+// Pose gradient: per camera, each of its 12 partial columns summed over the Gaussians in a
+// fixed order (each thread a contiguous run, then a tree over the threads).
+__global__ void __launch_bounds__(1024) k_pose_reduce(int N, const float *__restrict__ pose_part, float *g_view)
+{
+    __shared__ float sm[1024];
+    const int c = blockIdx.x / 12, k = blockIdx.x % 12;
+    const int per = (N + 1023) / 1024;
+    const int b = threadIdx.x * per, e = min(b + per, N);
+    float acc = 0.f;
+    for (int g = b; g < e; ++g) acc += pose_part[12 * ((size_t)c * N + g) + k];
+    sm[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) g_view[12 * c + k] = sm[0];
+}
+
 void launch_project_backward(const CamTable &ct, int N, const float *mean3d, const float *cov3d, const float *proj,
                              const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad,
-                             float *elem_grad, const int *err, const gs_grads *gr, cudaStream_t s)
+                             float *elem_grad, const int *err, const gs_grads *gr, float *pose_part, cudaStream_t s)
 {
     if (N <= 0) return;
     long long NE = (long long)ct.n * N;
     k_elem_grad_sum<<<(unsigned)((NE * 32 + 255) / 256), 256, 0, s>>>(NE, elem_off, elem_cnt, inst_grad, err, elem_grad);
+    float *pp = gr->viewmat ? pose_part : nullptr;
     k_project_backward<<<(N + 255) / 256, 256, 0, s>>>(ct, N, mean3d, cov3d, (const float4 *)proj, elem_grad, err,
                                                       gr->opacity, gr->rgb, gr->mean3d, gr->cov3d, gr->mean2d,
-                                                      gr->conic);
+                                                      gr->conic, pp);
+    if (pp) k_pose_reduce<<<ct.n * 12, 1024, 0, s>>>(N, pp, gr->viewmat);
 }
 
 }  // namespace gs

@@ -172,7 +172,7 @@ class TopKRenderer:
         return o, lo, g
 
     # ------------------------------------------------------------------ backward
-    def alloc_grads(self, N: int, with_2d: bool = False):
+    def alloc_grads(self, N: int, with_2d: bool = False, with_pose: bool = False):
         dev = self.device
         g = dict(feat=torch.empty(N, self.D, dtype=torch.float32, device=dev),
                  opacity=torch.empty(N, dtype=torch.float32, device=dev),
@@ -182,9 +182,11 @@ class TopKRenderer:
         if with_2d:
             g["mean2d"] = torch.empty(self.n_cams, N, 2, dtype=torch.float32, device=dev)
             g["conic"] = torch.empty(self.n_cams, N, 3, dtype=torch.float32, device=dev)
+        if with_pose:
+            g["viewmat"] = torch.empty(self.n_cams, 3, 4, dtype=torch.float32, device=dev)
         return g
 
-    def backward(self, dL_dF, dL_dC, dL_dD, grads=None, with_2d=False):
+    def backward(self, dL_dF, dL_dC, dL_dD, grads=None, with_2d=False, with_pose=False):
         """The adjoint (gs_backward).  dL_dF = None is the geometry-only adjoint of the
         hybrid schedule: no feature loss, so grads['feat'] is left as it is."""
         st = self.state
@@ -195,11 +197,12 @@ class TopKRenderer:
             _need(dL_dF, self.feat_torch_dtype, (self.P, self.D), "dL_dF")
         _need(dL_dC, torch.float32, (self.P, 3), "dL_dC")
         _need(dL_dD, torch.float32, (self.P,), "dL_dD")
-        g = grads if grads is not None else self.alloc_grads(N, with_2d)
+        g = grads if grads is not None else self.alloc_grads(N, with_2d, with_pose)
         gg = A.GsGrads(g["feat"].data_ptr() if dL_dF is not None else None, g["opacity"].data_ptr(),
                        g["rgb"].data_ptr(), g["mean3d"].data_ptr(),
                        g["cov3d"].data_ptr(), g["mean2d"].data_ptr() if "mean2d" in g else None,
-                       g["conic"].data_ptr() if "conic" in g else None)
+                       g["conic"].data_ptr() if "conic" in g else None,
+                       g["viewmat"].data_ptr() if "viewmat" in g else None)
         def run():
             A.check(self.lib.gs_backward(ctypes.byref(self.cfg), self.cams, self.n_cams, N, _p(st["mean3d"]),
                                          _p(st["cov3d"]), _p(st["opacity"]), _p(st["rgb"]), _p(st["feats"]),
