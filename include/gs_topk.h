@@ -148,7 +148,13 @@ int gs_feature_blend(const gs_config *cfg, int64_t n_pix, int32_t n_gauss, const
  * are not used and may be NULL) and no feature term in dL/dw.  The walk is recomputed, not stored; feature gradients
  * are reduced per Gaussian after a sort of the Top-K (pixel, slot) pairs by
  * Gaussian, and geometry gradients per (Gaussian, tile) instance, without atomics,
- * so the results are deterministic. */
+ * so the results are deterministic.  Streams: the feature-gradient reduction runs on
+ * a library-owned auxiliary stream of the current device (created by the first call
+ * made outside a stream capture, kept until exit), forked after the work queued on
+ * `stream` and joined back to `stream` before the call returns, so all outputs are
+ * ordered on `stream` as if everything ran there; a call made while `stream` is being
+ * captured uses the auxiliary stream only if it already exists (the fork and join are
+ * then captured), otherwise everything runs on `stream`. */
 int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
                 const float *mean3d, const float *cov3d, const float *opacity, const float *rgb,
                 const void *feats, const float *proj,

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #ifndef GS_BUILT_SM
 #define GS_BUILT_SM 0
@@ -155,6 +156,46 @@ static int launch_status()
     return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }
 
+// Library-owned auxiliary stream of a device, with the fork and join events of one
+// backward call; created on first use, kept until the process exits.
+struct AuxStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int kMaxDevices = 64;
+
+static std::mutex &aux_mutex()
+{
+    static std::mutex m;
+    return m;
+}
+
+// The auxiliary stream of the current device, or nullptr (the caller then runs
+// everything on its own stream): not yet created while `s` is being captured (a
+// creation is not captured work), or creation failed.  Call under aux_mutex().
+static const AuxStream *aux_stream(cudaStream_t s)
+{
+    static AuxStream aux[kMaxDevices];
+    static bool failed[kMaxDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    AuxStream &a = aux[dev];
+    if (a.s) return &a;
+    if (failed[dev]) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    AuxStream n;
+    if (cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&n.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&n.join, cudaEventDisableTiming) != cudaSuccess) {
+        failed[dev] = true;
+        cudaGetLastError();
+        return nullptr;
+    }
+    a = n;
+    return &a;
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -287,16 +328,36 @@ int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int
     cudaStream_t s = (cudaStream_t)stream;
     CamTable ct;
     make_camtable(cfg, cams, n_cams, ct);
-    if (with_feature && !launch_feature_grad(ct, L, cfg->feat_dtype, n_gauss, topk_idx, topk_w, feats, dL_dF,
-                                             grads->feat, ws, s))
-        return GS_ERR_UNSUPPORTED;
-    if (!launch_walk_bwd(ct, L, cfg->K, n_gauss, proj, ws, rgb_out, depth_out, topk_idx, topk_w, dL_dC, dL_dD,
-                         with_feature, s))
-        return GS_ERR_UNSUPPORTED;
-    launch_project_backward(ct, n_gauss, mean3d, cov3d, proj, ws_ptr<uint32_t>(ws, L.elem_off),
-                            ws_ptr<uint32_t>(ws, L.elem_cnt), ws_ptr<float>(ws, L.inst_grad),
-                            ws_ptr<float>(ws, L.elem_grad), ws_ptr<int>(ws, L.header), grads,
-                            ws_ptr<float>(ws, L.pose_part), s);
+    if (with_feature && !L.use_tiles) return GS_ERR_UNSUPPORTED;
+    // Two independent chains: (h, re-walk, projection adjoint) on `stream`, the
+    // feature-gradient reduction on the device's auxiliary stream, forked after the
+    // work already queued on `stream` and joined back before returning.  The re-walk is
+    // issue-bound and the reduction memory-bound, so they overlap.
+    std::unique_lock<std::mutex> lk(aux_mutex());
+    const AuxStream *aux = with_feature ? aux_stream(s) : nullptr;
+    if (aux) {
+        if (cudaEventRecord(aux->fork, s) != cudaSuccess || cudaStreamWaitEvent(aux->s, aux->fork, 0) != cudaSuccess)
+            return GS_ERR_CUDA;
+    }
+    bool ok = true;
+    if (with_feature) {
+        ok = launch_feature_grad(ct, L, cfg->feat_dtype, n_gauss, topk_idx, topk_w, dL_dF, grads->feat, ws,
+                                 aux ? aux->s : s) &&
+             launch_feature_h(L, cfg->feat_dtype, topk_idx, feats, dL_dF, ws, s);
+    }
+    ok = ok && launch_walk_bwd(ct, L, cfg->K, n_gauss, proj, ws, rgb_out, depth_out, topk_idx, topk_w, dL_dC, dL_dD,
+                               with_feature, s);
+    if (ok)
+        launch_project_backward(ct, n_gauss, mean3d, cov3d, proj, ws_ptr<uint32_t>(ws, L.elem_off),
+                                ws_ptr<uint32_t>(ws, L.elem_cnt), ws_ptr<float>(ws, L.inst_grad),
+                                ws_ptr<float>(ws, L.elem_grad), ws_ptr<int>(ws, L.header), grads,
+                                ws_ptr<float>(ws, L.pose_part), s);
+    // the join is queued on every path after a fork, so a capture of `stream` stays whole
+    if (aux) {
+        if (cudaEventRecord(aux->join, aux->s) != cudaSuccess || cudaStreamWaitEvent(s, aux->join, 0) != cudaSuccess)
+            return GS_ERR_CUDA;
+    }
+    if (!ok) return GS_ERR_UNSUPPORTED;
     return launch_status();
 }
 

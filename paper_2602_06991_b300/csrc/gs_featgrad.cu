@@ -214,9 +214,19 @@ __global__ void __launch_bounds__(kFixCols *kFixGroups) k_fgrad_fixup(int D4, co
 bool launch_tile_grad(const CamTable &ct, const WsLayout &L, int dtype, const int *topk_idx, const float *topk_w,
                       const void *dLdF, void *ws, cudaStream_t s);
 
+// h = dL/dF . f per slot, read by the re-walk.
+bool launch_feature_h(const WsLayout &L, int dtype, const int *topk_idx, const void *feats, const void *dLdF,
+                      void *ws, cudaStream_t s)
+{
+    if (!L.use_tiles) return false;
+    return launch_h(dtype, L.K, L.D, L.P, topk_idx, feats, dLdF, ws_ptr<float>(ws, L.hbuf),
+                    ws_ptr<const int>(ws, L.header), s);
+}
+
+// The feature gradient proper: per-block partial rows, then per-Gaussian sums.  It
+// reads only the Top-K record and dL/dF, so it may run beside the re-walk.
 bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N, const int *topk_idx,
-                         const float *topk_w, const void *feats, const void *dLdF, float *grad_feat, void *ws,
-                         cudaStream_t s)
+                         const float *topk_w, const void *dLdF, float *grad_feat, void *ws, cudaStream_t s)
 {
     if (!L.use_tiles) return false;
     uint32_t *hdr = ws_ptr<uint32_t>(ws, L.header);
@@ -234,9 +244,7 @@ bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N
     const float4 *trows = ws_ptr<float4>(ws, L.tile_rows);
     const unsigned nbN = (unsigned)((N + 255) / 256);
 
-    // h = dL/dF . f per slot for the re-walk, then the per-block partial rows
-    if (!launch_h(dtype, L.K, L.D, L.P, topk_idx, feats, dLdF, ws_ptr<float>(ws, L.hbuf), (const int *)hdr, s))
-        return false;
+    // per-block partial rows
     if (!launch_tile_grad(ct, L, dtype, topk_idx, topk_w, dLdF, ws, s)) return false;
     // T4: (Gaussian, row) pairs sorted by Gaussian, segments, pieces
     k_markers<<<nbN, 256, 0, s>>>(N, pk[0], pv[0]);

@@ -363,9 +363,10 @@ bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const 
                      const float *dLdC, const float *dLdD, bool with_feature, cudaStream_t s);
 bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, const float *w, const void *feats,
                   void *F, const int *err, cudaStream_t s);
+bool launch_feature_h(const WsLayout &L, int dtype, const int *topk_idx, const void *feats, const void *dLdF,
+                      void *ws, cudaStream_t s);
 bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N, const int *topk_idx,
-                         const float *topk_w, const void *feats, const void *dLdF, float *grad_feat, void *ws,
-                         cudaStream_t s);
+                         const float *topk_w, const void *dLdF, float *grad_feat, void *ws, cudaStream_t s);
 bool tile_grad_supported(int dtype, int D, int K);
 // Feature-gradient pixel blocks: the largest of 8x8, 8x4, 4x4 whose dL/dF rows fit one
 // 64 KB shared-memory stage ({0, 0}: none).
