@@ -136,7 +136,7 @@ class Step:
         if events: events[1].record()
         r.blend_loss(self.inp[4], self.tgt[0], self.tgt[1], self.tgt[2], lo=self.lo)
         if events: events[2].record()
-        r.backward(self.lo["dL_dF"], self.lo["dL_dC"], self.lo["dL_dD"], grads=self.grads)
+        r.backward(self.lo["dL_dF"], self.lo["dL_dC"], self.lo["dL_dD"], grads=self.grads, h_from_loss=True)
         if events: events[3].record()
 
     def run_blend_only(self):

@@ -162,6 +162,20 @@ int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int
                 const void *dL_dF, const float *dL_dC, const float *dL_dD,
                 const gs_grads *grads, void *ws, size_t ws_bytes, void *stream);
 
+/* gs_backward with options.  flags: 0, or GS_BWD_H_FROM_LOSS -- dL_dF is the gradient
+ * that the last gs_feature_blend_loss call on this workspace wrote, unmodified since:
+ * that call also left the per-slot terms h = dL/dF . f_idx of the re-walk in ws
+ * (computed from rows it had just read), and they are reused instead of being
+ * recomputed from dL_dF.  Passing the flag for any other dL_dF gives wrong gradients.
+ * Unknown flag bits: GS_ERR_ARG. */
+#define GS_BWD_H_FROM_LOSS 1u
+int gs_backward_ex(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                   const float *mean3d, const float *cov3d, const float *opacity, const float *rgb,
+                   const void *feats, const float *proj,
+                   const float *rgb_out, const float *depth_out, const int32_t *topk_idx, const float *topk_w,
+                   const void *dL_dF, const float *dL_dC, const float *dL_dD,
+                   const gs_grads *grads, uint32_t flags, void *ws, size_t ws_bytes, void *stream);
+
 /* Training loss of the benchmark workloads (Eqs. 5-7 leave the weights and the
  * feature distance open; this one takes 1 - cosine for the feature, as the workload
  * specifies): L = w_feat mean_p(1 - cos(F_p, Fgt_p)) + w_rgb mean_p |C_p - Cgt_p|_1 / 3
@@ -178,9 +192,11 @@ int gs_loss_cos_l1(const gs_config *cfg, int64_t n_pix, const void *F, const voi
 
 /* Training form of a4 + loss in one pass (same results as gs_feature_blend followed
  * by gs_loss_cos_l1 on the same inputs, without reading F back): pixels are processed
- * in screen-tile order, so needs the cameras and the workspace of the render (read
- * only: its error word).  Outputs F_out (P x D) and the loss gradients as
- * gs_loss_cos_l1; scratch of gs_loss_scratch_size(P) bytes. */
+ * in screen-tile order, so needs the cameras and the workspace of the render (it reads
+ * the error word).  Outputs F_out (P x D) and the loss gradients as gs_loss_cos_l1;
+ * scratch of gs_loss_scratch_size(P) bytes.  It also writes into ws the re-walk's
+ * per-slot terms h = dL/dF . f for the dL_dF it outputs, which gs_backward_ex with
+ * GS_BWD_H_FROM_LOSS reuses. */
 int gs_feature_blend_loss(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
                           const int32_t *topk_idx, const float *topk_w, const void *feats, const void *F_gt,
                           const float *rgb, const float *rgb_gt, const float *depth, const float *depth_gt,

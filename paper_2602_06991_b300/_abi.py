@@ -12,6 +12,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libgs_topk.so")
 
 GS_OK, GS_ERR_ARG, GS_ERR_WORKSPACE, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_OVERFLOW, GS_ERR_UNSUPPORTED = range(7)
+GS_BWD_H_FROM_LOSS = 1      # gs_backward_ex flag: reuse the h terms gs_feature_blend_loss left in ws
 GS_F32, GS_BF16 = 0, 1
 GS_MAX_CAMERAS = 16
 GS_MAX_K = 32
@@ -70,6 +71,9 @@ PROTOTYPES = {
     "gs_backward": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.POINTER(GsCamera), ctypes.c_int32,
                                    ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                    ctypes.POINTER(GsGrads), vp, ctypes.c_size_t, vp]),
+    "gs_backward_ex": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.POINTER(GsCamera), ctypes.c_int32,
+                                      ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                      ctypes.POINTER(GsGrads), ctypes.c_uint32, vp, ctypes.c_size_t, vp]),
     "gs_loss_scratch_size": (ctypes.c_size_t, [ctypes.c_int64]),
     "gs_loss_cos_l1": (ctypes.c_int, [ctypes.POINTER(GsConfig), ctypes.c_int64, vp, vp, vp, vp, vp, vp,
                                       ctypes.c_float, ctypes.c_float, ctypes.c_float, vp, vp, vp, vp, vp,

@@ -310,6 +310,18 @@ int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int
                 const void *dL_dF, const float *dL_dC, const float *dL_dD,
                 const gs_grads *grads, void *ws, size_t ws_bytes, void *stream)
 {
+    return gs_backward_ex(cfg, cams, n_cams, n_gauss, mean3d, cov3d, opacity, rgb, feats, proj, rgb_out, depth_out,
+                          topk_idx, topk_w, dL_dF, dL_dC, dL_dD, grads, 0u, ws, ws_bytes, stream);
+}
+
+int gs_backward_ex(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
+                   const float *mean3d, const float *cov3d, const float *opacity, const float *rgb,
+                   const void *feats, const float *proj,
+                   const float *rgb_out, const float *depth_out, const int32_t *topk_idx, const float *topk_w,
+                   const void *dL_dF, const float *dL_dC, const float *dL_dD,
+                   const gs_grads *grads, uint32_t flags, void *ws, size_t ws_bytes, void *stream)
+{
+    if (flags & ~(uint32_t)GS_BWD_H_FROM_LOSS) return GS_ERR_ARG;
     WsLayout L;
     if (!make_layout(cfg, cams, n_cams, n_gauss, L)) return GS_ERR_ARG;
     // dL_dF == NULL: geometry-only adjoint (no feature loss): no feature gradient, no
@@ -341,9 +353,12 @@ int gs_backward(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int
     }
     bool ok = true;
     if (with_feature) {
+        // h = dL/dF . f per slot: left in ws by gs_feature_blend_loss when the caller
+        // says dL_dF is that call's and the call took the path that writes it
+        const bool h_ready = (flags & GS_BWD_H_FROM_LOSS) && blend_loss_writes_h(cfg->feat_dtype, cfg->K, cfg->D);
         ok = launch_feature_grad(ct, L, cfg->feat_dtype, n_gauss, topk_idx, topk_w, dL_dF, grads->feat, ws,
                                  aux ? aux->s : s) &&
-             launch_feature_h(L, cfg->feat_dtype, topk_idx, feats, dL_dF, ws, s);
+             (h_ready || launch_feature_h(L, cfg->feat_dtype, topk_idx, feats, dL_dF, ws, s));
     }
     ok = ok && launch_walk_bwd(ct, L, cfg->K, n_gauss, proj, ws, rgb_out, depth_out, topk_idx, topk_w, dL_dC, dL_dD,
                                with_feature, s);
@@ -404,7 +419,7 @@ int gs_feature_blend_loss(const gs_config *cfg, const gs_camera *cams, int32_t n
     make_camtable(cfg, cams, n_cams, ct);
     if (!launch_blend_loss(ct, cfg->feat_dtype, cfg->K, cfg->D, L.P, topk_idx, topk_w, feats, F_gt, rgb, rgb_gt, depth,
                            depth_gt, w_feat, w_rgb, w_depth, F_out, dL_dF, dL_dC, dL_dD, loss, (float *)scratch,
-                           ws_ptr<int>(ws, L.header), (cudaStream_t)stream))
+                           ws_ptr<float>(ws, L.hbuf), ws_ptr<int>(ws, L.header), (cudaStream_t)stream))
         return GS_ERR_UNSUPPORTED;
     return launch_status();
 }

@@ -345,33 +345,13 @@ bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, cons
 // total of pixel (l >> 3) & 3).  Per-pixel form (other widths, K > 16): a group of lanes
 // per pixel, one reduction per slot.
 // ------------------------------------------------------------------------------------
-template <int KM, bool BF16, int CPL>
-__global__ void __launch_bounds__(256) k_h_group(long long n_pix, int K, int nch, const int *__restrict__ idx,
-                                                 const void *__restrict__ feats, const void *__restrict__ dLdF,
-                                                 float *__restrict__ h, const int *__restrict__ err)
+template <int G, bool BF16, int CPL>
+__device__ __forceinline__ void group_h(int U, int nch, int K, int lane, long long p0, const void *__restrict__ feats,
+                                        const GroupTable &t, const float (&d)[G][CPL][Chunk<BF16>::VEC],
+                                        float *__restrict__ h)
 {
     using Ch = Chunk<BF16>;
     constexpr int VEC = Ch::VEC;
-    constexpr int G = Group<KM>::G;
-    __shared__ GroupTable s_t[8];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const long long p0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G;
-    if (p0 >= n_pix) return;                         // whole warp leaves together
-    const bool bad = err && *err;
-    GroupTable &t = s_t[wib];
-    const int U = group_table<KM, G, false>(p0, n_pix, K, idx, nullptr, bad, lane, t);
-    float d[G][CPL][VEC];
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const int ch = lane + 32 * c;
-            if (p0 + g < n_pix && ch < nch) Ch::load(dLdF, (size_t)(p0 + g) * nch + ch, d[g][c]);
-            else {
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) d[g][c][v] = 0.f;
-            }
-        }
     auto load_row = [&](int u, float (&x)[CPL][VEC]) {
         const size_t base = (size_t)t.id[u] * nch;
 #pragma unroll
@@ -418,6 +398,36 @@ __global__ void __launch_bounds__(256) k_h_group(long long n_pix, int K, int nch
             dot_row(u + 1, xb);
         }
     }
+}
+
+template <int KM, bool BF16, int CPL>
+__global__ void __launch_bounds__(256) k_h_group(long long n_pix, int K, int nch, const int *__restrict__ idx,
+                                                 const void *__restrict__ feats, const void *__restrict__ dLdF,
+                                                 float *__restrict__ h, const int *__restrict__ err)
+{
+    using Ch = Chunk<BF16>;
+    constexpr int VEC = Ch::VEC;
+    constexpr int G = Group<KM>::G;
+    __shared__ GroupTable s_t[8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long p0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G;
+    if (p0 >= n_pix) return;                         // whole warp leaves together
+    const bool bad = err && *err;
+    GroupTable &t = s_t[wib];
+    const int U = group_table<KM, G, false>(p0, n_pix, K, idx, nullptr, bad, lane, t);
+    float d[G][CPL][VEC];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int ch = lane + 32 * c;
+            if (p0 + g < n_pix && ch < nch) Ch::load(dLdF, (size_t)(p0 + g) * nch + ch, d[g][c]);
+            else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) d[g][c][v] = 0.f;
+            }
+        }
+    group_h<G, BF16, CPL>(U, nch, K, lane, p0, feats, t, d, h);
 }
 
 template <bool BF16>
@@ -703,7 +713,8 @@ __global__ void __launch_bounds__(256) k_blend_loss_group(long long n_pix, int K
                                                           float wf, float wc, float wd, float invP,
                                                           void *__restrict__ F, void *__restrict__ dLdF,
                                                           float *__restrict__ dLdC, float *__restrict__ dLdD,
-                                                          float *__restrict__ part, const int *__restrict__ err)
+                                                          float *__restrict__ part, float *__restrict__ h,
+                                                          const int *__restrict__ err)
 {
     using Ch = Chunk<BF16>;
     constexpr int VEC = Ch::VEC;
@@ -720,7 +731,13 @@ __global__ void __launch_bounds__(256) k_blend_loss_group(long long n_pix, int K
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         const long long p = p0 + g;
-        if (p >= n_pix) break;                      // warp-uniform
+        if (p >= n_pix) {                           // warp-uniform
+#pragma unroll
+            for (int c = 0; c < CPL; ++c)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[g][c][v] = 0.f;
+            continue;
+        }
         float gt[CPL][VEC];
         float ff = 0.f, fg = 0.f, gg = 0.f;
 #pragma unroll
@@ -761,6 +778,13 @@ __global__ void __launch_bounds__(256) k_blend_loss_group(long long n_pix, int K
 #pragma unroll
                 for (int v = 0; v < VEC; ++v) gdx[v] = fmaf(ca, gt[c][v], cb * acc[g][c][v]);
                 Ch::store(dLdF, (size_t)p * nch + ch, gdx);
+                // acc now holds dL/dF as stored, for h below
+#pragma unroll
+                for (int v = 0; v < VEC; ++v)
+                    acc[g][c][v] = BF16 ? __bfloat162float(__float2bfloat16(gdx[v])) : gdx[v];
+            } else {
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) acc[g][c][v] = 0.f;
             }
         }
         if (lane == g) {
@@ -776,18 +800,20 @@ __global__ void __launch_bounds__(256) k_blend_loss_group(long long n_pix, int K
             part[p] = (wf * (1.f - cosv) + wc * lc / 3.f + wd * fabsf(dd)) * invP;
         }
     }
+    // the re-walk's per-slot terms h = dL/dF . f, from rows the blend just read (L2)
+    if (h) group_h<G, BF16, CPL>(U, nch, K, lane, p0, feats, t, acc, h);
 }
 
 template <int KM, bool BF16>
 static void blend_loss_group_launch(int cpl, unsigned blocks, cudaStream_t s, long long n_pix, int K, int nch,
                                     const int *idx, const float *w, const void *feats, const void *Fgt, const float *C,
                                     const float *Cgt, const float *Dp, const float *Dgt, float wf, float wc, float wd,
-                                    float invP, void *F, void *dLdF, float *dLdC, float *dLdD, float *part,
+                                    float invP, void *F, void *dLdF, float *dLdC, float *dLdD, float *part, float *h,
                                     const int *err)
 {
 #define GS_BLGC(CP)                                                                                                   \
     k_blend_loss_group<KM, BF16, CP><<<blocks, 256, 0, s>>>(n_pix, K, nch, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, wf, wc, \
-                                                            wd, invP, F, dLdF, dLdC, dLdD, part, err)
+                                                            wd, invP, F, dLdF, dLdC, dLdD, part, h, err)
     switch (cpl) {
     case 1: GS_BLGC(1); break;
     case 2: GS_BLGC(2); break;
@@ -820,10 +846,15 @@ static bool blend_loss_cpl(int cpl, unsigned blocks, long long n_pix, int K, int
     return false;
 }
 
+bool blend_loss_writes_h(int dtype, int K, int D)
+{
+    return group_cpl(dtype, K, dtype == GS_BF16 ? D / 8 : D / 4) != 0;
+}
+
 bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_pix, const int *idx, const float *w,
                        const void *feats, const void *Fgt, const float *C, const float *Cgt, const float *Dp,
                        const float *Dgt, float wf, float wc, float wd, void *F, void *dLdF, float *dLdC, float *dLdD,
-                       float *loss, float *part, const int *err, cudaStream_t s)
+                       float *loss, float *part, float *h, const int *err, cudaStream_t s)
 {
     (void)ct;
     if (n_pix <= 0) return true;
@@ -844,7 +875,7 @@ bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_
         const unsigned gblocks = (unsigned)((gw * 32 + 255) / 256);
 #define GS_BLG(KMV, BF)                                                                                          \
     blend_loss_group_launch<KMV, BF>(gcpl, gblocks, s, n_pix, K, nch, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, wf, wc, \
-                                     wd, invP, F, dLdF, dLdC, dLdD, part, err)
+                                     wd, invP, F, dLdF, dLdC, dLdD, part, h, err)
         if (dtype == GS_BF16) {
             switch (KM) { case 4: GS_BLG(4, true); break; case 8: GS_BLG(8, true); break; default: GS_BLG(16, true); }
         } else {

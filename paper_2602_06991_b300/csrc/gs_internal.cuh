@@ -378,10 +378,13 @@ size_t tile_runs_bytes(int B, int K);
 void retile(const CamTable &ct, int bw, int bh, CamTable &out);
 bool launch_h(int dtype, int K, int D, long long n_pix, const int *idx, const void *feats, const void *dLdF,
               float *h, const int *err, cudaStream_t s);
+// The fused training form also writes h = dL/dF . f per Top-K slot (into `h`) when it
+// takes the pixel-group path; blend_loss_writes_h says whether it does.
+bool blend_loss_writes_h(int dtype, int K, int D);
 bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_pix, const int *idx, const float *w,
                        const void *feats, const void *Fgt, const float *C, const float *Cgt, const float *Dp,
                        const float *Dgt, float wf, float wc, float wd, void *F, void *dLdF, float *dLdC, float *dLdD,
-                       float *loss, float *part, const int *err, cudaStream_t s);
+                       float *loss, float *part, float *h, const int *err, cudaStream_t s);
 bool launch_loss(int dtype, int D, long long n_pix, const void *F, const void *Fgt, const float *C, const float *Cgt,
                  const float *Dp, const float *Dgt, float wf, float wc, float wd, void *dLdF, float *dLdC,
                  float *dLdD, float *loss, float *part, cudaStream_t s);

@@ -127,6 +127,7 @@ class TopKRenderer:
 
     def _select_into(self, N, mean3d, cov3d, opacity, rgb, o):
         """a1-a3 only (projection, binning, Top-K walk)."""
+        self._h_valid = False                    # a new Top-K (or workspace): no h from a loss
         L, cfg, s = self.lib, ctypes.byref(self.cfg), self._stream()
         ws, wsb = _p(self.ws), self.ws.numel()
         A.check(L.gs_preprocess(cfg, self.cams, self.n_cams, N, _p(mean3d), _p(cov3d), _p(opacity), _p(rgb),
@@ -156,6 +157,8 @@ class TopKRenderer:
             float(w_depth), _p(o["F"]), _p(lo["dL_dF"]), _p(lo["dL_dC"]), _p(lo["dL_dD"]), _p(lo["loss"]),
             _p(self.ws), self.ws.numel(), _p(lo["scratch"]), lo["scratch"].numel(), self._stream()),
             "gs_feature_blend_loss")
+        # that call also left h = dL/dF . f in the workspace for this dL_dF
+        self._loss_dLdF, self._h_valid = lo["dL_dF"].data_ptr(), True
         return lo
 
     def train_step(self, mean3d, cov3d, opacity, rgb, feats, F_gt, rgb_gt, depth_gt, out=None, lo=None, grads=None,
@@ -168,7 +171,7 @@ class TopKRenderer:
         self._select_into(N, mean3d, cov3d, opacity, rgb, o)
         self.state = dict(N=N, mean3d=mean3d, cov3d=cov3d, opacity=opacity, rgb=rgb, feats=feats, out=o)
         lo = self.blend_loss(feats, F_gt, rgb_gt, depth_gt, *weights, lo=lo)
-        g = self.backward(lo["dL_dF"], lo["dL_dC"], lo["dL_dD"], grads=grads)
+        g = self.backward(lo["dL_dF"], lo["dL_dC"], lo["dL_dD"], grads=grads, h_from_loss=True)
         return o, lo, g
 
     # ------------------------------------------------------------------ backward
@@ -186,12 +189,18 @@ class TopKRenderer:
             g["viewmat"] = torch.empty(self.n_cams, 3, 4, dtype=torch.float32, device=dev)
         return g
 
-    def backward(self, dL_dF, dL_dC, dL_dD, grads=None, with_2d=False, with_pose=False):
-        """The adjoint (gs_backward).  dL_dF = None is the geometry-only adjoint of the
-        hybrid schedule: no feature loss, so grads['feat'] is left as it is."""
+    def backward(self, dL_dF, dL_dC, dL_dD, grads=None, with_2d=False, with_pose=False, h_from_loss=False):
+        """The adjoint (gs_backward_ex).  dL_dF = None is the geometry-only adjoint of the
+        hybrid schedule: no feature loss, so grads['feat'] is left as it is.
+        h_from_loss: dL_dF is the tensor the last blend_loss wrote, unmodified since, so
+        the per-slot terms that call left in the workspace are reused (recomputed if a
+        capacity retry has replaced the workspace since)."""
         st = self.state
         if st is None:
             raise RuntimeError("backward before forward")
+        if h_from_loss and (dL_dF is None or getattr(self, "_loss_dLdF", None) != dL_dF.data_ptr()):
+            raise ValueError("h_from_loss: dL_dF is not the gradient the last blend_loss wrote")
+        h_reuse = h_from_loss and getattr(self, "_h_valid", False)
         N, o = st["N"], st["out"]
         if dL_dF is not None:
             _need(dL_dF, self.feat_torch_dtype, (self.P, self.D), "dL_dF")
@@ -203,14 +212,14 @@ class TopKRenderer:
                        g["cov3d"].data_ptr(), g["mean2d"].data_ptr() if "mean2d" in g else None,
                        g["conic"].data_ptr() if "conic" in g else None,
                        g["viewmat"].data_ptr() if "viewmat" in g else None)
-        def run():
-            A.check(self.lib.gs_backward(ctypes.byref(self.cfg), self.cams, self.n_cams, N, _p(st["mean3d"]),
-                                         _p(st["cov3d"]), _p(st["opacity"]), _p(st["rgb"]), _p(st["feats"]),
-                                         _p(o["proj"]), _p(o["rgb"]), _p(o["depth"]), _p(o["topk_idx"]),
-                                         _p(o["topk_w"]), _p(dL_dF), _p(dL_dC), _p(dL_dD), ctypes.byref(gg),
-                                         _p(self.ws), self.ws.numel(), self._stream()), "gs_backward")
+        def run(flags):
+            A.check(self.lib.gs_backward_ex(ctypes.byref(self.cfg), self.cams, self.n_cams, N, _p(st["mean3d"]),
+                                            _p(st["cov3d"]), _p(st["opacity"]), _p(st["rgb"]), _p(st["feats"]),
+                                            _p(o["proj"]), _p(o["rgb"]), _p(o["depth"]), _p(o["topk_idx"]),
+                                            _p(o["topk_w"]), _p(dL_dF), _p(dL_dC), _p(dL_dD), ctypes.byref(gg),
+                                            flags, _p(self.ws), self.ws.numel(), self._stream()), "gs_backward_ex")
 
-        run()
+        run(A.GS_BWD_H_FROM_LOSS if h_reuse else 0)
         if self.check_overflow:
             # the per-block partial feature rows have a capacity that grows with
             # max_instances: on overflow, grow it, redo a1-a3 into the new workspace (same
@@ -224,7 +233,7 @@ class TopKRenderer:
                 self.ws = None
                 self._ensure_ws(N)
                 self._select_into(N, st["mean3d"], st["cov3d"], st["opacity"], st["rgb"], o)
-                run()
+                run(0)                  # the new workspace holds no h from the loss
                 code, _ = self.sync_status()
             A.check(code, "backward")
         return g

@@ -179,3 +179,37 @@ def test_backward_feature_block_shapes(D, K, dtype):
     print("block shapes", D, K, dtype, errs)
     for k, e in errs.items():
         assert e <= U.GRAD_TOL, (k, e, errs)
+
+
+@pytest.mark.parametrize("case", ["small_f32", "bf16_groups", "per_pixel_path"])
+def test_backward_reuses_loss_h(case):
+    """gs_backward_ex with GS_BWD_H_FROM_LOSS reuses the per-slot h = dL/dF . f that the
+    fused blend + loss left in the workspace; the gradients are bit-identical to the
+    call that recomputes h from dL_dF.  'per_pixel_path' (K = 32) takes the blend path
+    that writes no h, so the flag must fall back to recomputing it.  A dL_dF other than
+    the loss's own is refused by the binding."""
+    if case == "small_f32":
+        sc, cams, K, tile, _ = S.make_config("small", 5)
+        dtype = "f32"
+    else:
+        D, K, dtype = (768, 16, "bf16") if case == "bf16_groups" else (136, 32, "f32")
+        sc = S.random_scene_box(21, 1500, D, box=((-1, 1), (-1, 1), (2, 4)))
+        cams = S.orbit_cameras(22, [(45, 29, 50.0), (38, 31, 45.0)], radius=3.0)
+        tile = (16, 16)
+    # capacity for the partial feature rows up front, so no retry replaces the workspace
+    r, ts, out = U.gpu_forward(sc, cams, K, tile, feat_dtype=dtype, max_instances=256 * len(cams) * sc.n)
+    P = sum(c.n_pix for c in cams)
+    g = torch.Generator().manual_seed(23)
+    F_gt = torch.randn(P, sc.d, generator=g).cuda().to(r.feat_torch_dtype)
+    C_gt = torch.rand(P, 3, generator=g).cuda()
+    D_gt = (2 + 2 * torch.rand(P, generator=g)).cuda()
+    lo = r.blend_loss(ts[4], F_gt, C_gt, D_gt)
+    ga = {k: v.clone() for k, v in r.backward(lo["dL_dF"], lo["dL_dC"], lo["dL_dD"], with_2d=True).items()}
+    assert r._h_valid, "a capacity retry replaced the workspace"
+    gb = r.backward(lo["dL_dF"], lo["dL_dC"], lo["dL_dD"], with_2d=True, h_from_loss=True)
+    torch.cuda.synchronize()
+    for k in ga:
+        assert torch.equal(ga[k], gb[k]), k
+    assert float(ga["feat"].abs().sum()) > 0 and float(ga["opacity"].abs().sum()) > 0
+    with pytest.raises(ValueError):
+        r.backward(lo["dL_dF"].clone(), lo["dL_dC"], lo["dL_dD"], h_from_loss=True)
