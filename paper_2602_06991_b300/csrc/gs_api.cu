@@ -114,7 +114,7 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     for (int i = 0; i < 2; ++i) L.inst_vals[i] = take(u * L.Mcap);
     L.inst_elem = take(u * L.Mcap);
     L.tile_range = take(8 * (size_t)L.n_tiles);
-    L.sort_hist = take(u * 256 * (kSortBlocks + 1));
+    L.sort_hist = take(u * 256 * (kRadixBlocks + 1));
     L.scan_aux = take(u * (kSortBlocks + 32));
     L.inst_grad = take(sizeof(float) * kGradVals * L.Mcap);
     L.elem_grad = take(sizeof(float) * kGradVals * L.NE);

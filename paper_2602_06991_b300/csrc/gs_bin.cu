@@ -7,7 +7,7 @@
 //   3. emit one instance per (element, tile), in depth order, keyed by global tile id;
 //   4. stable radix sort of the instances by tile id -> within a tile, depth order
 //      (ties keep element order, i.e. ascending Gaussian id within a camera);
-//   5. per-tile [start, end) ranges.
+//   5. per-tile [start, end) ranges (a search per tile over the sorted keys).
 // The instance count is only known on the device; every launch after step 2 reads it
 // from the workspace header, so nothing synchronises with the host.
 #include "gs_internal.cuh"
@@ -93,15 +93,39 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
     }
 }
 
-__global__ void k_tile_ranges(const uint32_t *__restrict__ keys, const uint32_t *n_dev, uint32_t mcap, int2 *ranges,
-                              uint32_t n_tiles)
+// Per-tile [start, end) of the sorted instances: one warp per tile finds the first
+// position whose key is >= its tile id by a 32-way search over the sorted keys (a few
+// dependent steps instead of a pass over every instance); that position ends the
+// previous tile's range.  Empty tiles get start == end.
+__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t *__restrict__ keys, const uint32_t *n_dev,
+                                                     uint32_t mcap, int2 *ranges, uint32_t n_tiles)
 {
-    uint32_t n = min(*n_dev, mcap);
-    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
-        uint32_t t = keys[m];
-        if (t >= n_tiles) continue;
-        if (m == 0 || keys[m - 1] != t) ranges[t].x = (int)m;
-        if (m + 1 == n || keys[m + 1] != t) ranges[t].y = (int)(m + 1);
+    const uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= n_tiles) return;                       // whole warp
+    const uint32_t n = min(*n_dev, mcap);
+    uint32_t lo = 0, hi = n;                        // the answer lies in [lo, hi]
+    while (hi - lo > 32) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t pos = lo + (uint32_t)lane * step;
+        const bool valid = pos < hi;
+        const unsigned less = __ballot_sync(0xffffffffu, valid && keys[pos] < t);
+        const unsigned probes = __ballot_sync(0xffffffffu, valid);
+        const int c = __popc(less);
+        if (c == 0) {
+            hi = lo;
+            break;
+        }
+        const uint32_t nlo = lo + (uint32_t)(c - 1) * step + 1;
+        hi = c < __popc(probes) ? lo + (uint32_t)c * step : hi;
+        lo = nlo;
+    }
+    const uint32_t pos = lo + (uint32_t)lane;
+    const uint32_t first = lo + (uint32_t)__popc(__ballot_sync(0xffffffffu, pos < hi && keys[pos] < t));
+    if (lane == 0) {
+        ranges[t].x = (int)first;
+        if (t > 0) ranges[t - 1].y = (int)first;
+        if (t + 1 == n_tiles) ranges[t].y = (int)n;
     }
 }
 
@@ -131,8 +155,8 @@ void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *
     uint32_t *inst_elem = ws_ptr<uint32_t>(ws, L.inst_elem);
     int2 *ranges = ws_ptr<int2>(ws, L.tile_range);
 
-    cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
     if (NE <= 0) {
+        cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
         cudaMemsetAsync(n_inst, 0, sizeof(uint32_t), s);
         return;
     }
@@ -145,7 +169,8 @@ void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *
                                   elem_off, elem_cnt, err);
     int icur = radix_sort_pairs(ik[0], ik[1], iv[0], iv[1], L.Mcap, n_inst, bits_for(L.n_tiles), hist, s);
     (void)icur;   // equals L.inst_sorted
-    k_tile_ranges<<<148 * 4, 256, 0, s>>>(ik[L.inst_sorted], n_inst, (uint32_t)L.Mcap, ranges, (uint32_t)L.n_tiles);
+    k_tile_ranges<<<(unsigned)(((long long)L.n_tiles * 32 + 255) / 256), 256, 0, s>>>(
+        ik[L.inst_sorted], n_inst, (uint32_t)L.Mcap, ranges, (uint32_t)L.n_tiles);
 }
 
 }  // namespace gs

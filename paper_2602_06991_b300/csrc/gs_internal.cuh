@@ -26,6 +26,7 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 elements per tile
 constexpr int kSortBlocks = 296;                       // 2 per SM on a 148-SM B300
+constexpr int kRadixBlocks = 592;                      // radix passes: 4 per SM, one wave
 constexpr int kPieceLen = 16;                          // partial rows per feature-gradient work piece
 constexpr int kGradVals = 10;                          // per-instance partial 2D gradient
 
@@ -280,7 +281,7 @@ struct WsLayout {
     size_t inst_keys[2], inst_vals[2];     // Mcap
     size_t inst_elem;          // Mcap
     size_t tile_range;         // n_tiles x int2
-    size_t sort_hist;          // kSortBlocks x 256
+    size_t sort_hist;          // (kRadixBlocks + 1) x 256
     size_t scan_aux;           // scan block sums
     size_t inst_grad;          // Mcap x kGradVals floats (per-instance partial 2D gradients)
     size_t elem_grad;          // NE x kGradVals floats (per-element sums of the instance partials)

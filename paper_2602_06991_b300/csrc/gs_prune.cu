@@ -182,7 +182,7 @@ size_t prune_select_ws(int N)
 {
     auto a = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t u = sizeof(uint32_t);
-    return a(256) + 4 * a(u * (size_t)(N > 0 ? N : 1)) + a(u * 256 * (kSortBlocks + 1));
+    return a(256) + 4 * a(u * (size_t)(N > 0 ? N : 1)) + a(u * 256 * (kRadixBlocks + 1));
 }
 
 bool launch_prune_select(int N, const int *count, const float *S, int tau, double ratio, const float *expo,
@@ -196,7 +196,7 @@ bool launch_prune_select(int N, const int *count, const float *S, int tau, doubl
     uint32_t *k1 = (uint32_t *)((char *)k0 + vec);
     uint32_t *v0 = (uint32_t *)((char *)k1 + vec);
     uint32_t *v1 = (uint32_t *)((char *)v0 + vec);
-    uint32_t *hist = (uint32_t *)((char *)v1 + vec);
+    uint32_t *hist = (uint32_t *)((char *)v1 + vec);         // (kRadixBlocks + 1) x 256
     cudaMemsetAsync(hdr, 0, 256, s);
     const unsigned nb = (unsigned)((N + 255) / 256);
     k_prune_keys<<<nb, 256, 0, s>>>(N, count, S, tau, expo, k0, v0, hdr);

@@ -3,8 +3,9 @@
 // Radix sort: least-significant-digit, 8-bit digits, reduce-then-scan per pass:
 //   upsweep   : each block counts the digits of its contiguous range of tiles;
 //   scan      : one block turns the (digit-major, block-minor) counts into offsets;
-//   downsweep : each block ranks its keys stably (warp match + per-warp counters) and
-//               scatters them to their final positions.
+//   downsweep : each block ranks its keys stably (warp match + per-warp counters),
+//               reorders each tile by digit in shared memory and writes every digit's
+//               run to consecutive final positions.
 // No block waits on another, so nothing can spin.  Stability makes the multi-pass
 // sort correct and keeps equal keys in input order (used to keep depth order within
 // a tile, and to put each Gaussian's marker entry first in its segment).
@@ -55,13 +56,17 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_upsweep(const uint32_t *__r
 }
 
 // Offsets of a pass, step 1: one CTA per digit d scans that digit's counts over the
-// G blocks (hist[b][d] becomes the exclusive prefix over blocks 0..b-1) and writes the
-// digit total to hist[G][d].  The downsweep adds the prefix of the digit totals.
+// G blocks (hist[b][d] becomes the exclusive prefix over blocks 0..b-1; each thread
+// takes a contiguous run of blocks) and writes the digit total to hist[G][d].  The
+// downsweep adds the prefix of the digit totals.
 __global__ void __launch_bounds__(512) k_rs_scan(uint32_t *hist, int G)
 {
     __shared__ uint32_t warp_sums[16];
     const int d = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    uint32_t v = t < G ? hist[(size_t)t * 256 + d] : 0u;
+    const int per = (G + 511) / 512;
+    const int b0 = min(t * per, G), b1 = min(b0 + per, G);
+    uint32_t v = 0;
+    for (int b = b0; b < b1; ++b) v += hist[(size_t)b * 256 + d];
     uint32_t inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -70,14 +75,15 @@ __global__ void __launch_bounds__(512) k_rs_scan(uint32_t *hist, int G)
     }
     if (lane == 31) warp_sums[warp] = inc;
     __syncthreads();
-    uint32_t before = 0, total = 0;
-    for (int w = 0; w < 16; ++w) {
-        uint32_t x = warp_sums[w];
-        before += w < warp ? x : 0u;
-        total += x;
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += warp_sums[w];
+    uint32_t run = inc - v + before;
+    for (int b = b0; b < b1; ++b) {
+        const uint32_t x = hist[(size_t)b * 256 + d];
+        hist[(size_t)b * 256 + d] = run;
+        run += x;
     }
-    if (t < G) hist[(size_t)t * 256 + d] = inc - v + before;
-    if (t == 0) hist[(size_t)G * 256 + d] = total;
+    if (t == 511) hist[(size_t)G * 256 + d] = run;   // the last run ends at block G
 }
 
 // Exclusive scan in place of len uint32 by one block of 1024 threads.
@@ -116,15 +122,22 @@ __global__ void __launch_bounds__(1024) k_scan_single(uint32_t *data, int len, u
     if (total && tid == 1023) *total = run;
 }
 
+// Downsweep of a pass: per tile of kSortTile keys, stable ranks (warp match +
+// per-warp digit counters), then the tile is reordered by digit in shared memory and
+// written out in that order, so each digit's run of the tile goes to consecutive
+// addresses (coalesced) instead of one scattered store per key.
 __global__ void __launch_bounds__(kSortThreads) k_rs_downsweep(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                                uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                                long long n_host, const uint32_t *n_dev, int shift,
                                                                const uint32_t *__restrict__ hist)
 {
     constexpr int W = kSortThreads / 32;
-    __shared__ uint32_t s_base[256];
-    __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_base[256];     // global position of this block's next key of each digit
+    __shared__ uint32_t s_tot[W];
+    __shared__ uint32_t s_start[256];    // first position of each digit in the reordered tile
+    __shared__ uint32_t s_wsum[W];
     __shared__ uint32_t s_wcnt[W][257];
+    __shared__ uint32_t s_k[kSortTile], s_v[kSortTile];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     {
@@ -170,27 +183,49 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_downsweep(const uint32_t *_
             lr[i] = before + __popc(peers & lt_mask);
         }
         __syncthreads();
+        uint32_t run = 0;
         {
-            uint32_t run = 0;
 #pragma unroll
             for (int w = 0; w < W; ++w) {
                 uint32_t c = s_wcnt[w][tid];
                 s_wcnt[w][tid] = run;
                 run += c;
             }
-            s_tot[tid] = run;
+            // exclusive prefix of the tile's digit counts over the digits
+            uint32_t inc = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) s_wsum[warp] = inc;
+            __syncthreads();
+            uint32_t before = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) before += w < warp ? s_wsum[w] : 0u;
+            s_start[tid] = inc - run + before;
         }
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
             if (dg[i] < 256) {
-                uint32_t pos = s_base[dg[i]] + s_wcnt[warp][dg[i]] + lr[i];
-                kout[pos] = k[i];
-                vout[pos] = v[i];
+                const uint32_t lp = s_start[dg[i]] + s_wcnt[warp][dg[i]] + lr[i];
+                s_k[lp] = k[i];
+                s_v[lp] = v[i];
             }
         }
         __syncthreads();
-        s_base[tid] += s_tot[tid];
+        const long long rem = n - t * kSortTile;
+        const int cnt = rem < kSortTile ? (int)rem : kSortTile;
+        for (int j = tid; j < cnt; j += kSortThreads) {
+            const uint32_t kk = s_k[j];
+            const int d = (int)((kk >> shift) & 255u);
+            const uint32_t pos = s_base[d] + (uint32_t)j - s_start[d];
+            kout[pos] = kk;
+            vout[pos] = s_v[j];
+        }
+        __syncthreads();
+        s_base[tid] += run;
     }
 }
 
@@ -200,7 +235,7 @@ int radix_sort_pairs(uint32_t *keys0, uint32_t *keys1, uint32_t *vals0, uint32_t
     if (n_host <= 0 || n_bits <= 0) return 0;
     int passes = (n_bits + 7) / 8;
     long long n_tiles = (n_host + kSortTile - 1) / kSortTile;
-    int G = (int)(n_tiles < kSortBlocks ? n_tiles : kSortBlocks);
+    int G = (int)(n_tiles < kRadixBlocks ? n_tiles : kRadixBlocks);
     uint32_t *kb[2] = {keys0, keys1}, *vb[2] = {vals0, vals1};
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
