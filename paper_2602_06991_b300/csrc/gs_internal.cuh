@@ -272,8 +272,11 @@ struct TopK {
 // ------------------------------------------------------------------------------------
 // Workspace layout (host-computed; all offsets 256-byte aligned)
 // ------------------------------------------------------------------------------------
+constexpr int kHdrWalkTiles = 16;   // header word: next tile of the persistent re-walk
+
 struct WsLayout {
-    size_t header;             // 256 B: [0] error word, [1] instance count, [2] pieces, [3..] bbox
+    size_t header;             // 256 B: [0] error word, [1] instance count, [2] pieces, [3] multi-piece
+                               // segments, [8] partial rows, [9] pairs, [16] re-walk tile counter
     size_t depth_keys[2], depth_vals[2];   // NE
     size_t elem_cnt;           // NE (tiles touched, per element)
     size_t elem_off;           // NE (first pre-sort instance of each element)

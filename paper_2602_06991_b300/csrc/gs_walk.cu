@@ -20,6 +20,8 @@
 // and written once per (Gaussian, tile) instance: no atomics, deterministic.
 #include "gs_internal.cuh"
 
+#include <algorithm>
+
 namespace gs {
 
 template <int TW, int TH, int KM>
@@ -120,10 +122,12 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
 
 // PPT vertically adjacent pixels per thread: a thread sums its pixels' contributions to
 // a staged Gaussian in registers, so each warp-level reduction covers 32 PPT pixels.
-constexpr int kBwdPPT = 2;
+constexpr int kBwdPPT = 2;                       // 4 was measured slower (more registers, fewer warps)
+// pixels per thread of a TW x TH tile: kBwdPPT while that leaves at least one warp
+__host__ __device__ constexpr int bwd_ppt(int tw, int th) { return tw * th / kBwdPPT >= 32 ? kBwdPPT : tw * th / 32; }
 
 template <int TW, int TH, int KM>
-__global__ void __launch_bounds__(TW *TH / kBwdPPT) k_walk_bwd(CamTable ct, int K, int N, const float4 *__restrict__ proj,
+__global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable ct, int K, int N, const float4 *__restrict__ proj,
                                                               const uint32_t *__restrict__ inst_vals,
                                                               const uint32_t *__restrict__ inst_elem,
                                                               const int2 *__restrict__ ranges, const int *__restrict__ err,
@@ -134,9 +138,10 @@ __global__ void __launch_bounds__(TW *TH / kBwdPPT) k_walk_bwd(CamTable ct, int 
                                                               const float *__restrict__ hbuf,
                                                               const float *__restrict__ dLdC,
                                                               const float *__restrict__ dLdD,
-                                                              float *__restrict__ inst_grad)
+                                                              float *__restrict__ inst_grad,
+                                                              unsigned *__restrict__ tile_counter)
 {
-    constexpr int PPT = kBwdPPT;
+    constexpr int PPT = bwd_ppt(TW, TH);
     constexpr int NT = TW * TH / PPT;
     constexpr int NW = NT / 32;
     constexpr int BB = 64;                       // Gaussians per staged batch
@@ -145,159 +150,167 @@ __global__ void __launch_bounds__(TW *TH / kBwdPPT) k_walk_bwd(CamTable ct, int 
     __shared__ uint32_t s_o[BB];
     __shared__ float s_red[NW][BB][kGradVals];
     __shared__ int s_jend[NW];
+    __shared__ int s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
-    const int c = cam_of_tile(ct, tile);
-    const CamDev &cam = ct.c[c];
-    const int lt = tile - cam.tile_off;
-    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    int2 rg = ranges[tile];
-    if (*err) rg.y = rg.x;
-    const int px = tx * TW + (tid % TW);
-    const float pxf = (float)px + 0.5f;
+    // persistent: each CTA takes the next unprocessed tile until none is left
+    for (;;) {
+        if (tid == 0) s_tile = (int)atomicAdd(tile_counter, 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= ct.n_tiles) break;               // block-uniform
+        const int c = cam_of_tile(ct, tile);
+        const CamDev &cam = ct.c[c];
+        const int lt = tile - cam.tile_off;
+        const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+        int2 rg = ranges[tile];
+        if (*err) rg.y = rg.x;
+        const int px = tx * TW + (tid % TW);
+        const float pxf = (float)px + 0.5f;
 
-    float pyf[PPT], dC0[PPT], dC1[PPT], dC2[PPT], dD[PPT], total[PPT], T[PPT], prefix[PPT];
-    int kid[PPT][KM];
-    float kfp[PPT][KM];
-    bool pdone[PPT];
-#pragma unroll
-    for (int r = 0; r < PPT; ++r) {
-        const int py = ty * TH + (tid / TW) * PPT + r;
-        pyf[r] = (float)py + 0.5f;
-        const bool inside = px < cam.W && py < cam.H;
-        pdone[r] = !inside;
-        T[r] = 1.f;
-        prefix[r] = 0.f;
-        dC0[r] = dC1[r] = dC2[r] = dD[r] = total[r] = 0.f;
-#pragma unroll
-        for (int k = 0; k < KM; ++k) { kid[r][k] = -2; kfp[r][k] = 0.f; }
-        if (inside) {
-            const long long p = cam.pix_off + (long long)py * cam.W + px;
-            dC0[r] = dLdC[3 * p]; dC1[r] = dLdC[3 * p + 1]; dC2[r] = dLdC[3 * p + 2];
-            dD[r] = dLdD[p];
-            total[r] = dC0[r] * rgb_out[3 * p] + dC1[r] * rgb_out[3 * p + 1] + dC2[r] * rgb_out[3 * p + 2] +
-                       dD[r] * depth_out[p];
-            float S = 0.f;
-#pragma unroll
-            for (int k = 0; k < KM; ++k)
-                if (k < K) S += topk_w[p * K + k];
-            const float inv = S > 0.f ? 1.f / S : 0.f;
-            float H = 0.f;
-#pragma unroll
-            for (int k = 0; k < KM; ++k) {
-                if (k < K) {
-                    const int id = topk_idx[p * K + k];
-                    if (id >= 0) {
-                        kid[r][k] = id;
-                        kfp[r][k] = hbuf ? hbuf[p * K + k] : 0.f;    // no feature loss: no term
-                        H += topk_w[p * K + k] * inv * kfp[r][k];
+        float pyf[PPT], dC0[PPT], dC1[PPT], dC2[PPT], dD[PPT], total[PPT], T[PPT], prefix[PPT];
+        int kid[PPT][KM];
+        float kfp[PPT][KM];
+        bool pdone[PPT];
+    #pragma unroll
+        for (int r = 0; r < PPT; ++r) {
+            const int py = ty * TH + (tid / TW) * PPT + r;
+            pyf[r] = (float)py + 0.5f;
+            const bool inside = px < cam.W && py < cam.H;
+            pdone[r] = !inside;
+            T[r] = 1.f;
+            prefix[r] = 0.f;
+            dC0[r] = dC1[r] = dC2[r] = dD[r] = total[r] = 0.f;
+    #pragma unroll
+            for (int k = 0; k < KM; ++k) { kid[r][k] = -2; kfp[r][k] = 0.f; }
+            if (inside) {
+                const long long p = cam.pix_off + (long long)py * cam.W + px;
+                dC0[r] = dLdC[3 * p]; dC1[r] = dLdC[3 * p + 1]; dC2[r] = dLdC[3 * p + 2];
+                dD[r] = dLdD[p];
+                total[r] = dC0[r] * rgb_out[3 * p] + dC1[r] * rgb_out[3 * p + 1] + dC2[r] * rgb_out[3 * p + 2] +
+                           dD[r] * depth_out[p];
+                float S = 0.f;
+    #pragma unroll
+                for (int k = 0; k < KM; ++k)
+                    if (k < K) S += topk_w[p * K + k];
+                const float inv = S > 0.f ? 1.f / S : 0.f;
+                float H = 0.f;
+    #pragma unroll
+                for (int k = 0; k < KM; ++k) {
+                    if (k < K) {
+                        const int id = topk_idx[p * K + k];
+                        if (id >= 0) {
+                            kid[r][k] = id;
+                            kfp[r][k] = hbuf ? hbuf[p * K + k] : 0.f;    // no feature loss: no term
+                            H += topk_w[p * K + k] * inv * kfp[r][k];
+                        }
                     }
                 }
-            }
-#pragma unroll
-            for (int k = 0; k < KM; ++k) kfp[r][k] = (kfp[r][k] - H) * inv;
-        }
-    }
-    auto all_done = [&]() {
-        bool d = true;
-#pragma unroll
-        for (int r = 0; r < PPT; ++r) d = d && pdone[r];
-        return d;
-    };
-    const int cN = c * N;
-    for (int b0 = rg.x; b0 < rg.y; b0 += BB) {
-        if (__syncthreads_count(!all_done()) == 0) {
-            // every pixel stopped: the remaining instances of this tile contribute nothing
-            for (int m = b0 + tid; m < rg.y; m += NT) {
-                float *dst = inst_grad + (size_t)kGradVals * inst_vals[m];
-#pragma unroll
-                for (int v = 0; v < kGradVals; ++v) dst[v] = 0.f;
-            }
-            break;
-        }
-        for (int t = tid; t < BB; t += NT) {
-            if (b0 + t < rg.y) {
-                const uint32_t o = inst_vals[b0 + t];
-                const uint32_t e = inst_elem[o];
-                const float4 *rr = proj + 4 * (size_t)e;
-                s_r0[t] = rr[0];
-                s_r1[t] = rr[1];
-                s_r2[t] = rr[2];
-                s_r3[t] = rr[3];
-                s_g[t] = (int)e - cN;
-                s_o[t] = o;
+    #pragma unroll
+                for (int k = 0; k < KM; ++k) kfp[r][k] = (kfp[r][k] - H) * inv;
             }
         }
-        __syncthreads();
-        const int cnt = min(BB, rg.y - b0);
-        // a warp whose pixels have all stopped leaves the batch; the per-tile sum below
-        // counts its entries only up to that point
-        int j_end = cnt;
-        for (int j = 0; j < cnt; ++j) {
-            if (__all_sync(0xffffffffu, all_done())) {
-                j_end = j;
+        auto all_done = [&]() {
+            bool d = true;
+    #pragma unroll
+            for (int r = 0; r < PPT; ++r) d = d && pdone[r];
+            return d;
+        };
+        const int cN = c * N;
+        for (int b0 = rg.x; b0 < rg.y; b0 += BB) {
+            if (__syncthreads_count(!all_done()) == 0) {
+                // every pixel stopped: the remaining instances of this tile contribute nothing
+                for (int m = b0 + tid; m < rg.y; m += NT) {
+                    float *dst = inst_grad + (size_t)kGradVals * inst_vals[m];
+    #pragma unroll
+                    for (int v = 0; v < kGradVals; ++v) dst[v] = 0.f;
+                }
                 break;
             }
-            float v[kGradVals];
-#pragma unroll
-            for (int i = 0; i < kGradVals; ++i) v[i] = 0.f;
-            bool contrib = false;
-            const float4 r0 = s_r0[j], r1 = s_r1[j];
-#pragma unroll
-            for (int r = 0; r < PPT; ++r) {
-                if (pdone[r]) continue;
-                float dx, dy;
-                const float q = eval_q(pxf, pyf[r], r0, r1, dx, dy);
-                if (q > kQMax) continue;
-                float G, ao;
-                const float alpha = eval_alpha(q, r1.w, G, ao);
-                if (alpha < kAlphaMin) continue;
-                const float test_T = __fmul_rn(T[r], __fsub_rn(1.f, alpha));
-                if (test_T < kTStop) {
-                    pdone[r] = true;
-                    continue;
+            for (int t = tid; t < BB; t += NT) {
+                if (b0 + t < rg.y) {
+                    const uint32_t o = inst_vals[b0 + t];
+                    const uint32_t e = inst_elem[o];
+                    const float4 *rr = proj + 4 * (size_t)e;
+                    s_r0[t] = rr[0];
+                    s_r1[t] = rr[1];
+                    s_r2[t] = rr[2];
+                    s_r3[t] = rr[3];
+                    s_g[t] = (int)e - cN;
+                    s_o[t] = o;
                 }
-                contrib = true;
-                const float w = __fmul_rn(alpha, T[r]);
-                const float4 r2 = s_r2[j];
-                const int gid = s_g[j];
-                float fp = 0.f;
-#pragma unroll
-                for (int k = 0; k < KM; ++k) fp = (kid[r][k] == gid) ? kfp[r][k] : fp;
-                const float gi = dC0[r] * r2.x + dC1[r] * r2.y + dC2[r] * r2.z + dD[r] * r2.w + fp;
-                prefix[r] = fmaf(gi, w, prefix[r]);
-                const float suffix = total[r] - prefix[r];
-                const float dalpha = gi * T[r] - __fdividef(suffix, 1.f - alpha);
-                v[6] += w * dC0[r]; v[7] += w * dC1[r]; v[8] += w * dC2[r]; v[9] += w * dD[r];
-                if (ao < kAlphaClamp) {
-                    const float4 r3 = s_r3[j];
-                    v[5] += dalpha * G;
-                    const float dq = -0.5f * alpha * dalpha;
-                    v[2] += dq * dx * dx;
-                    v[3] += dq * 2.f * dx * dy;
-                    v[4] += dq * dy * dy;
-                    v[0] += -2.f * dq * (r3.x * dx + r3.y * dy);
-                    v[1] += -2.f * dq * (r3.y * dx + r3.z * dy);
-                }
-                T[r] = test_T;
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                const float d = warp_reduce10(v, lane);
-                const int vi = vidx10(lane);
-                if (!(lane & 1) && vi >= 0) s_red[warp][j][vi] = d;
-            } else if (lane < kGradVals) {
-                s_red[warp][j][lane] = 0.f;
+            __syncthreads();
+            const int cnt = min(BB, rg.y - b0);
+            // a warp whose pixels have all stopped leaves the batch; the per-tile sum below
+            // counts its entries only up to that point
+            int j_end = cnt;
+            for (int j = 0; j < cnt; ++j) {
+                if (__all_sync(0xffffffffu, all_done())) {
+                    j_end = j;
+                    break;
+                }
+                float v[kGradVals];
+    #pragma unroll
+                for (int i = 0; i < kGradVals; ++i) v[i] = 0.f;
+                bool contrib = false;
+                const float4 r0 = s_r0[j], r1 = s_r1[j];
+    #pragma unroll
+                for (int r = 0; r < PPT; ++r) {
+                    if (pdone[r]) continue;
+                    float dx, dy;
+                    const float q = eval_q(pxf, pyf[r], r0, r1, dx, dy);
+                    if (q > kQMax) continue;
+                    float G, ao;
+                    const float alpha = eval_alpha(q, r1.w, G, ao);
+                    if (alpha < kAlphaMin) continue;
+                    const float test_T = __fmul_rn(T[r], __fsub_rn(1.f, alpha));
+                    if (test_T < kTStop) {
+                        pdone[r] = true;
+                        continue;
+                    }
+                    contrib = true;
+                    const float w = __fmul_rn(alpha, T[r]);
+                    const float4 r2 = s_r2[j];
+                    const int gid = s_g[j];
+                    float fp = 0.f;
+    #pragma unroll
+                    for (int k = 0; k < KM; ++k) fp = (kid[r][k] == gid) ? kfp[r][k] : fp;
+                    const float gi = dC0[r] * r2.x + dC1[r] * r2.y + dC2[r] * r2.z + dD[r] * r2.w + fp;
+                    prefix[r] = fmaf(gi, w, prefix[r]);
+                    const float suffix = total[r] - prefix[r];
+                    const float dalpha = gi * T[r] - __fdividef(suffix, 1.f - alpha);
+                    v[6] += w * dC0[r]; v[7] += w * dC1[r]; v[8] += w * dC2[r]; v[9] += w * dD[r];
+                    if (ao < kAlphaClamp) {
+                        const float4 r3 = s_r3[j];
+                        v[5] += dalpha * G;
+                        const float dq = -0.5f * alpha * dalpha;
+                        v[2] += dq * dx * dx;
+                        v[3] += dq * 2.f * dx * dy;
+                        v[4] += dq * dy * dy;
+                        v[0] += -2.f * dq * (r3.x * dx + r3.y * dy);
+                        v[1] += -2.f * dq * (r3.y * dx + r3.z * dy);
+                    }
+                    T[r] = test_T;
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    const float d = warp_reduce10(v, lane);
+                    const int vi = vidx10(lane);
+                    if (!(lane & 1) && vi >= 0) s_red[warp][j][vi] = d;
+                } else if (lane < kGradVals) {
+                    s_red[warp][j][lane] = 0.f;
+                }
+            }
+            if (lane == 0) s_jend[warp] = j_end;
+            __syncthreads();
+            for (int i = tid; i < cnt * kGradVals; i += NT) {
+                const int j = i / kGradVals, vi = i - j * kGradVals;
+                float sum = 0.f;
+    #pragma unroll
+                for (int w = 0; w < NW; ++w) sum += j < s_jend[w] ? s_red[w][j][vi] : 0.f;
+                inst_grad[(size_t)kGradVals * s_o[j] + vi] = sum;
             }
         }
-        if (lane == 0) s_jend[warp] = j_end;
-        __syncthreads();
-        for (int i = tid; i < cnt * kGradVals; i += NT) {
-            const int j = i / kGradVals, vi = i - j * kGradVals;
-            float sum = 0.f;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) sum += j < s_jend[w] ? s_red[w][j][vi] : 0.f;
-            inst_grad[(size_t)kGradVals * s_o[j] + vi] = sum;
-        }
+        __syncthreads();                         // shared state is free for the next tile
     }
 }
 
@@ -320,14 +333,26 @@ template <int TW, int TH>
 static bool walk_bwd_k(int KM, dim3 grid, cudaStream_t s, const CamTable &ct, int K, int N, const float4 *proj,
                        const uint32_t *iv, const uint32_t *ie, const int2 *rg, const int *err, const float *C,
                        const float *Dp, const int *ti, const float *tw, const float *h, const float *dC,
-                       const float *dD, float *ig)
+                       const float *dD, float *ig, unsigned *ctr)
 {
-    constexpr int B = TW * TH / kBwdPPT;
+    constexpr int B = TW * TH / bwd_ppt(TW, TH);
+    auto go = [&](auto kern) {
+        // persistent grid: the resident CTAs per SM times the SMs (a tile counter hands
+        // out the tiles, so uneven tiles balance across CTAs)
+        int dev = 0, sms = 148, occ = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, B, 0);
+        const long long want = (long long)sms * std::max(1, occ);
+        const unsigned g = (unsigned)std::min<long long>(want, grid.x);
+        cudaMemsetAsync(ctr, 0, sizeof(unsigned), s);
+        kern<<<g, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig, ctr);
+    };
     switch (KM) {
-    case 4: k_walk_bwd<TW, TH, 4><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig); return true;
-    case 8: k_walk_bwd<TW, TH, 8><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig); return true;
-    case 16: k_walk_bwd<TW, TH, 16><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig); return true;
-    case 32: k_walk_bwd<TW, TH, 32><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig); return true;
+    case 4: go(k_walk_bwd<TW, TH, 4>); return true;
+    case 8: go(k_walk_bwd<TW, TH, 8>); return true;
+    case 16: go(k_walk_bwd<TW, TH, 16>); return true;
+    case 32: go(k_walk_bwd<TW, TH, 32>); return true;
     }
     return false;
 }
@@ -363,12 +388,13 @@ bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const 
     const int2 *rg = ws_ptr<int2>(ws, L.tile_range);
     const float *h = with_feature ? ws_ptr<float>(ws, L.hbuf) : nullptr;
     float *ig = ws_ptr<float>(ws, L.inst_grad);
+    unsigned *ctr = ws_ptr<unsigned>(ws, L.header) + kHdrWalkTiles;
     dim3 grid(ct.n_tiles);
     int KM = k_bucket(K);
-    if (ct.tile_w == 16 && ct.tile_h == 16) return walk_bwd_k<16, 16>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig);
-    if (ct.tile_w == 32 && ct.tile_h == 8) return walk_bwd_k<32, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig);
-    if (ct.tile_w == 16 && ct.tile_h == 8) return walk_bwd_k<16, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig);
-    if (ct.tile_w == 8 && ct.tile_h == 8) return walk_bwd_k<8, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig);
+    if (ct.tile_w == 16 && ct.tile_h == 16) return walk_bwd_k<16, 16>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, ctr);
+    if (ct.tile_w == 32 && ct.tile_h == 8) return walk_bwd_k<32, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, ctr);
+    if (ct.tile_w == 16 && ct.tile_h == 8) return walk_bwd_k<16, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, ctr);
+    if (ct.tile_w == 8 && ct.tile_h == 8) return walk_bwd_k<8, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, ctr);
     return false;
 }
 
