@@ -85,15 +85,18 @@ __global__ void k_multi_flags(int N, const uint32_t *__restrict__ multi, uint32_
 
 // Zero gradient rows of the Gaussians selected nowhere: one thread per float4 of the
 // N x D gradient, a grid-stride streaming fill.
+// Zero rows for the Gaussians no pixel selected: one warp per row, grid-stride over the
+// Gaussians, 16-byte stores.
 __global__ void __launch_bounds__(256) k_zero_unselected(int N, int D4, const uint32_t *__restrict__ seg_start,
                                                          const uint32_t *__restrict__ seg_end,
                                                          float4 *__restrict__ grad_f)
 {
-    const long long total = (long long)N * D4;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int g = (int)(i / D4);
-        if (seg_end[g] == seg_start[g]) grad_f[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < N; g += nwarps) {
+        if (seg_end[g] != seg_start[g]) continue;          // warp-uniform
+        float4 *row = grad_f + g * D4;
+        for (int c = lane; c < D4; c += 32) row[c] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 

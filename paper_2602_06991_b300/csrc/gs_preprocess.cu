@@ -171,9 +171,14 @@ __global__ void __launch_bounds__(256) k_elem_grad_sum(long long NE, const uint3
     if (*err == 0) {
         const uint32_t o0 = elem_off[e], n = elem_cnt[e];
         for (uint32_t i = lane; i < n; i += 32) {
-            const float *pg = inst_grad + kGradVals * (size_t)(o0 + i);
+            // 40-byte record, 8-byte aligned: five 8-byte loads
+            const float2 *pg = (const float2 *)(inst_grad + kGradVals * (size_t)(o0 + i));
 #pragma unroll
-            for (int k = 0; k < kGradVals; ++k) v[k] += pg[k];
+            for (int k = 0; k < kGradVals / 2; ++k) {
+                const float2 x = __ldg(pg + k);
+                v[2 * k] += x.x;
+                v[2 * k + 1] += x.y;
+            }
         }
     }
     float d = warp_reduce16(v, lane);
