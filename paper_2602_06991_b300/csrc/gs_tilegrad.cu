@@ -179,6 +179,129 @@ __global__ void __launch_bounds__(1024) k_tile_slots(CamTable ct, int K, int nso
     }
 }
 
+// T1, warp form (fewer than 2^22 Gaussians, at most 512 slots): one warp per block.
+// The slots' 32-bit keys (id << 9 | slot) are sorted in registers by a bitonic network
+// (KPT keys per lane, element e = lane KPT + r; strides below KPT inside a lane, the
+// others across lanes by shuffles), so no shared-memory round trip or block barrier
+// sits in the sort.  Same order, records and runs as k_tile_slots.
+template <int TW, int TH, int KPT>
+__global__ void __launch_bounds__(128) k_tile_slots_warp(CamTable ct, int K, const int *__restrict__ topk_idx,
+                                                         const float *__restrict__ topk_w, const int *__restrict__ err,
+                                                         uint2 *__restrict__ rec, uint2 *__restrict__ runs,
+                                                         uint32_t *__restrict__ tile_u)
+{
+    constexpr int B = TW * TH;
+    constexpr int NS = 32 * KPT;
+    constexpr uint32_t kNone = 0xffffffffu;
+    __shared__ float s_w[4][NS];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int tile = blockIdx.x * 4 + wib;
+    if (tile >= ct.n_tiles) return;                          // whole warp
+    const int nslots = B * K;
+    float *w = s_w[wib];
+    const int c = cam_of_tile(ct, tile);
+    const CamDev &cam = ct.c[c];
+    const int lt = tile - cam.tile_off;
+    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+    const bool bad = *err != 0;
+    uint32_t key[KPT];
+#pragma unroll
+    for (int r = 0; r < KPT; ++r) {
+        const int i = lane * KPT + r;
+        key[r] = kNone;
+        if (i < nslots) {
+            float wi = 0.f;
+            const int pl = i / K, k = i - pl * K;
+            const int px = tx * TW + (pl % TW), py = ty * TH + (pl / TW);
+            if (!bad && px < cam.W && py < cam.H) {
+                const long long p = cam.pix_off + (long long)py * cam.W + px;
+                const int id = topk_idx[p * K + k];
+                wi = topk_w[p * K + k];
+                if (id >= 0) key[r] = ((uint32_t)id << 9) | (uint32_t)i;
+            }
+            w[i] = wi;
+        }
+    }
+    __syncwarp();
+    // renormalised weights w' = w / S per pixel (S in slot order)
+    for (int pl = lane; pl < B; pl += 32) {
+        float S = 0.f;
+        for (int k = 0; k < K; ++k) S += w[pl * K + k];
+        const float inv = S > 0.f ? 1.f / S : 0.f;
+        for (int k = 0; k < K; ++k) w[pl * K + k] *= inv;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int size = 2; size <= NS; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= KPT) {
+                const int lm = stride / KPT;
+                const bool lower = (lane & lm) == 0;
+#pragma unroll
+                for (int r = 0; r < KPT; ++r) {
+                    const bool up = ((lane * KPT + r) & size) == 0;
+                    const uint32_t o = __shfl_xor_sync(0xffffffffu, key[r], lm);
+                    key[r] = (lower == up) ? min(key[r], o) : max(key[r], o);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < KPT; ++r) {
+                    if ((r & stride) == 0) {
+                        const bool up = ((lane * KPT + r) & size) == 0;
+                        const uint32_t a = key[r], b = key[r | stride];
+                        key[r] = up ? min(a, b) : max(a, b);
+                        key[r | stride] = up ? max(a, b) : min(a, b);
+                    }
+                }
+            }
+        }
+    }
+    // run starts (valid keys sort first), their exclusive scan over the lanes
+    const uint32_t before_lane = __shfl_up_sync(0xffffffffu, key[KPT - 1], 1);
+    bool st[KPT];
+    int starts = 0, valid = 0;
+#pragma unroll
+    for (int r = 0; r < KPT; ++r) {
+        const uint32_t pk = r ? key[r - 1] : before_lane;
+        const bool v = key[r] != kNone;
+        st[r] = v && ((lane == 0 && r == 0) || (pk >> 9) != (key[r] >> 9));
+        starts += st[r];
+        valid += v;
+    }
+    int inc = starts, vtot = valid;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+        vtot += __shfl_xor_sync(0xffffffffu, vtot, o);
+    }
+    const int U = __shfl_sync(0xffffffffu, inc, 31);
+    int u = inc - starts - 1;
+    uint2 *brec = rec + (size_t)tile * nslots;
+    uint2 *bruns = runs + (size_t)tile * runs_stride(nslots);
+#pragma unroll
+    for (int r = 0; r < KPT; ++r) {
+        const int e = lane * KPT + r;
+        if (e < nslots) {
+            uint2 rr = make_uint2(0u, 0u);
+            if (key[r] != kNone) {
+                if (st[r]) {
+                    ++u;
+                    bruns[u] = make_uint2((uint32_t)e, key[r] >> 9);
+                }
+                const int sl = (int)(key[r] & 511u);
+                rr = make_uint2((uint32_t)(sl / K) | ((uint32_t)u << 16), __float_as_uint(w[sl]));
+            }
+            brec[e] = rr;
+        }
+    }
+    if (lane == 0) {
+        tile_u[tile] = (uint32_t)U;
+        bruns[U] = make_uint2((uint32_t)vtot, 0u);
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // T3: per-block accumulation from shared-memory stages filled by TMA
 // ------------------------------------------------------------------------------------
@@ -187,7 +310,7 @@ constexpr int kBlkNW = kBlkNT / 32;
 constexpr int kTmaInner = 256;                       // elements per TMA box row (box limit)
 constexpr long long kWaitCycles = 2000000000ll;      // bounded mbarrier wait (~1 s)
 
-struct alignas(64) TmaMaps {
+struct TmaMaps {
     CUtensorMap m[GS_MAX_CAMERAS];                   // dL/dF of each camera as [H][W][D]
 };
 
@@ -571,10 +694,23 @@ static bool tile_launch(const CamTable &cb, const WsLayout &L, int dtype, const 
     uint32_t *pv = ws_ptr<uint32_t>(ws, L.pair_vals[0]);
     uint32_t *aux = ws_ptr<uint32_t>(ws, L.scan_aux);
     const int nsort = tile_sort_len(B * L.K);
-    const size_t sm1 = (sizeof(unsigned long long) + sizeof(float)) * nsort;
-    const int nt1 = std::min(1024, std::max(32, nsort / 2));
-    cudaFuncSetAttribute(k_tile_slots<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-    k_tile_slots<TW, TH><<<cb.n_tiles, nt1, sm1, s>>>(cb, L.K, nsort, topk_idx, topk_w, err, rec, runs, tile_u);
+    if (L.N < (1 << 22) && nsort <= 512) {
+        const unsigned g = (unsigned)((cb.n_tiles + 3) / 4);
+#define GS_TSW(KP) k_tile_slots_warp<TW, TH, KP><<<g, 128, 0, s>>>(cb, L.K, topk_idx, topk_w, err, rec, runs, tile_u)
+        switch (std::max(32, nsort) / 32) {
+        case 1: GS_TSW(1); break;
+        case 2: GS_TSW(2); break;
+        case 4: GS_TSW(4); break;
+        case 8: GS_TSW(8); break;
+        default: GS_TSW(16); break;
+        }
+#undef GS_TSW
+    } else {
+        const size_t sm1 = (sizeof(unsigned long long) + sizeof(float)) * nsort;
+        const int nt1 = std::min(1024, std::max(32, nsort / 2));
+        cudaFuncSetAttribute(k_tile_slots<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+        k_tile_slots<TW, TH><<<cb.n_tiles, nt1, sm1, s>>>(cb, L.K, nsort, topk_idx, topk_w, err, rec, runs, tile_u);
+    }
     exclusive_scan_u32(tile_u, row_base, cb.n_tiles, hdr + 8, aux, s);
     const size_t sm3 = block_accum_smem(B, L.K, L.D, dtype);
     const int st_sz = (int)stage_bytes(B, L.K, dtype, L.D);
