@@ -64,6 +64,10 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            # the sampler is live (first row in) before the timed region starts
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
@@ -197,11 +201,13 @@ def measured_traffic(kernel, rel_src):
 def blend_loss_algorithmic_bytes(step):
     """Bytes the fused gather-blend + loss must move: F written, F_gt read and dL/dF
     written (3 P D s), the Top-K record read (P K 8), colour/depth and their targets read
-    and their gradients written (P (3 + 3 + 1 + 1 + 3 + 1) 4), each distinct row once."""
+    and their gradients written (P (3 + 3 + 1 + 1 + 3 + 1) 4), the re-walk's per-slot
+    terms h written (P K 4), each distinct row once."""
     idx = step.out["topk_idx"]
     uniq = int(np.unique(idx.cpu().numpy()[idx.cpu().numpy() >= 0]).size)
     s = 2 if step.fdt == "bf16" else 4
-    return 3 * step.P * step.D * s + step.P * step.K * 8 + step.P * 12 * 4 + uniq * step.D * s
+    return (3 * step.P * step.D * s + step.P * step.K * 8 + step.P * 12 * 4 + step.P * step.K * 4 +
+            uniq * step.D * s)
 
 
 def blend_algorithmic_bytes(step):
@@ -544,7 +550,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="frame")
