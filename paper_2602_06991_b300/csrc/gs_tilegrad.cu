@@ -3,25 +3,24 @@
 //
 //   dL/df_g = sum over (pixel p, slot k) with idx_k(p) = g of w'_k(p) dL/dF_p     (Eqs. 3-4)
 //
-// (h_k(p) = dL/dF_p . f_{idx_k(p)}, needed by the re-walk, comes from the pixel-group
-// kernel k_h_group in gs_blend.cu.)
+// (h_k(p) = dL/dF_p . f_{idx_k(p)}, needed by the re-walk, comes from the fused blend +
+// loss kernel or from k_h_group in gs_blend.cu.)
 //
 // The screen is cut into small pixel blocks (8x8, 8x4 or 4x4, the largest whose dL/dF
 // rows fit one 64 KB shared-memory stage with at most 512 slots), independent of the
 // binning tile.
-// Stage T1 (k_tile_slots): one CTA per block sorts the block's (Gaussian, slot) keys in
-//   shared memory (bitonic: deterministic) and writes, in sorted order, one record per
-//   slot (pixel, run, renormalised weight) and one entry per run of equal Gaussians
-//   (first position, id); U_b = the number of runs.
+// Stage T1 (k_tile_slots_warp, or k_tile_slots for very large scenes): per block, the
+//   (Gaussian, slot) keys are sorted (bitonic: deterministic) and, in sorted order, one
+//   record per slot (pixel, run, renormalised weight) and one entry per run of equal
+//   Gaussians (first position, id) are written; U_b = the number of runs.
 // Stage T2: exclusive scan of U_b over blocks gives every (block, Gaussian) its partial
 //   row -- deterministic, no atomics.
-// Stage T3 (k_block_accum): a persistent CTA per SM walks blocks.  While it reduces one
-//   block, the dL/dF rows (tensor-map TMA boxes), records and run table (bulk copies) of
-//   its next block stream into the other shared-memory stage, completing on an
-//   mbarrier, so no global round trip sits on the path.  Each warp takes an equal contiguous share of the block's sorted
-//   slots and sums w' dL/dF over the slots of each Gaussian in registers, whole rows at
-//   a time (16 B per lane per 128-column chunk) read from shared memory.  A Gaussian
-//   whose slots straddle warps is finished in fixed order from shared-memory edge rows.
+// Stage T3 (k_block_accum): a persistent CTA per SM walks blocks.  A producer warp
+//   streams each block's dL/dF rows (tensor-map TMA boxes), records and run table (bulk
+//   copies) into a ring of shared-memory stages, completing on mbarriers, while eight
+//   consumer warps reduce the stages already full: each consumer owns whole runs and sums
+//   w' dL/dF over a run's slots in slot order, whole rows at a time (16 B per lane per
+//   128-column chunk) read from shared memory, then writes the run's partial row.
 // Stage T4: the partial rows are reduced per Gaussian by the sort-by-Gaussian segmented
 //   reduction of gs_featgrad.cu in row mode.
 #include "gs_internal.cuh"
