@@ -213,3 +213,37 @@ def test_backward_reuses_loss_h(case):
     assert float(ga["feat"].abs().sum()) > 0 and float(ga["opacity"].abs().sum()) > 0
     with pytest.raises(ValueError):
         r.backward(lo["dL_dF"].clone(), lo["dL_dC"], lo["dL_dD"], h_from_loss=True)
+
+
+def test_slot_sort_fallback_matches_warp_path():
+    """Scenes of 2^22 Gaussians or more take the shared-memory slot sort (64-bit keys)
+    instead of the warp form (32-bit keys).  The 'small' scene is rendered alone and
+    again with 2^22 culled Gaussians (behind the camera) appended after it: the visible
+    Gaussians keep their ids, so the two paths must give bit-identical gradients for
+    them, and zero for the appended ones."""
+    sc, cams, K, tile, _ = S.make_config("small", 6)
+    n0, extra = sc.n, (1 << 22) + 16 - sc.n
+    rng = np.random.default_rng(7)
+    far = S.Scene(mean3d=np.concatenate([sc.mean3d, np.column_stack(
+                      [rng.uniform(-1, 1, extra), rng.uniform(-1, 1, extra), rng.uniform(-6, -2, extra)])]).astype(np.float32),
+                  cov3d=np.concatenate([sc.cov3d, np.tile(sc.cov3d[:1], (extra, 1))]).astype(np.float32),
+                  opacity=np.concatenate([sc.opacity, np.full(extra, 0.5, np.float32)]),
+                  rgb=np.concatenate([sc.rgb, np.full((extra, 3), 0.5, np.float32)]),
+                  feats=np.concatenate([sc.feats, np.tile(sc.feats[:1], (extra, 1))]).astype(np.float32))
+    assert far.n >= (1 << 22)
+    P = cams[0].n_pix
+    dF, dC, dD = (torch.from_numpy(a).cuda() for a in S.upstream_grads(8, P, sc.d))
+    grads = []
+    for scene in (sc, far):
+        r, ts, out = U.gpu_forward(scene, cams, K, tile, max_instances=1 << 20)
+        g = r.backward(dF, dC, dD, with_2d=True)
+        torch.cuda.synchronize()
+        grads.append({k: v.clone() for k, v in g.items()})
+        del r, ts, out, g
+    a, b = grads
+    for k in ("feat", "opacity", "rgb", "mean3d", "cov3d"):
+        assert torch.equal(a[k], b[k][:n0]), k
+        assert float(b[k][n0:].abs().max()) == 0.0, k
+    for k in ("mean2d", "conic"):
+        assert torch.equal(a[k], b[k][:, :n0]), k
+    assert float(a["feat"].abs().sum()) > 0
