@@ -117,6 +117,7 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     L.sort_hist = take(u * 256 * (kRadixBlocks + 1));
     L.scan_aux = take(u * (kSortBlocks + 32));
     L.inst_grad = take(sizeof(float) * kGradVals * L.Mcap);
+    L.inst_walked = take((size_t)L.Mcap);
     L.elem_grad = take(sizeof(float) * kGradVals * L.NE);
     L.pose_part = take(sizeof(float) * 12 * L.NE);
     for (int i = 0; i < 2; ++i) L.pair_keys[i] = take(u * L.n_pairs);
@@ -365,6 +366,7 @@ int gs_backward_ex(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, 
     if (ok)
         launch_project_backward(ct, n_gauss, mean3d, cov3d, proj, ws_ptr<uint32_t>(ws, L.elem_off),
                                 ws_ptr<uint32_t>(ws, L.elem_cnt), ws_ptr<float>(ws, L.inst_grad),
+                                ws_ptr<uint8_t>(ws, L.inst_walked),
                                 ws_ptr<float>(ws, L.elem_grad), ws_ptr<int>(ws, L.header), grads,
                                 ws_ptr<float>(ws, L.pose_part), s);
     // the join is queued on every path after a fork, so a capture of `stream` stays whole

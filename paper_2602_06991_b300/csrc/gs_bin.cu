@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
                                                    const uint32_t *__restrict__ sorted_e,
                                                    const uint32_t *__restrict__ offsets, uint32_t mcap,
                                                    uint32_t *inst_keys, uint32_t *inst_vals, uint32_t *inst_elem,
-                                                   uint32_t *elem_off, uint32_t *elem_cnt, int *err)
+                                                   uint8_t *inst_walked, uint32_t *elem_off, uint32_t *elem_cnt,
+                                                   int *err)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -89,6 +90,7 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
             inst_keys[oo] = (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx);
             inst_vals[oo] = oo;
             inst_elem[oo] = ej;
+            inst_walked[oo] = 0;                // set by the re-walk for the instances it reaches
         }
     }
 }
@@ -166,7 +168,7 @@ void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *
     k_count_tiles<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], counts, elem_cnt);
     exclusive_scan_u32(counts, counts, NE, n_inst, aux, s);
     k_duplicate<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], counts, (uint32_t)L.Mcap, ik[0], iv[0], inst_elem,
-                                  elem_off, elem_cnt, err);
+                                  ws_ptr<uint8_t>(ws, L.inst_walked), elem_off, elem_cnt, err);
     int icur = radix_sort_pairs(ik[0], ik[1], iv[0], iv[1], L.Mcap, n_inst, bits_for(L.n_tiles), hist, s);
     (void)icur;   // equals L.inst_sorted
     k_tile_ranges<<<(unsigned)(((long long)L.n_tiles * 32 + 255) / 256), 256, 0, s>>>(

@@ -287,6 +287,7 @@ struct WsLayout {
     size_t sort_hist;          // (kRadixBlocks + 1) x 256
     size_t scan_aux;           // scan block sums
     size_t inst_grad;          // Mcap x kGradVals floats (per-instance partial 2D gradients)
+    size_t inst_walked;        // Mcap bytes: 1 where the re-walk wrote the instance's partials
     size_t elem_grad;          // NE x kGradVals floats (per-element sums of the instance partials)
     size_t pose_part;          // NE x 12 floats (per-element partial pose gradients)
     size_t pair_keys[2], pair_vals[2];     // N + P K
@@ -356,7 +357,7 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t
 void launch_preprocess(const CamTable &ct, int N, const float *mean3d, const float *cov3d, const float *opac,
                        const float *rgb, float *proj, cudaStream_t s);
 void launch_project_backward(const CamTable &ct, int N, const float *mean3d, const float *cov3d, const float *proj,
-                             const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad,
+                             const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad, const uint8_t *walked,
                              float *elem_grad, const int *err, const gs_grads *gr, float *pose_part, cudaStream_t s);
 void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *proj, void *ws, cudaStream_t s);
 bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj, void *ws,

@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(256) k_preprocess(CamTable ct, int N, const fl
 // (contiguous pre-sort indices) and the 10 partial sums are reduced across the warp.
 __global__ void __launch_bounds__(256) k_elem_grad_sum(long long NE, const uint32_t *__restrict__ elem_off,
                                                        const uint32_t *__restrict__ elem_cnt,
-                                                       const float *__restrict__ inst_grad, const int *err,
+                                                       const float *__restrict__ inst_grad,
+                                                       const uint8_t *__restrict__ walked, const int *err,
                                                        float *__restrict__ elem_grad)
 {
     const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -171,6 +172,7 @@ __global__ void __launch_bounds__(256) k_elem_grad_sum(long long NE, const uint3
     if (*err == 0) {
         const uint32_t o0 = elem_off[e], n = elem_cnt[e];
         for (uint32_t i = lane; i < n; i += 32) {
+            if (!walked[o0 + i]) continue;                  // past where its tile's walk stopped
             // 40-byte record, 8-byte aligned: five 8-byte loads
             const float2 *pg = (const float2 *)(inst_grad + kGradVals * (size_t)(o0 + i));
 #pragma unroll
@@ -339,11 +341,13 @@ __global__ void __launch_bounds__(1024) k_pose_reduce(int N, const float *__rest
 
 void launch_project_backward(const CamTable &ct, int N, const float *mean3d, const float *cov3d, const float *proj,
                              const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad,
-                             float *elem_grad, const int *err, const gs_grads *gr, float *pose_part, cudaStream_t s)
+                             const uint8_t *walked, float *elem_grad, const int *err, const gs_grads *gr,
+                             float *pose_part, cudaStream_t s)
 {
     if (N <= 0) return;
     long long NE = (long long)ct.n * N;
-    k_elem_grad_sum<<<(unsigned)((NE * 32 + 255) / 256), 256, 0, s>>>(NE, elem_off, elem_cnt, inst_grad, err, elem_grad);
+    k_elem_grad_sum<<<(unsigned)((NE * 32 + 255) / 256), 256, 0, s>>>(NE, elem_off, elem_cnt, inst_grad, walked, err,
+                                                                        elem_grad);
     float *pp = gr->viewmat ? pose_part : nullptr;
     k_project_backward<<<(N + 255) / 256, 256, 0, s>>>(ct, N, mean3d, cov3d, (const float4 *)proj, elem_grad, err,
                                                       gr->opacity, gr->rgb, gr->mean3d, gr->cov3d, gr->mean2d,

@@ -17,7 +17,9 @@
 // and the suffix sum is total - prefix with total = dL/dC . C + dL/dD . D (the
 // feature terms sum to zero over the Top-K set).  Per-Gaussian partials are reduced
 // across the tile's pixels (warp reduce-scatter, then a fixed-order sum over warps)
-// and written once per (Gaussian, tile) instance: no atomics, deterministic.
+// and written once per walked (Gaussian, tile) instance, which is flagged; instances
+// past the point where every pixel of the tile stopped are never written (their flags,
+// cleared at binning, stay 0).  No atomics, deterministic.
 #include "gs_internal.cuh"
 
 #include <algorithm>
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
                                                               const float *__restrict__ dLdC,
                                                               const float *__restrict__ dLdD,
                                                               float *__restrict__ inst_grad,
+                                                              uint8_t *__restrict__ inst_walked,
                                                               unsigned *__restrict__ tile_counter)
 {
     constexpr int PPT = bwd_ppt(TW, TH);
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
     __shared__ int s_g[BB];
     __shared__ uint32_t s_o[BB];
     __shared__ float s_red[NW][BB][kGradVals];
-    __shared__ int s_jend[NW];
+    __shared__ unsigned long long s_wrote[NW];   // per warp: the staged Gaussians it reduced
     __shared__ int s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // persistent: each CTA takes the next unprocessed tile until none is left
@@ -166,12 +169,16 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
         if (*err) rg.y = rg.x;
         const int px = tx * TW + (tid % TW);
         const float pxf = (float)px + 0.5f;
+        // pixel-centre rectangle of this warp: all TW columns, its thread rows x PPT rows
+        const float wx0 = (float)(tx * TW) + 0.5f, wx1 = (float)(tx * TW + TW) - 0.5f;
+        const float wy0 = (float)(ty * TH + ((tid - lane) / TW) * PPT) + 0.5f;
+        const float wy1 = (float)(ty * TH + ((tid - lane + 31) / TW) * PPT + PPT - 1) + 0.5f;
 
         float pyf[PPT], dC0[PPT], dC1[PPT], dC2[PPT], dD[PPT], total[PPT], T[PPT], prefix[PPT];
         int kid[PPT][KM];
         float kfp[PPT][KM];
         bool pdone[PPT];
-    #pragma unroll
+#pragma unroll
         for (int r = 0; r < PPT; ++r) {
             const int py = ty * TH + (tid / TW) * PPT + r;
             pyf[r] = (float)py + 0.5f;
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
             T[r] = 1.f;
             prefix[r] = 0.f;
             dC0[r] = dC1[r] = dC2[r] = dD[r] = total[r] = 0.f;
-    #pragma unroll
+#pragma unroll
             for (int k = 0; k < KM; ++k) { kid[r][k] = -2; kfp[r][k] = 0.f; }
             if (inside) {
                 const long long p = cam.pix_off + (long long)py * cam.W + px;
@@ -189,12 +196,12 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
                 total[r] = dC0[r] * rgb_out[3 * p] + dC1[r] * rgb_out[3 * p + 1] + dC2[r] * rgb_out[3 * p + 2] +
                            dD[r] * depth_out[p];
                 float S = 0.f;
-    #pragma unroll
+#pragma unroll
                 for (int k = 0; k < KM; ++k)
                     if (k < K) S += topk_w[p * K + k];
                 const float inv = S > 0.f ? 1.f / S : 0.f;
                 float H = 0.f;
-    #pragma unroll
+#pragma unroll
                 for (int k = 0; k < KM; ++k) {
                     if (k < K) {
                         const int id = topk_idx[p * K + k];
@@ -205,27 +212,21 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
                         }
                     }
                 }
-    #pragma unroll
+#pragma unroll
                 for (int k = 0; k < KM; ++k) kfp[r][k] = (kfp[r][k] - H) * inv;
             }
         }
         auto all_done = [&]() {
             bool d = true;
-    #pragma unroll
+#pragma unroll
             for (int r = 0; r < PPT; ++r) d = d && pdone[r];
             return d;
         };
         const int cN = c * N;
         for (int b0 = rg.x; b0 < rg.y; b0 += BB) {
-            if (__syncthreads_count(!all_done()) == 0) {
-                // every pixel stopped: the remaining instances of this tile contribute nothing
-                for (int m = b0 + tid; m < rg.y; m += NT) {
-                    float *dst = inst_grad + (size_t)kGradVals * inst_vals[m];
-    #pragma unroll
-                    for (int v = 0; v < kGradVals; ++v) dst[v] = 0.f;
-                }
-                break;
-            }
+            // every pixel stopped: the remaining instances of this tile contribute nothing
+            // (their walked flags stay 0, so the per-element sums skip them)
+            if (__syncthreads_count(!all_done()) == 0) break;
             for (int t = tid; t < BB; t += NT) {
                 if (b0 + t < rg.y) {
                     const uint32_t o = inst_vals[b0 + t];
@@ -241,20 +242,26 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
             }
             __syncthreads();
             const int cnt = min(BB, rg.y - b0);
-            // a warp whose pixels have all stopped leaves the batch; the per-tile sum below
-            // counts its entries only up to that point
-            int j_end = cnt;
-            for (int j = 0; j < cnt; ++j) {
-                if (__all_sync(0xffffffffu, all_done())) {
-                    j_end = j;
-                    break;
-                }
+            // only the staged Gaussians that can reach a pixel of this warp's rectangle (the
+            // exact ellipse-rectangle test of the forward walk), in list order; a warp whose
+            // pixels have all stopped leaves the batch.  The per-tile sum below counts the
+            // entries a warp reduced (its mask), all others are zero for it.
+            static_assert(BB == 64, "two 32-bit ballots per batch");
+            const unsigned m0 = __ballot_sync(0xffffffffu, lane < cnt && touches_rect(s_r0[lane], s_r1[lane], wx0, wx1, wy0, wy1));
+            const unsigned m1 = __ballot_sync(0xffffffffu, lane + 32 < cnt &&
+                                                               touches_rect(s_r0[lane + 32], s_r1[lane + 32], wx0, wx1, wy0, wy1));
+            unsigned long long live = ((unsigned long long)m1 << 32) | m0;
+            unsigned long long wrote = 0ull;
+            while (live) {
+                if (__all_sync(0xffffffffu, all_done())) break;
+                const int j = __ffsll((long long)live) - 1;
+                live &= live - 1;
                 float v[kGradVals];
-    #pragma unroll
+#pragma unroll
                 for (int i = 0; i < kGradVals; ++i) v[i] = 0.f;
                 bool contrib = false;
                 const float4 r0 = s_r0[j], r1 = s_r1[j];
-    #pragma unroll
+#pragma unroll
                 for (int r = 0; r < PPT; ++r) {
                     if (pdone[r]) continue;
                     float dx, dy;
@@ -273,7 +280,7 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
                     const float4 r2 = s_r2[j];
                     const int gid = s_g[j];
                     float fp = 0.f;
-    #pragma unroll
+#pragma unroll
                     for (int k = 0; k < KM; ++k) fp = (kid[r][k] == gid) ? kfp[r][k] : fp;
                     const float gi = dC0[r] * r2.x + dC1[r] * r2.y + dC2[r] * r2.z + dD[r] * r2.w + fp;
                     prefix[r] = fmaf(gi, w, prefix[r]);
@@ -296,18 +303,18 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
                     const float d = warp_reduce10(v, lane);
                     const int vi = vidx10(lane);
                     if (!(lane & 1) && vi >= 0) s_red[warp][j][vi] = d;
-                } else if (lane < kGradVals) {
-                    s_red[warp][j][lane] = 0.f;
+                    wrote |= 1ull << j;
                 }
             }
-            if (lane == 0) s_jend[warp] = j_end;
+            if (lane == 0) s_wrote[warp] = wrote;
             __syncthreads();
             for (int i = tid; i < cnt * kGradVals; i += NT) {
                 const int j = i / kGradVals, vi = i - j * kGradVals;
                 float sum = 0.f;
-    #pragma unroll
-                for (int w = 0; w < NW; ++w) sum += j < s_jend[w] ? s_red[w][j][vi] : 0.f;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) sum += ((s_wrote[w] >> j) & 1ull) ? s_red[w][j][vi] : 0.f;
                 inst_grad[(size_t)kGradVals * s_o[j] + vi] = sum;
+                if (vi == 0) inst_walked[s_o[j]] = 1;
             }
         }
         __syncthreads();                         // shared state is free for the next tile
@@ -333,7 +340,7 @@ template <int TW, int TH>
 static bool walk_bwd_k(int KM, dim3 grid, cudaStream_t s, const CamTable &ct, int K, int N, const float4 *proj,
                        const uint32_t *iv, const uint32_t *ie, const int2 *rg, const int *err, const float *C,
                        const float *Dp, const int *ti, const float *tw, const float *h, const float *dC,
-                       const float *dD, float *ig, unsigned *ctr)
+                       const float *dD, float *ig, uint8_t *wk, unsigned *ctr)
 {
     constexpr int B = TW * TH / bwd_ppt(TW, TH);
     auto go = [&](auto kern) {
@@ -346,7 +353,7 @@ static bool walk_bwd_k(int KM, dim3 grid, cudaStream_t s, const CamTable &ct, in
         const long long want = (long long)sms * std::max(1, occ);
         const unsigned g = (unsigned)std::min<long long>(want, grid.x);
         cudaMemsetAsync(ctr, 0, sizeof(unsigned), s);
-        kern<<<g, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig, ctr);
+        kern<<<g, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig, wk, ctr);
     };
     switch (KM) {
     case 4: go(k_walk_bwd<TW, TH, 4>); return true;
@@ -388,13 +395,14 @@ bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const 
     const int2 *rg = ws_ptr<int2>(ws, L.tile_range);
     const float *h = with_feature ? ws_ptr<float>(ws, L.hbuf) : nullptr;
     float *ig = ws_ptr<float>(ws, L.inst_grad);
+    uint8_t *wk = ws_ptr<uint8_t>(ws, L.inst_walked);
     unsigned *ctr = ws_ptr<unsigned>(ws, L.header) + kHdrWalkTiles;
     dim3 grid(ct.n_tiles);
     int KM = k_bucket(K);
-    if (ct.tile_w == 16 && ct.tile_h == 16) return walk_bwd_k<16, 16>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, ctr);
-    if (ct.tile_w == 32 && ct.tile_h == 8) return walk_bwd_k<32, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, ctr);
-    if (ct.tile_w == 16 && ct.tile_h == 8) return walk_bwd_k<16, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, ctr);
-    if (ct.tile_w == 8 && ct.tile_h == 8) return walk_bwd_k<8, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, ctr);
+    if (ct.tile_w == 16 && ct.tile_h == 16) return walk_bwd_k<16, 16>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, wk, ctr);
+    if (ct.tile_w == 32 && ct.tile_h == 8) return walk_bwd_k<32, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, wk, ctr);
+    if (ct.tile_w == 16 && ct.tile_h == 8) return walk_bwd_k<16, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, wk, ctr);
+    if (ct.tile_w == 8 && ct.tile_h == 8) return walk_bwd_k<8, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, wk, ctr);
     return false;
 }
 
