@@ -220,7 +220,7 @@ __device__ __forceinline__ void group_accumulate(int U, int nch, int lane, const
 }
 
 template <int KM, bool BF16, int CPL>
-__global__ void __launch_bounds__(256) k_blend_group(long long n_pix, int K, int nch, const int *__restrict__ idx,
+__global__ void __launch_bounds__(256, 2) k_blend_group(long long n_pix, int K, int nch, const int *__restrict__ idx,
                                                      const float *__restrict__ wts, const void *__restrict__ feats,
                                                      void *__restrict__ F, const int *__restrict__ err)
 {
@@ -401,7 +401,7 @@ __device__ __forceinline__ void group_h(int U, int nch, int K, int lane, long lo
 }
 
 template <int KM, bool BF16, int CPL>
-__global__ void __launch_bounds__(256) k_h_group(long long n_pix, int K, int nch, const int *__restrict__ idx,
+__global__ void __launch_bounds__(256, 2) k_h_group(long long n_pix, int K, int nch, const int *__restrict__ idx,
                                                  const void *__restrict__ feats, const void *__restrict__ dLdF,
                                                  float *__restrict__ h, const int *__restrict__ err)
 {
@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(256) k_blend_loss(long long n_pix, int K, int 
 // registers as in k_blend_group, then pixel by pixel the target row is read, |F|^2,
 // F.Fgt and |Fgt|^2 are reduced over the warp, and F and dL/dF are written.
 template <int KM, bool BF16, int CPL>
-__global__ void __launch_bounds__(256) k_blend_loss_group(long long n_pix, int K, int nch,
+__global__ void __launch_bounds__(256, 2) k_blend_loss_group(long long n_pix, int K, int nch,
                                                           const int *__restrict__ idx, const float *__restrict__ wts,
                                                           const void *__restrict__ feats, const void *__restrict__ Fgt,
                                                           const float *__restrict__ C, const float *__restrict__ Cgt,
