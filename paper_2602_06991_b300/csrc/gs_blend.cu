@@ -723,6 +723,13 @@ __global__ void __launch_bounds__(256, 2) k_blend_loss_group(long long n_pix, in
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long p0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * G;
     if (p0 >= n_pix) return;
+    {
+        // start the target rows on their way to L2 while the blend gathers feature rows
+        const long long pend = min(p0 + G, n_pix);
+        const char *a = (const char *)Fgt + (size_t)p0 * nch * 16;
+        const long long lines = ((pend - p0) * nch * 16 + 127) / 128;
+        for (long long l = lane; l < lines; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(a + 128 * l));
+    }
     const bool bad = *err != 0;
     GroupTable &t = s_t[wib];
     const int U = group_table<KM, G>(p0, n_pix, K, idx, wts, bad, lane, t);
