@@ -10,10 +10,12 @@
 //
 // Backward: the same walk is recomputed (not stored) with the very same inlined
 // evaluation, so contributor sets and transmittances match the forward bit for bit.
+// Its CTAs are persistent (tiles come from a counter) and each warp skips the staged
+// Gaussians whose ellipse misses its pixel rectangle, as the forward walk does.
 // For contributor i with upstream dL/dC, dL/dD and the feature term,
 //   dL/dw_i = dL/dC . c_i + dL/dD z_i + [i in K] (h_i - H) / S,
 //   dL/dalpha_i = dL/dw_i T_i - (sum_{m>i} dL/dw_m w_m) / (1 - alpha_i),
-// where h_i = dL/dF . f_i (computed by the feature-gradient pass), H = sum_k w'_k h_k,
+// where h_i = dL/dF . f_i (written by the fused blend + loss, or by k_h_group), H = sum_k w'_k h_k,
 // and the suffix sum is total - prefix with total = dL/dC . C + dL/dD . D (the
 // feature terms sum to zero over the Top-K set).  Per-Gaussian partials are reduced
 // across the tile's pixels (warp reduce-scatter, then a fixed-order sum over warps)
