@@ -7,7 +7,8 @@
 // loss kernel or from k_h_group in gs_blend.cu.)
 //
 // The screen is cut into small pixel blocks (8x8, 8x4 or 4x4, the largest whose dL/dF
-// rows fit one 64 KB shared-memory stage with at most 512 slots), independent of the
+// rows fit one 64 KB shared-memory stage with at most 512 slots; blocks of 32 or more
+// pixels whose rows fit half a stage take that, so two CTAs share an SM), independent of the
 // binning tile.
 // Stage T1 (k_tile_slots_warp, or k_tile_slots for very large scenes): per block, the
 //   (Gaussian, slot) keys are sorted (bitonic: deterministic) and, in sorted order, one
@@ -39,6 +40,10 @@ FgBlock fg_block_shape(int dtype, int D, int K)
     // the rows of a block (in 256-element TMA box rows) fit one 64 KB stage and its slots
     // number at most 512
     const int row = (D < 256 ? D : (D + 255) / 256 * 256) * (dtype == GS_BF16 ? 2 : 4);
+    // blocks of at least 32 pixels in stages of half the maximum first (two CTAs per SM:
+    // more consumer warps for rows of many short runs), else the largest that fits
+    if (64 * row <= kStageMax / 2 && 64 * K <= 512) return {8, 8};
+    if (32 * row <= kStageMax / 2 && 32 * K <= 512) return {8, 4};
     if (64 * row <= kStageMax && 64 * K <= 512) return {8, 8};
     if (32 * row <= kStageMax && 32 * K <= 512) return {8, 4};
     if (16 * row <= kStageMax && 16 * K <= 512) return {4, 4};
@@ -646,6 +651,10 @@ static void accum_one(unsigned grid, size_t sm, cudaStream_t s, const TmaMaps &m
                       const uint32_t *tu, float *rows, uint32_t *pk, uint32_t *pv, int *err)
 {
     cudaFuncSetAttribute(k_block_accum<TW, TH, BF16, CPLV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    // persistent: as many CTAs as fit on the SMs (grid arrives as blocks, capped at one per SM)
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_block_accum<TW, TH, BF16, CPLV>, kBlkNT + 32, sm);
+    grid = std::max(1u, std::min(grid * (unsigned)std::max(1, occ), (unsigned)cb.n_tiles));
     k_block_accum<TW, TH, BF16, CPLV><<<grid, kBlkNT + 32, sm, s>>>(maps, cb, L.K, L.D, st_sz, rec, runs, rbase, tu,
                                                                (uint32_t)L.rows_cap, rows, pk, pv, L.N, err);
 }
