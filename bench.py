@@ -104,14 +104,15 @@ class ClockSampler:
 class Step:
     """All buffers of one training step, resident on the device."""
 
-    def __init__(self, workload, seed=0, tile=None, scene=None):
+    def __init__(self, workload, seed=0, tile=None, scene=None, max_instances=0):
         import torch
         import gs_scenes as S
         from paper_2602_06991_b300.renderer import TopKRenderer
         sc, cams, K, tile0, fdt = scene if scene is not None else S.make_config(workload, seed)
         tile = tuple(tile) if tile is not None else tile0
         self.scene, self.cams, self.K, self.tile, self.fdt = sc, cams, K, tile, fdt
-        self.r = TopKRenderer(cams, K=K, D=sc.d, tile=tile, feat_dtype=fdt, check_overflow=True)
+        self.r = TopKRenderer(cams, K=K, D=sc.d, tile=tile, feat_dtype=fdt, check_overflow=True,
+                              max_instances=max_instances)
         dev = self.r.device
         tdt = self.r.feat_torch_dtype
         t = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(dev).to(dt).contiguous()
@@ -556,15 +557,10 @@ def _cpu_pixels(workload, budget_s, seed=0, pixel_seed=0):
     while time.perf_counter() - t_start < budget_s:
         pix = rng.choice(cam.n_pix, batch, replace=False)
         r = oracle.render(sc, cam, K, pixels=pix, proj=proj)
-        # loss gradient at those pixels (plain numpy, FP64), then the oracle adjoint
-        F, Fg = r["F"], Fgt[pix].astype(np.float64)
-        nf = np.linalg.norm(F, axis=1, keepdims=True)
-        ng = np.linalg.norm(Fg, axis=1, keepdims=True)
-        ok = (nf > 0) & (ng > 0)
-        cosv = np.where(ok, (F * Fg).sum(1, keepdims=True) / np.maximum(nf * ng, 1e-300), 0)
-        dF = np.where(ok, -(Fg / np.maximum(nf * ng, 1e-300) - cosv * F / np.maximum(nf ** 2, 1e-300)), 0) / cam.n_pix
-        dC = np.sign(r["C"] - Cgt[pix]) / (3 * cam.n_pix)
-        dD = np.sign(r["D"] - Dgt[pix]) / cam.n_pix
+        # the loss and its gradient at those pixels (their share of the frame's mean), then
+        # the oracle adjoint
+        _, dF, dC, dD = oracle.loss_cos_l1(r["F"], Fgt[pix], r["C"], Cgt[pix], r["D"], Dgt[pix],
+                                           n_total=cam.n_pix)
         oracle.backward(sc, cam, K, dF, dC, dD, pixels=pix, proj=proj)
         done += batch
     return done, time.perf_counter() - t_start

@@ -21,6 +21,8 @@ Functions follow the paper's definitions:
   adam_step  -- the Adam update (Kingma and Ba, with bias correction) of the mapping
                iterations, FP64
   loss_geo   -- the colour/depth L1 loss of the geometry-only iterations and its gradient
+  loss_cos_l1 -- the training loss of the benchmark workloads (Sec. 3.4, Eqs. 5-7 read
+               as 1 - cosine on features plus L1 on colour and depth) and its gradients
 """
 from __future__ import annotations
 
@@ -75,6 +77,8 @@ def _L():
         lib.or_pixel_walk.argtypes = [i, dp, dp, ctypes.c_double, ctypes.c_double, dp, i, ip, dp, dp, ip]
         lib.or_prune_stats.argtypes = [i, dp, dp, i, i, dp, dp, ctypes.POINTER(ctypes.c_longlong), dp, ip]
         lib.or_render_vanilla.argtypes = [i, dp, dp, dp, i, i, dp, dp, dp, ip]
+        lib.or_loss_cos_l1.argtypes = [i, ctypes.c_longlong, i, dp, dp, dp, dp, dp, dp, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, dp, dp, dp, dp]
         _lib = lib
         global PROJ_LEN, CAM_LEN
         PROJ_LEN = lib.or_proj_len()
@@ -295,3 +299,27 @@ def loss_geo(C, Cgt, D, Dgt, w_rgb, w_depth):
     P = D.shape[0]
     loss = (w_rgb * np.abs(C - Cgt).sum(1) / 3 + w_depth * np.abs(D - Dgt)).sum() / P
     return loss, w_rgb / (3 * P) * np.sign(C - Cgt), w_depth / P * np.sign(D - Dgt)
+
+
+def loss_cos_l1(F, F_gt, C, C_gt, D, D_gt, w_feat=1.0, w_rgb=1.0, w_depth=1.0, n_total=None):
+    """Training loss of the workloads and its gradients, FP64 (gs_oracle.c, or_loss_cos_l1):
+    L = (1/P) sum_p [w_feat (1 - cos(F_p, Fgt_p)) + w_rgb |C_p - Cgt_p|_1 / 3 + w_depth |D_p - Dgt_p|],
+    a pixel with |F_p| = 0 or |Fgt_p| = 0 adding w_feat and no feature gradient.  The
+    pixels given may be a chunk of n_total (default: all of them); the returned loss is
+    then their share of the mean.  Returns (loss, dF (P, Dim), dC (P, 3), dD (P,))."""
+    L = _L()
+    F, pF = _d(F)
+    G, pG = _d(F_gt)
+    P, Dim = F.shape
+    assert G.shape == (P, Dim)
+    C_, pC = _d(np.asarray(C).reshape(P, 3))
+    Cg, pCg = _d(np.asarray(C_gt).reshape(P, 3))
+    D_, pD = _d(np.asarray(D).reshape(P))
+    Dg, pDg = _d(np.asarray(D_gt).reshape(P))
+    dF, pdF = _d(np.zeros((P, Dim)))
+    dC, pdC = _d(np.zeros((P, 3)))
+    dD, pdD = _d(np.zeros(P))
+    lo, plo = _d(np.zeros(1))
+    L.or_loss_cos_l1(P, int(P if n_total is None else n_total), Dim, pF, pG, pC, pCg, pD, pDg, float(w_feat),
+                     float(w_rgb), float(w_depth), pdF, pdC, pdD, plo)
+    return float(lo[0]), dF, dC, dD

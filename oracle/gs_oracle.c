@@ -509,3 +509,56 @@ int or_render_vanilla(int n, const double *proj, const double *opac, const doubl
     free(cand); free(walk);
     return 0;
 }
+
+/* ---------------------------------------------------------------------------------
+ * Training loss of the benchmark workloads.  Eqs. 5-7 of Sec. 3.4 name the terms (a
+ * feature distance, L1 on colour and on depth) but Eq. 6 is garbled and no weights
+ * are given; the reading used here takes, per pixel p,
+ *   l_p = w_feat (1 - cos(F_p, G_p)) + w_rgb |C_p - Cgt_p|_1 / 3 + w_depth |D_p - Dgt_p|,
+ * with cos(F, G) = F.G / (|F| |G|), and L = (1 / P_total) sum_p l_p.  A pixel with
+ * |F_p| = 0 or |G_p| = 0 has no direction: its cosine is taken as 0 (it adds w_feat)
+ * and it passes no feature gradient.  Gradients, with sign(0) = 0:
+ *   dL/dF_p = (w_feat / P_total) (cos F_p / |F_p|^2 - G_p / (|F_p| |G_p|)),
+ *   dL/dC_p = (w_rgb / (3 P_total)) sign(C_p - Cgt_p),
+ *   dL/dD_p = (w_depth / P_total) sign(D_p - Dgt_p).
+ * P of the P_total pixels are given here; *loss receives their share sum_p l_p / P_total
+ * (so the shares of disjoint chunks add up to L).
+ * ------------------------------------------------------------------------------- */
+static double sgn(double x) { return (x > 0.0) - (x < 0.0); }
+
+int or_loss_cos_l1(int P, long long P_total, int D, const double *F, const double *G, const double *C,
+                   const double *Cgt, const double *Dp, const double *Dgt, double w_feat, double w_rgb,
+                   double w_depth, double *dF, double *dC, double *dD, double *loss)
+{
+    double sum = 0.0;
+    const double inv = 1.0 / (double)P_total;
+    for (int p = 0; p < P; ++p) {
+        const double *f = F + (size_t)p * D, *g = G + (size_t)p * D;
+        double ff = 0.0, gg = 0.0, fg = 0.0;
+        for (int d = 0; d < D; ++d) {
+            ff += f[d] * f[d];
+            gg += g[d] * g[d];
+            fg += f[d] * g[d];
+        }
+        double cosv = 0.0;
+        double *df = dF + (size_t)p * D;
+        if (ff > 0.0 && gg > 0.0) {
+            const double nf = sqrt(ff), ng = sqrt(gg);
+            cosv = fg / (nf * ng);
+            for (int d = 0; d < D; ++d) df[d] = w_feat * inv * (cosv * f[d] / ff - g[d] / (nf * ng));
+        } else {
+            for (int d = 0; d < D; ++d) df[d] = 0.0;
+        }
+        double l1c = 0.0;
+        for (int i = 0; i < 3; ++i) {
+            const double e = C[3 * p + i] - Cgt[3 * p + i];
+            l1c += fabs(e);
+            dC[3 * p + i] = w_rgb * inv / 3.0 * sgn(e);
+        }
+        const double ed = Dp[p] - Dgt[p];
+        dD[p] = w_depth * inv * sgn(ed);
+        sum += w_feat * (1.0 - cosv) + w_rgb * l1c / 3.0 + w_depth * fabs(ed);
+    }
+    *loss = sum * inv;
+    return 0;
+}

@@ -41,6 +41,14 @@ MUTANTS = {
     "pose_translation_sign": ("g_view[4 * i + 3] += dp[i];", "g_view[4 * i + 3] -= dp[i];"),
     "vanilla_uses_alpha": ("for (int d = 0; d < D; ++d) Fp[d] += walk[i].w * f[d];",
                            "for (int d = 0; d < D; ++d) Fp[d] += walk[i].alpha * f[d];"),
+    "loss_grad_sign": ("(cosv * f[d] / ff - g[d] / (nf * ng))", "(g[d] / (nf * ng) - cosv * f[d] / ff)"),
+    "loss_grad_norm_not_squared": ("cosv * f[d] / ff", "cosv * f[d] / nf"),
+    "loss_rgb_not_averaged": ("w_rgb * l1c / 3.0", "w_rgb * l1c"),
+    "loss_drgb_factor": ("dC[3 * p + i] = w_rgb * inv / 3.0 * sgn(e);", "dC[3 * p + i] = w_rgb * inv * sgn(e);"),
+    "loss_not_a_mean": ("*loss = sum * inv;", "*loss = sum;"),
+    "loss_zero_row_adds_nothing": ("sum += w_feat * (1.0 - cosv)",
+                                   "sum += w_feat * (ff > 0.0 && gg > 0.0 ? 1.0 - cosv : 0.0)"),
+    "loss_depth_sign": ("dD[p] = w_depth * inv * sgn(ed);", "dD[p] = -w_depth * inv * sgn(ed);"),
     "prune_importance_is_alpha": ("if (walk[i].w > maxw[walk[i].g]) maxw[walk[i].g] = walk[i].w;",
                                   "if (walk[i].alpha > maxw[walk[i].g]) maxw[walk[i].g] = walk[i].alpha;"),
 }
@@ -60,6 +68,7 @@ def test_pins_catch_mutant(name):
         env = dict(os.environ, GS_ORACLE_LIB=so)
         r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                             os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                            os.path.join(ROOT, "tests", "test_oracle_prune.py")],
+                            os.path.join(ROOT, "tests", "test_oracle_prune.py"),
+                            os.path.join(ROOT, "tests", "test_oracle_loss.py")],
                            cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
         assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
