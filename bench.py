@@ -152,7 +152,7 @@ class Step:
                                     _p(self.inp[4]), _p(o["F"]), self.r._stream())
 
 
-def run_bf16_batched(args):
+def run_bf16_batched(args, hbm):
     """The BF16 multi-keyframe form: 1M Gaussians, BF16 rows, 8 orbit keyframes of mixed
     resolution rendered and back-propagated as one step (one launch per stage over all
     views, the whole step one CUDA graph), tile shape picked by the autotuner."""
@@ -169,17 +169,101 @@ def run_bf16_batched(args):
         torch.cuda.empty_cache()
         step = Step("batched", tile=tuned["tile"], scene=scene_k)
         ms = autotune.time_step(lambda: step.run, reps=max(5, min(args.steps, 20)), warmup=args.warmup)
+        st = status_of(step)
         sweep.append({"K": K, "tile": list(tuned["tile"]), "ms_per_step": round(ms, 4),
-                      "value": round(step.P / (ms * 1e-3) / 1e6, 3), "autotune_ms": tuned["ms"]})
+                      "value": round(step.P / (ms * 1e-3) / 1e6, 3), "autotune_ms": tuned["ms"], "status": st})
+        if K == K0:
+            main_roof = stage_rooflines(step, hbm)
         P, N, D = step.P, step.N, step.D
         del step
         torch.cuda.empty_cache()
     main = next(r for r in sweep if r["K"] == K0)
-    return {"value": main["value"], "unit": UNIT, "ms_per_step": main["ms_per_step"], "pixels_per_step": P,
-            "gaussians": N, "views": len(cams), "D": D, "K": K0, "dtype": "bf16", "tile": main["tile"],
-            "autotune_ms": main["autotune_ms"], "k_sweep": [{k: v for k, v in r.items() if k != "autotune_ms"}
-                                                             for r in sweep],
-            "workload": "batched: " + S.CONFIGS["batched"]}
+    out = {"value": main["value"], "unit": UNIT, "ms_per_step": main["ms_per_step"], "pixels_per_step": P,
+           "gaussians": N, "views": len(cams), "D": D, "K": K0, "dtype": "bf16", "tile": main["tile"],
+           "status": main["status"], "roofline": main_roof["blend_loss"], "backward_roofline": main_roof["backward"],
+           "autotune_ms": main["autotune_ms"], "k_sweep": [{k: v for k, v in r.items() if k != "autotune_ms"}
+                                                            for r in sweep],
+           "workload": "batched: " + S.CONFIGS["batched"]}
+    if any(r["status"] != "ok" for r in sweep):
+        out["rejected"] = "a workspace status after timed steps was not ok"
+    return out
+
+
+MAPPING_INSTANCES = 1_150_000_000
+
+
+def run_mapping(args, hbm, iters=100):
+    """The mapping-iteration workload: 3M Gaussians (70% on 20 planes and boxes, 30%
+    clutter), 8 keyframes of 1200x680, D=768 BF16 rows, K=16.  One iteration renders and
+    back-propagates all 8 views (a1-a3, the fused a4 + loss, a5 with every per-Gaussian
+    feature and geometry gradient) and takes the fused Adam step over every parameter:
+    float32 master weights, the bf16 feature rows the renderer reads refreshed by the same
+    launch.  `iters` iterations are captured into one CUDA graph (each with its own Adam
+    step count) and replayed; timed by CUDA events on the launching stream."""
+    import torch
+    import gs_scenes as S
+    from paper_2602_06991_b300.hybrid import AdamState, adam_step
+    scene = S.make_config("mapping", 0)
+    sc, cams, K, tile, fdt = scene
+    step = Step("mapping", scene=scene, max_instances=MAPPING_INSTANCES)
+    feat32 = torch.from_numpy(sc.feats).cuda()
+    del scene, sc
+    params = {"mean3d": step.inp[0], "cov3d": step.inp[1], "opacity": step.inp[2], "rgb": step.inp[3],
+              "feat": feat32}
+    grads = {k: step.grads[k] for k in ("mean3d", "cov3d", "opacity", "rgb", "feat")}
+    lr = {"mean3d": 1e-5, "cov3d": 1e-7, "opacity": 1e-4, "rgb": 1e-4, "feat": 1e-4}
+    state = AdamState(params)
+    copies = {"feat": step.inp[4]}
+
+    def iteration():
+        step.run()
+        adam_step(params, grads, state, lr, bf16_copies=copies)
+
+    for _ in range(2):
+        iteration()
+    torch.cuda.synchronize()
+    n_inst, n_rows = step.r.counts()
+    # stage times of one iteration (direct launches, events on the launching stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    step.run(ev[:4])
+    adam_step(params, grads, state, lr, bf16_copies=copies)
+    ev[4].record()
+    torch.cuda.synchronize()
+    stages = {"select_ms": ev[0].elapsed_time(ev[1]), "blend_loss_ms": ev[1].elapsed_time(ev[2]),
+              "backward_ms": ev[2].elapsed_time(ev[3]), "adam_ms": ev[3].elapsed_time(ev[4])}
+    stream = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        iteration()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(iters):
+            iteration()
+    g.replay()                                   # warm-up replay
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    g.replay()
+    t1.record()
+    torch.cuda.synchronize()
+    status = status_of(step)
+    ms = t0.elapsed_time(t1) / iters
+    sr = stage_rooflines(step, hbm, reps=3)
+    out = {"value": round(step.P / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "ms_per_iteration": round(ms, 3),
+           "iterations": iters, "captured": "one CUDA graph of all iterations, replayed once after a warm-up replay",
+           "pixels_per_iteration": step.P, "gaussians": step.N, "views": len(cams), "D": step.D, "K": step.K,
+           "dtype": "bf16", "instances": n_inst, "instance_capacity": MAPPING_INSTANCES, "feature_rows": n_rows,
+           "status": status, "stages": {k: round(v, 3) for k, v in stages.items()},
+           "roofline": sr["blend_loss"], "backward_roofline": sr["backward"],
+           "workload": "mapping: " + S.CONFIGS["mapping"]}
+    if status != "ok":
+        out["rejected"] = f"workspace status after the timed iterations: {status}"
+    del g, step, params, grads, state, feat32
+    torch.cuda.empty_cache()
+    return out
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
@@ -264,6 +348,75 @@ def aggregate_ranks(ms: float, pixels: int, world: int, device=None):
     return float(t_ms.item()), int(round(t_px.item()))
 
 
+def workload_config(workload, world, N, P, D, K, tile):
+    """The `config` object of the JSON line; both arms print the same one."""
+    import gs_scenes as S
+    return {"workload": f"{workload}: {S.CONFIGS[workload]}", "gaussians": N, "pixels_per_step": P, "D": D, "K": K,
+            "tile": list(tile), "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"}
+
+
+def blend_loss_bytes(P, D, K, s, uniq):
+    """Bytes the fused gather-blend + loss must move: F written, F_gt read and dL/dF
+    written (3 P D s), the Top-K record read (P K 8), colour/depth and their targets read
+    and their gradients written (P (3 + 3 + 1 + 1 + 3 + 1) 4), the re-walk's per-slot
+    terms h written (P K 4), each distinct selected row once (U D s)."""
+    return 3 * P * D * s + P * K * 8 + P * 12 * 4 + P * K * 4 + uniq * D * s
+
+
+def backward_bytes(P, D, K, s, N, NE):
+    """Bytes the adjoint must move: dL/dF read (P D s), the Top-K record and the per-slot
+    h read (P K 12), dL/dC, dL/dD, C and D read (P 8 4), the projected records read
+    (NE 64), the feature gradient written (N D 4) and the geometry gradients written
+    (N 13 4)."""
+    return P * D * s + P * K * 12 + P * 32 + NE * 64 + N * D * 4 + N * 52
+
+
+def unique_rows(step):
+    idx = step.out["topk_idx"]
+    v = idx[idx >= 0]
+    import torch
+    return int(torch.unique(v).numel())
+
+
+def stage_rooflines(step, hbm, reps=10):
+    """The step's two HBM-bound stages timed alone with CUDA events on the launching
+    stream (averaged over reps): the fused gather-blend + loss (one kernel and two small
+    fixed-order sums) and the whole adjoint (gs_backward_ex), against their algorithmic
+    bytes."""
+    import torch
+    s = 2 if step.fdt == "bf16" else 4
+    uniq = unique_rows(step)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    for _ in range(reps):
+        step.r.blend_loss(step.inp[4], step.tgt[0], step.tgt[1], step.tgt[2], lo=step.lo)
+    ev[1].record()
+    for _ in range(reps):
+        step.r.backward(step.lo["dL_dF"], step.lo["dL_dC"], step.lo["dL_dD"], grads=step.grads, h_from_loss=True)
+    ev[2].record()
+    torch.cuda.synchronize()
+    bl_ms, bw_ms = ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps
+    blb = blend_loss_bytes(step.P, step.D, step.K, s, uniq)
+    bwb = backward_bytes(step.P, step.D, step.K, s, step.N, step.N * len(step.cams))
+    out = {"blend_loss": {"kernel": "gs_feature_blend_loss (k_blend_loss_group)", "bound": "hbm",
+                          "achieved": round(blb / (bl_ms * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                          "frac": round(blb / (bl_ms * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": blb,
+                          "unique_rows": uniq, "kernel_ms": round(bl_ms, 4)},
+           "backward": {"stage": "gs_backward_ex (feature gradient, re-walk, projection adjoint)", "bound": "hbm",
+                        "achieved": round(bwb / (bw_ms * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(bwb / (bw_ms * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": bwb,
+                        "stage_ms": round(bw_ms, 4)}}
+    return out
+
+
+def status_of(step):
+    """The workspace status after timed work: anything but ok rejects the timing (a
+    bounded wait that ran out, or a capacity overflow, skips work)."""
+    from paper_2602_06991_b300 import _abi as A
+    code, _ = step.r.sync_status()
+    return A.status_string(code)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -323,6 +476,7 @@ def run_ours(args, rank, world, local_rank):
     t1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    status = status_of(step)
     ms = t0.elapsed_time(t1) / args.steps
     ms, total_pixels = aggregate_ranks(ms, step.P, world, device="cuda")
     value = total_pixels / (ms * 1e-3) / 1e6
@@ -332,15 +486,15 @@ def run_ours(args, rank, world, local_rank):
     achieved = ab / (blend_ms * 1e-3) / 1e9
     abl = blend_loss_algorithmic_bytes(step)
     achieved_bl = abl / (blend_loss_ms * 1e-3) / 1e9
+    sr = stage_rooflines(step, hbm)
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if step.fdt == "f32" else "bf16", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {__import__('gs_scenes').CONFIGS[args.workload]}",
-                   "gaussians": step.N, "pixels_per_step": step.P, "D": step.D, "K": step.K,
-                   "tile": list(step.tile), "graph": graph is not None,
-                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+        "config": workload_config(args.workload, world, step.N, step.P, step.D, step.K, step.tile),
+        "graph": graph is not None, "status": status,
         "stages": {k: round(v, 4) for k, v in stages.items()},
+        "backward_roofline": sr["backward"],
         "roofline": {"kernel": "gs_feature_blend_loss (k_blend_loss_group): the step's a4 stage", "bound": "hbm",
                      "achieved": round(achieved_bl, 1), "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved_bl / hbm, 4),
@@ -361,11 +515,16 @@ def run_ours(args, rank, world, local_rank):
         res["vanilla"] = run_vanilla(step)
     if rank == 0 and not args.no_e2e:
         res["e2e"] = run_e2e(step, args)
+    if status != "ok":
+        res["rejected"] = f"workspace status after the timed steps: {status}"
     if rank == 0 and not args.no_batched:
         del step
         torch.cuda.empty_cache()
-        res["bf16_batched"] = run_bf16_batched(args)
+        res["bf16_batched"] = run_bf16_batched(args, hbm)
         res["bf16_batched"]["speedup_vs_f32_frame"] = round(res["bf16_batched"]["value"] / res["value"], 3)
+    if rank == 0 and not args.no_mapping:
+        torch.cuda.empty_cache()
+        res["mapping"] = run_mapping(args, hbm)
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
     return res
@@ -601,10 +760,13 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     cb = cpu_baseline(args.workload, budget_s=max(5.0, min(60.0, 3.0 * args.steps)), all_cores=False)
+    import gs_scenes as S
+    sc, cams, K, tile, _ = S.make_config(args.workload, 0)
+    P = sum(c.width * c.height for c in cams)
     return {"metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"{args.workload}: {__import__('gs_scenes').CONFIGS[args.workload]}"},
+            "config": workload_config(args.workload, world, sc.n, P, sc.d, K, tile),
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -622,6 +784,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-launch-count", action="store_true", help="skip the CUPTI launch count (for ncu runs)")
     ap.add_argument("--no-batched", action="store_true", help="skip the BF16 multi-keyframe measurement")
+    ap.add_argument("--no-mapping", action="store_true", help="skip the mapping-iteration measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))

@@ -74,8 +74,8 @@ class Scene:
                      self.feats[idx].copy())
 
 
-def _unit_rows(rng, n, d):
-    v = rng.standard_normal((n, d))
+def _unit_rows(rng, n, d, dtype=np.float64):
+    v = rng.standard_normal((n, d), dtype=dtype)
     v /= np.linalg.norm(v, axis=1, keepdims=True)
     return v
 
@@ -105,10 +105,10 @@ def _random_cov6(rng, n, log_scale_mu=-3.0, log_scale_sigma=0.5, squash=None):
                      S[:, 1, 1], S[:, 1, 2], S[:, 2, 2]], axis=1)
 
 
-def _attrs(rng, n, d):
+def _attrs(rng, n, d, feat_dtype=np.float64):
     opac = 1.0 / (1.0 + np.exp(-rng.standard_normal(n)))
     rgb = rng.uniform(0.0, 1.0, size=(n, 3))
-    feats = _unit_rows(rng, n, d)
+    feats = _unit_rows(rng, n, d, feat_dtype)
     return opac, rgb, feats
 
 
@@ -136,11 +136,12 @@ def random_scene_box(seed: int, n: int, d: int, box=BOX,
 
 
 def planes_scene(seed: int, n: int, d: int, n_planes=5, frac_on_planes=0.8,
-                 box=BOX, patch=2.0, boxes_frac=0.0) -> Scene:
+                 box=BOX, patch=2.0, boxes_frac=0.0, feat_dtype=np.float64) -> Scene:
     """Surface-concentrated scene: frac_on_planes of the Gaussians lie uniformly on
     n_planes seeded 2x2 m planar patches (random normal, centre uniform in the box);
     a fraction boxes_frac of the patches are replaced by the six faces of a small
-    axis-aligned box; the rest is uniform clutter in the box."""
+    axis-aligned box; the rest is uniform clutter in the box.  feat_dtype: precision in
+    which the feature vectors are drawn (float32 keeps a multi-GB draw in memory)."""
     rng = np.random.default_rng(seed)
     lo = np.array([b[0] for b in box])
     hi = np.array([b[1] for b in box])
@@ -175,7 +176,7 @@ def planes_scene(seed: int, n: int, d: int, n_planes=5, frac_on_planes=0.8,
     perm = rng.permutation(n)
     mean = mean[perm]
     cov = _random_cov6(rng, n)
-    opac, rgb, feats = _attrs(rng, n, d)
+    opac, rgb, feats = _attrs(rng, n, d, feat_dtype)
     return _pack(mean, cov, opac, rgb, feats)
 
 
@@ -316,7 +317,7 @@ def make_config(name: str, seed: int = 0, n_override: Optional[int] = None):
         return sc, orbit_cameras(seed + 1000, sizes), 8, (16, 16), "bf16"
     if name == "mapping":
         sc = planes_scene(seed, n_override or 3_000_000, 768, n_planes=20,
-                          frac_on_planes=0.7, boxes_frac=0.3)
+                          frac_on_planes=0.7, boxes_frac=0.3, feat_dtype=np.float32)
         sizes = [(1200, 680, 600.0)] * 8
         return sc, orbit_cameras(seed + 2000, sizes), 16, (16, 16), "bf16"
     raise KeyError(name)

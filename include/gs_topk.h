@@ -77,6 +77,9 @@ typedef struct {
     int32_t tile_w, tile_h;    /* screen tile: 16x16, 32x8, 16x8 or 8x8 */
     int32_t feat_dtype;        /* GS_F32 or GS_BF16: feature rows, F and dL/dF */
     int32_t max_instances;     /* capacity of (Gaussian, tile) instances; 0: 32 per (camera, Gaussian) */
+    int32_t max_feature_rows;  /* capacity of gs_backward's partial feature-gradient rows, one per (pixel
+                                  block, selected Gaussian); 0: 32 per block, or max_instances per
+                                  (camera, Gaussian) when that is larger */
 } gs_config;
 
 /* Per-Gaussian gradient outputs of gs_backward (device, caller-allocated, fully
@@ -210,10 +213,13 @@ int gs_feature_blend_loss(const gs_config *cfg, const gs_camera *cams, int32_t n
  * paper has no counterpart; this is a property of the library.  No scratch argument:
  * the per-pixel partial sums live in a fixed array the library holds on every GPU that
  * loads it (GS_LOSS_NOALLOC_MAX_PIX + 360 floats, about 16.8 MB, kept until exit).
- * n_pix > GS_LOSS_NOALLOC_MAX_PIX returns GS_ERR_WORKSPACE without launching.  The
- * first call on a device looks up the array's device address for that device; make
- * it before any stream capture.  All calls share the array: calls whose kernels
- * overlap on the GPU race.  Allocates nothing. */
+ * n_pix > GS_LOSS_NOALLOC_MAX_PIX returns GS_ERR_WORKSPACE without launching; other
+ * arguments follow gs_loss_cos_l1's rules.  The first call on a device looks up the
+ * array's device address for that device; make it before any stream capture.  Later
+ * calls outside a capture look the address up again (it belongs to the device's current
+ * context, e.g. it changes after cudaDeviceReset); a call on a capturing stream reuses
+ * the last one found.  All calls share the array: calls whose kernels overlap on the
+ * GPU race.  Allocates nothing. */
 #define GS_LOSS_NOALLOC_MAX_PIX (1 << 22)
 int gs_loss_cos_l1_noalloc(const gs_config *cfg, int64_t n_pix, const void *F, const void *F_gt,
                            const float *rgb, const float *rgb_gt, const float *depth, const float *depth_gt,
@@ -232,7 +238,10 @@ int gs_loss_geo_l1(int64_t n_pix, const float *rgb, const float *rgb_gt, const f
  * launch (the optimiser of the mapping iterations; the paper leaves it to 3DGS):
  *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
  *   p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps),
- * element-wise; param, exp_avg (m) and exp_avg_sq (v) are updated in place, step >= 1. */
+ * element-wise; param, exp_avg (m) and exp_avg_sq (v) are updated in place, step >= 1.
+ * param_bf16 (optional, may be NULL): n bf16 values that receive the updated param
+ * rounded to nearest -- the BF16 copy a renderer with GS_BF16 feature rows reads, kept
+ * beside float32 master weights; 8-byte aligned. */
 #define GS_ADAM_MAX_TENSORS 16
 typedef struct {
     float *param;
@@ -241,6 +250,7 @@ typedef struct {
     float *exp_avg_sq;
     int64_t n;
     float lr;
+    void *param_bf16;
 } gs_adam_tensor;
 int gs_adam_step(const gs_adam_tensor *tensors, int32_t n_tensors, int32_t step, float beta1, float beta2, float eps,
                  void *stream);
@@ -277,6 +287,25 @@ int gs_prune_stats(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, 
 size_t gs_prune_select_workspace_size(int32_t n_gauss);
 int gs_prune_select(int32_t n_gauss, const int32_t *topk_count, const float *S, int32_t tau, double ratio,
                     const float *expo, uint8_t *keep, void *ws, size_t ws_bytes, void *stream);
+
+/* Bound, in SM clock cycles, of the device-side waits of the current render on this
+ * workspace (the mbarrier waits of the feature-gradient pipeline in gs_backward): each
+ * wait gives up once more than `cycles` cycles have passed, records GS_ERR_TIMEOUT in the
+ * error word, and its kernel finishes early (after waiting, with the default bound, for
+ * the copies it has in flight), so later kernels on the workspace skip their work and
+ * gs_sync_status reports the timeout.  cycles <= 0 selects the default, 2e9 cycles
+ * (about 1 s); gs_preprocess resets it to the default at the start of every render.
+ * Queued on `stream` like the other calls.  For failure-detection tests: a limit of a
+ * few cycles makes the first wait run out. */
+int gs_set_wait_limit(void *ws, size_t ws_bytes, int64_t cycles, void *stream);
+
+/* Synchronises `stream` and reads two counts of the last render on the workspace: the
+ * (Gaussian, tile) instances that gs_bin_sort produced and the partial feature-gradient
+ * rows that gs_backward needed -- whether or not they fitted the capacities, so a caller
+ * can size max_instances and max_feature_rows after a GS_ERR_OVERFLOW.  Either pointer
+ * may be NULL. */
+int gs_workspace_counts(const void *ws, size_t ws_bytes, void *stream, int64_t *n_instances,
+                        int64_t *n_feature_rows);
 
 /* Synchronises `stream` and returns the workspace error word as a status (GS_OK if
  * clear).  If n_instances is not NULL it receives the instance count of the last

@@ -31,7 +31,8 @@ class GsCamera(ctypes.Structure):
 
 class GsConfig(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("D", ctypes.c_int32), ("tile_w", ctypes.c_int32),
-                ("tile_h", ctypes.c_int32), ("feat_dtype", ctypes.c_int32), ("max_instances", ctypes.c_int32)]
+                ("tile_h", ctypes.c_int32), ("feat_dtype", ctypes.c_int32), ("max_instances", ctypes.c_int32),
+                ("max_feature_rows", ctypes.c_int32)]
 
 
 class GsGrads(ctypes.Structure):
@@ -41,7 +42,7 @@ class GsGrads(ctypes.Structure):
 
 class GsAdamTensor(ctypes.Structure):
     _fields_ = [("param", vp), ("grad", vp), ("exp_avg", vp), ("exp_avg_sq", vp), ("n", ctypes.c_int64),
-                ("lr", ctypes.c_float)]
+                ("lr", ctypes.c_float), ("param_bf16", vp)]
 
 
 GS_ADAM_MAX_TENSORS = 16
@@ -95,6 +96,9 @@ PROTOTYPES = {
     "gs_prune_select_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),
     "gs_prune_select": (ctypes.c_int, [ctypes.c_int32, vp, vp, ctypes.c_int32, ctypes.c_double, vp, vp, vp,
                                        ctypes.c_size_t, vp]),
+    "gs_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_size_t, ctypes.c_int64, vp]),
+    "gs_workspace_counts": (ctypes.c_int, [vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int64)]),
     "gs_sync_status": (ctypes.c_int, [vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int64)]),
 }
 

@@ -20,11 +20,11 @@ static bool tile_ok(int tw, int th)
     return (tw == 16 && th == 16) || (tw == 32 && th == 8) || (tw == 16 && th == 8) || (tw == 8 && th == 8);
 }
 
-static bool cfg_ok(const gs_config *cfg)
+bool cfg_ok(const gs_config *cfg)
 {
     return cfg && cfg->K >= 1 && cfg->K <= GS_MAX_K && cfg->D >= 8 && cfg->D <= 1024 && cfg->D % 8 == 0 &&
            tile_ok(cfg->tile_w, cfg->tile_h) && (cfg->feat_dtype == GS_F32 || cfg->feat_dtype == GS_BF16) &&
-           cfg->max_instances >= 0;
+           cfg->max_instances >= 0 && cfg->max_feature_rows >= 0;
 }
 
 static bool cams_ok(const gs_camera *cams, int n_cams)
@@ -90,9 +90,13 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     if (L.use_tiles) retile(ct, fb.bw, fb.bh, cb);
     L.n_fgblocks = L.use_tiles ? cb.n_tiles : 0;
     // partial feature-gradient rows: one per (block, selected Gaussian), so never more
-    // than P K; sized for 32 per block or Mcap / 16, growing with max_instances (an
-    // overflow sets the error word and yields no feature gradient).
-    L.rows_cap = L.use_tiles ? std::min(L.PK, std::max((long long)L.n_fgblocks * 32, mcap / 16)) : 0;
+    // than P K; the configured capacity, else 32 per block, or the instance capacity per
+    // element when that is larger (an overflow sets the error word and yields no feature
+    // gradient; gs_workspace_counts then reports the rows needed).
+    const long long per_block = std::max(32ll, mcap / std::max(1ll, L.NE));
+    const long long rows_want = cfg->max_feature_rows > 0 ? (long long)cfg->max_feature_rows
+                                                          : (long long)L.n_fgblocks * per_block;
+    L.rows_cap = L.use_tiles ? std::min(L.PK, rows_want) : 0;
     L.n_pairs = N + L.rows_cap;
     if (L.NE > 0x7fffffffll || L.n_pairs > 0x7fffffffll) return false;
     L.max_pieces_rows = N + (L.rows_cap + kPieceLen - 1) / kPieceLen + 1;
@@ -144,6 +148,8 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     L.total = off;
     return true;
 }
+
+__global__ void k_store_u64(unsigned long long *dst, unsigned long long v) { *dst = v; }
 
 static int ws_check(const WsLayout &L, const void *ws, size_t ws_bytes)
 {
@@ -254,6 +260,7 @@ int gs_preprocess(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, i
     CamTable ct;
     make_camtable(cfg, cams, n_cams, ct);
     cudaMemsetAsync(ws_ptr<char>(ws, L.header), 0, 16, s);
+    cudaMemsetAsync(ws_ptr<char>(ws, L.header + kHdrWaitLimitByte), 0, 8, s);   // default wait bound
     launch_preprocess(ct, n_gauss, mean3d, cov3d, opacity, rgb, proj, s);
     return launch_status();
 }
@@ -450,7 +457,9 @@ int gs_adam_step(const gs_adam_tensor *tensors, int32_t n_tensors, int32_t step,
         if (a.n < 0) return GS_ERR_ARG;
         if (a.n == 0) continue;
         if (!a.param || !a.grad || !a.exp_avg || !a.exp_avg_sq) return GS_ERR_ARG;
-        t[nt++] = AdamTensor{a.param, a.grad, a.exp_avg, a.exp_avg_sq, (long long)a.n, a.lr};
+        if (((uintptr_t)a.param_bf16 & 7) != 0) return GS_ERR_ARG;
+        t[nt++] = AdamTensor{a.param, a.grad, a.exp_avg, a.exp_avg_sq, (long long)a.n, a.lr,
+                             (__nv_bfloat16 *)a.param_bf16};
     }
     if (nt == 0) return GS_OK;
     launch_adam(t, nt, step, beta1, beta2, eps, (cudaStream_t)stream);
@@ -505,6 +514,26 @@ int gs_prune_select(int32_t n_gauss, const int32_t *topk_count, const float *S, 
     if (!launch_prune_select(n_gauss, topk_count, S, tau, ratio, expo, keep, ws, (cudaStream_t)stream))
         return GS_ERR_UNSUPPORTED;
     return launch_status();
+}
+
+int gs_set_wait_limit(void *ws, size_t ws_bytes, int64_t cycles, void *stream)
+{
+    if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < 256) return GS_ERR_WORKSPACE;
+    const unsigned long long v = cycles > 0 ? (unsigned long long)cycles : 0ull;
+    k_store_u64<<<1, 1, 0, (cudaStream_t)stream>>>(ws_ptr<unsigned long long>(ws, kHdrWaitLimitByte), v);
+    return launch_status();
+}
+
+int gs_workspace_counts(const void *ws, size_t ws_bytes, void *stream, int64_t *n_instances,
+                        int64_t *n_feature_rows)
+{
+    if (!ws || ws_bytes < 256) return GS_ERR_WORKSPACE;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GS_ERR_CUDA;
+    uint32_t h[9];
+    if (cudaMemcpy(h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
+    if (n_instances) *n_instances = (int64_t)h[1];
+    if (n_feature_rows) *n_feature_rows = (int64_t)h[8];
+    return GS_OK;
 }
 
 int gs_sync_status(const void *ws, size_t ws_bytes, void *stream, int64_t *n_instances)

@@ -84,6 +84,13 @@ __global__ void __launch_bounds__(256) k_adam(const __grid_constant__ AdamTable 
             *(float4 *)(t.param + i0) = p;
             *(float4 *)(t.m + i0) = m;
             *(float4 *)(t.v + i0) = v;
+            if (t.pb) {                 // 4 bf16 = 8 bytes (the copy is 8-byte aligned)
+                __nv_bfloat162 lo = __floats2bfloat162_rn(p.x, p.y), hi = __floats2bfloat162_rn(p.z, p.w);
+                uint2 u;
+                u.x = *(const uint32_t *)&lo;
+                u.y = *(const uint32_t *)&hi;
+                *(uint2 *)(t.pb + i0) = u;
+            }
         } else {
             for (long long i = i0; i < i0 + 4 && i < t.n; ++i) {
                 float p = t.param[i], m = t.m[i], v = t.v[i];
@@ -91,6 +98,7 @@ __global__ void __launch_bounds__(256) k_adam(const __grid_constant__ AdamTable 
                 t.param[i] = p;
                 t.m[i] = m;
                 t.v[i] = v;
+                if (t.pb) t.pb[i] = __float2bfloat16_rn(p);
             }
         }
     }
@@ -108,7 +116,7 @@ bool launch_adam(const AdamTensor *t, int n_tensors, int step, float beta1, floa
     }
     tab.start[n_tensors] = acc;
     for (int i = n_tensors; i < kAdamMaxTensors; ++i) {
-        tab.t[i] = AdamTensor{nullptr, nullptr, nullptr, nullptr, 0, 0.f};
+        tab.t[i] = AdamTensor{nullptr, nullptr, nullptr, nullptr, 0, 0.f, nullptr};
         tab.start[i + 1] = acc;
     }
     // bias corrections in double on the host

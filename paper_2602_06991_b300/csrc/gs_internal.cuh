@@ -273,10 +273,12 @@ struct TopK {
 // Workspace layout (host-computed; all offsets 256-byte aligned)
 // ------------------------------------------------------------------------------------
 constexpr int kHdrWalkTiles = 16;   // header word: next tile of the persistent re-walk
+constexpr int kHdrWaitLimitByte = 96;   // header bytes [96, 104): bound of the pipeline waits (0: default)
 
 struct WsLayout {
     size_t header;             // 256 B: [0] error word, [1] instance count, [2] pieces, [3] multi-piece
-                               // segments, [8] partial rows, [9] pairs, [16] re-walk tile counter
+                               // segments, [8] partial rows, [9] pairs, [16] re-walk tile counter,
+                               // [24..25] the wait limit (64-bit, SM cycles, 0 = default)
     size_t depth_keys[2], depth_vals[2];   // NE
     size_t elem_cnt;           // NE (tiles touched, per element)
     size_t elem_off;           // NE (first pre-sort instance of each element)
@@ -315,6 +317,8 @@ struct WsLayout {
     int N, K, D, n_tiles, n_cams;
 };
 
+// The argument rules every entry point applies to a gs_config (K, D, tile shape, dtype).
+bool cfg_ok(const gs_config *cfg);
 bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N, WsLayout &L);
 bool make_camtable(const gs_config *cfg, const gs_camera *cams, int n_cams, CamTable &ct);
 int bits_for(long long v);
@@ -336,6 +340,7 @@ struct AdamTensor {
     float *m, *v;
     long long n;
     float lr;
+    __nv_bfloat16 *pb;         // optional bf16 copy of param (nullptr: none)
 };
 constexpr int kAdamMaxTensors = 16;
 bool launch_adam(const AdamTensor *t, int n_tensors, int step, float beta1, float beta2, float eps, cudaStream_t s);

@@ -155,23 +155,32 @@ __global__ void __launch_bounds__(256) k_preprocess(CamTable ct, int N, const fl
 // then chain through conic -> Sigma2D -> (J R, Sigma3D) -> camera-space mean -> world
 // mean.  Partial layout per instance: du, dv, da, db, dc, dopacity, dr, dg, db, dz.
 // ------------------------------------------------------------------------------------
-// One warp per (camera, Gaussian) element: lanes stride over the element's instances
-// (contiguous pre-sort indices) and the 10 partial sums are reduced across the warp.
+// Per-element sums of the re-walk's instance partials (an element's instances are the
+// contiguous pre-sort range [elem_off, elem_off + elem_cnt)), skipping the instances the
+// re-walk never reached.  One thread per element sums a short range in instance order;
+// the ranges longer than kElemSerial (Gaussians near the camera, over many tiles) are
+// then taken one at a time by the whole warp (strided lanes, a fixed shuffle tree).
+// Either way the order is fixed, so the result is deterministic.
+constexpr uint32_t kElemSerial = 48;
+
 __global__ void __launch_bounds__(256) k_elem_grad_sum(long long NE, const uint32_t *__restrict__ elem_off,
                                                        const uint32_t *__restrict__ elem_cnt,
                                                        const float *__restrict__ inst_grad,
                                                        const uint8_t *__restrict__ walked, const int *err,
                                                        float *__restrict__ elem_grad)
 {
-    const long long e = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    if (e >= NE) return;
-    float v[16];
+    uint32_t o0 = 0, n = 0;
+    if (e < NE && *err == 0) {
+        o0 = elem_off[e];
+        n = elem_cnt[e];
+    }
+    if (e < NE && n <= kElemSerial) {
+        float v[kGradVals];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = 0.f;
-    if (*err == 0) {
-        const uint32_t o0 = elem_off[e], n = elem_cnt[e];
-        for (uint32_t i = lane; i < n; i += 32) {
+        for (int k = 0; k < kGradVals; ++k) v[k] = 0.f;
+        for (uint32_t i = 0; i < n; ++i) {
             if (!walked[o0 + i]) continue;                  // past where its tile's walk stopped
             // 40-byte record, 8-byte aligned: five 8-byte loads
             const float2 *pg = (const float2 *)(inst_grad + kGradVals * (size_t)(o0 + i));
@@ -182,10 +191,33 @@ __global__ void __launch_bounds__(256) k_elem_grad_sum(long long NE, const uint3
                 v[2 * k + 1] += x.y;
             }
         }
+        float2 *dst = (float2 *)(elem_grad + kGradVals * (size_t)e);
+#pragma unroll
+        for (int k = 0; k < kGradVals / 2; ++k) dst[k] = make_float2(v[2 * k], v[2 * k + 1]);
     }
-    float d = warp_reduce16(v, lane);
-    int vi = (lane >> 1) & 15;
-    if (!(lane & 1) && vi < kGradVals) elem_grad[kGradVals * e + vi] = d;
+    unsigned long_ones = __ballot_sync(0xffffffffu, n > kElemSerial);
+    while (long_ones) {
+        const int j = __ffs(long_ones) - 1;
+        long_ones &= long_ones - 1;
+        const uint32_t oj = __shfl_sync(0xffffffffu, o0, j), nj = __shfl_sync(0xffffffffu, n, j);
+        const long long ej = __shfl_sync(0xffffffffu, e, j);
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = 0.f;
+        for (uint32_t i = lane; i < nj; i += 32) {
+            if (!walked[oj + i]) continue;
+            const float2 *pg = (const float2 *)(inst_grad + kGradVals * (size_t)(oj + i));
+#pragma unroll
+            for (int k = 0; k < kGradVals / 2; ++k) {
+                const float2 x = __ldg(pg + k);
+                v[2 * k] += x.x;
+                v[2 * k + 1] += x.y;
+            }
+        }
+        const float d = warp_reduce16(v, lane);
+        const int vi = (lane >> 1) & 15;
+        if (!(lane & 1) && vi < kGradVals) elem_grad[kGradVals * ej + vi] = d;
+    }
 }
 
 __global__ void __launch_bounds__(256) k_project_backward(CamTable ct, int N, const float *__restrict__ mean3d,
@@ -346,8 +378,8 @@ void launch_project_backward(const CamTable &ct, int N, const float *mean3d, con
 {
     if (N <= 0) return;
     long long NE = (long long)ct.n * N;
-    k_elem_grad_sum<<<(unsigned)((NE * 32 + 255) / 256), 256, 0, s>>>(NE, elem_off, elem_cnt, inst_grad, walked, err,
-                                                                        elem_grad);
+    k_elem_grad_sum<<<(unsigned)((NE + 255) / 256), 256, 0, s>>>(NE, elem_off, elem_cnt, inst_grad, walked, err,
+                                                                   elem_grad);
     float *pp = gr->viewmat ? pose_part : nullptr;
     k_project_backward<<<(N + 255) / 256, 256, 0, s>>>(ct, N, mean3d, cov3d, (const float4 *)proj, elem_grad, err,
                                                       gr->opacity, gr->rgb, gr->mean3d, gr->cov3d, gr->mean2d,

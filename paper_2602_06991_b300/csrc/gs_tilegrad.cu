@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(128) k_tile_slots_warp(CamTable ct, int K, con
 constexpr int kBlkNT = 256;
 constexpr int kBlkNW = kBlkNT / 32;
 constexpr int kTmaInner = 256;                       // elements per TMA box row (box limit)
-constexpr long long kWaitCycles = 2000000000ll;      // bounded mbarrier wait (~1 s)
+constexpr long long kWaitCycles = 2000000000ll;      // default bound of an mbarrier wait (~1 s)
 
 struct TmaMaps {
     CUtensorMap m[GS_MAX_CAMERAS];                   // dL/dF of each camera as [H][W][D]
@@ -329,12 +329,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-// Waits for the phase with the given parity to complete; false after kWaitCycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// Waits for the phase with the given parity to complete; false once more than `limit`
+// SM clock cycles have passed.  The elapsed time is checked before every probe, so a
+// limit of a few cycles runs out on the first check whether or not the phase is done.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit)
 {
     const uint32_t a = smem_u32(bar);
     const long long t0 = clock64();
     while (true) {
+        if (clock64() - t0 > limit) return false;
         uint32_t done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n"
@@ -342,7 +345,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
                      : "r"(a), "r"(parity)
                      : "memory");
         if (done) return true;
-        if (clock64() - t0 > kWaitCycles) return false;
     }
 }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -431,7 +433,8 @@ __global__ void __launch_bounds__(kBlkNT + 32, 1) k_block_accum(const __grid_con
                                                                 const uint32_t *__restrict__ tile_u,
                                                                 uint32_t rows_cap, float *__restrict__ rows,
                                                                 uint32_t *__restrict__ pair_keys,
-                                                                uint32_t *__restrict__ pair_vals, int N, int *err)
+                                                                uint32_t *__restrict__ pair_vals, int N, int *err,
+                                                                const unsigned long long *__restrict__ wait_limit)
 {
     constexpr int B = TW * TH;
     using Rw = SRow<BF16>;
@@ -441,6 +444,7 @@ __global__ void __launch_bounds__(kBlkNT + 32, 1) k_block_accum(const __grid_con
     __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages];
     __shared__ uint32_t s_meta[kStages][2];          // (U, row base) of the block in each stage
     __shared__ int s_bad, s_issued, s_done[kBlkNW];
+    __shared__ long long s_limit;
     const int nslots = B * K;
     const int rstride = runs_stride(nslots);
     const int nch = D / VEC;                           // 16-byte chunks per row
@@ -467,10 +471,14 @@ __global__ void __launch_bounds__(kBlkNT + 32, 1) k_block_accum(const __grid_con
         fence_mbar_init();
         s_bad = *err != 0;
         s_issued = 0;
+        // the pipeline waits' bound (0: the default); the final drain keeps the default
+        const unsigned long long wl = *wait_limit;
+        s_limit = wl == 0ull || wl > (unsigned long long)kWaitCycles ? kWaitCycles : (long long)wl;
     }
     if (tid < kBlkNW) s_done[tid] = 0;
     __syncthreads();
     const bool bad = s_bad != 0;
+    const long long limit = s_limit;
 
     if (warp == kBlkNW) {
         // producer
@@ -486,7 +494,7 @@ __global__ void __launch_bounds__(kBlkNT + 32, 1) k_block_accum(const __grid_con
                 const int blk = blockIdx.x + j * G;
                 uint32_t U2 = 0, rb2 = 0;
                 if (j + 2 < my_n) { U2 = tile_u[blk + 2 * G]; rb2 = row_base[blk + 2 * G]; }
-                if (j >= kStages && !mbar_wait(&s_empty[sidx], ((j / kStages) - 1) & 1)) {
+                if (j >= kStages && !mbar_wait(&s_empty[sidx], ((j / kStages) - 1) & 1, limit)) {
                     atomicOr(err, kErrTimeout);
                     break;
                 }
@@ -519,7 +527,7 @@ __global__ void __launch_bounds__(kBlkNT + 32, 1) k_block_accum(const __grid_con
         int j = 0;
         for (; j < my_n; ++j) {
             const int sidx = j % kStages;
-            if (!mbar_wait(&s_full[sidx], (j / kStages) & 1)) {
+            if (!mbar_wait(&s_full[sidx], (j / kStages) & 1, limit)) {
                 if (lane == 0) atomicOr(err, kErrTimeout);
                 break;
             }
@@ -575,12 +583,13 @@ __global__ void __launch_bounds__(kBlkNT + 32, 1) k_block_accum(const __grid_con
         if (lane == 0) s_done[warp] = j;
     }
     __syncthreads();
-    // copies still in flight (only after a timed-out wait): wait for them, bounded
+    // copies still in flight (only after a timed-out wait): wait for them with the
+    // default bound whatever the pipeline's limit, so no copy lands after the CTA exits
     if (tid == 0) {
         int done = my_n;
         for (int w = 0; w < kBlkNW; ++w) done = min(done, s_done[w]);
         if (bad) done = 0;
-        for (int jj = done; jj < s_issued; ++jj) mbar_wait(&s_full[jj % kStages], (jj / kStages) & 1);
+        for (int jj = done; jj < s_issued; ++jj) mbar_wait(&s_full[jj % kStages], (jj / kStages) & 1, kWaitCycles);
     }
 }
 
@@ -648,7 +657,8 @@ static bool make_maps(const CamTable &cb, int dtype, int D, const void *dLdF, Tm
 template <int TW, int TH, bool BF16, int CPLV>
 static void accum_one(unsigned grid, size_t sm, cudaStream_t s, const TmaMaps &maps, const CamTable &cb,
                       const WsLayout &L, int st_sz, const uint2 *rec, const uint2 *runs, const uint32_t *rbase,
-                      const uint32_t *tu, float *rows, uint32_t *pk, uint32_t *pv, int *err)
+                      const uint32_t *tu, float *rows, uint32_t *pk, uint32_t *pv, int *err,
+                      const unsigned long long *wl)
 {
     cudaFuncSetAttribute(k_block_accum<TW, TH, BF16, CPLV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     // persistent: as many CTAs as fit on the SMs (grid arrives as blocks, capped at one per SM)
@@ -656,22 +666,23 @@ static void accum_one(unsigned grid, size_t sm, cudaStream_t s, const TmaMaps &m
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_block_accum<TW, TH, BF16, CPLV>, kBlkNT + 32, sm);
     grid = std::max(1u, std::min(grid * (unsigned)std::max(1, occ), (unsigned)cb.n_tiles));
     k_block_accum<TW, TH, BF16, CPLV><<<grid, kBlkNT + 32, sm, s>>>(maps, cb, L.K, L.D, st_sz, rec, runs, rbase, tu,
-                                                               (uint32_t)L.rows_cap, rows, pk, pv, L.N, err);
+                                                               (uint32_t)L.rows_cap, rows, pk, pv, L.N, err, wl);
 }
 
 template <int TW, int TH, bool BF16>
 static void accum_launch(int cpl, unsigned grid, size_t sm, cudaStream_t s, const TmaMaps &maps, const CamTable &cb,
                          const WsLayout &L, int st_sz, const uint2 *rec, const uint2 *runs, const uint32_t *rbase,
-                         const uint32_t *tu, float *rows, uint32_t *pk, uint32_t *pv, int *err)
+                         const uint32_t *tu, float *rows, uint32_t *pk, uint32_t *pv, int *err,
+                         const unsigned long long *wl)
 {
     // (D <= 1024 caps bf16 rows at 4 chunks per lane; float32 rows at 8)
     switch (cpl) {
-    case 1: accum_one<TW, TH, BF16, 1>(grid, sm, s, maps, cb, L, st_sz, rec, runs, rbase, tu, rows, pk, pv, err); break;
-    case 2: accum_one<TW, TH, BF16, 2>(grid, sm, s, maps, cb, L, st_sz, rec, runs, rbase, tu, rows, pk, pv, err); break;
-    case 4: accum_one<TW, TH, BF16, 4>(grid, sm, s, maps, cb, L, st_sz, rec, runs, rbase, tu, rows, pk, pv, err); break;
+    case 1: accum_one<TW, TH, BF16, 1>(grid, sm, s, maps, cb, L, st_sz, rec, runs, rbase, tu, rows, pk, pv, err, wl); break;
+    case 2: accum_one<TW, TH, BF16, 2>(grid, sm, s, maps, cb, L, st_sz, rec, runs, rbase, tu, rows, pk, pv, err, wl); break;
+    case 4: accum_one<TW, TH, BF16, 4>(grid, sm, s, maps, cb, L, st_sz, rec, runs, rbase, tu, rows, pk, pv, err, wl); break;
     default:
         accum_one<TW, TH, BF16, (BF16 ? 4 : 8)>(grid, sm, s, maps, cb, L, st_sz, rec, runs, rbase, tu, rows, pk, pv,
-                                                 err);
+                                                 err, wl);
         break;
     }
 }
@@ -725,12 +736,13 @@ static bool tile_launch(const CamTable &cb, const WsLayout &L, int dtype, const 
     const int nch = L.D / (dtype == GS_BF16 ? 8 : 4);
     const int cpl = nch <= 32 ? 1 : nch <= 64 ? 2 : nch <= 128 ? 4 : 8;
     const unsigned grid = (unsigned)std::max(1, std::min(cb.n_tiles, sm_count()));
+    const unsigned long long *wl = ws_ptr<const unsigned long long>(ws, L.header + kHdrWaitLimitByte);
     if (dtype == GS_BF16)
         accum_launch<TW, TH, true>(cpl, grid, sm3, s, maps, cb, L, st_sz, rec, runs, row_base, tile_u, rows, pk, pv,
-                                   err);
+                                   err, wl);
     else
         accum_launch<TW, TH, false>(cpl, grid, sm3, s, maps, cb, L, st_sz, rec, runs, row_base, tile_u, rows, pk, pv,
-                                    err);
+                                    err, wl);
     return true;
 }
 

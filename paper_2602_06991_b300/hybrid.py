@@ -44,11 +44,14 @@ class AdamState:
 
 def adam_step(params: Dict[str, torch.Tensor], grads: Dict[str, torch.Tensor], state: AdamState,
               lr: Dict[str, float], names: Sequence[str] = None, beta1: float = 0.9, beta2: float = 0.999,
-              eps: float = 1e-15):
+              eps: float = 1e-15, bf16_copies: Dict[str, torch.Tensor] = None):
     """One Adam step (in place) over the named tensors, all in a single launch.  Only the
     tensors in `names` (default: all) are stepped; their moments advance together, so a
     semantic-rate tensor keeps its own step count by being passed only on semantic
-    iterations with its own AdamState."""
+    iterations with its own AdamState.  bf16_copies: for float32 master weights whose
+    renderer copy is bf16 (the BF16 feature rows), the bf16 tensor the same launch
+    refreshes from the updated master."""
+    bf16_copies = bf16_copies or {}
     names = list(params) if names is None else list(names)
     if len(names) > A.GS_ADAM_MAX_TENSORS:
         raise ValueError("too many tensors for one Adam launch")
@@ -61,8 +64,11 @@ def adam_step(params: Dict[str, torch.Tensor], grads: Dict[str, torch.Tensor], s
                 raise TypeError(f"{k}.{nm} must be a contiguous float32 CUDA tensor")
         if g.numel() != p.numel():
             raise ValueError(f"gradient of {k} has {g.numel()} elements, parameter {p.numel()}")
+        cp = bf16_copies.get(k)
+        if cp is not None and (cp.dtype != torch.bfloat16 or cp.numel() != p.numel() or not cp.is_contiguous()):
+            raise TypeError(f"bf16 copy of {k} must be a contiguous bfloat16 tensor of {p.numel()} elements")
         arr[i] = A.GsAdamTensor(p.data_ptr(), g.data_ptr(), state.m[k].data_ptr(), state.v[k].data_ptr(), p.numel(),
-                                float(lr[k]))
+                                float(lr[k]), cp.data_ptr() if cp is not None else None)
     lib = A.load()
     stream = ctypes.c_void_p(torch.cuda.current_stream(params[names[0]].device).cuda_stream)
     A.check(lib.gs_adam_step(arr, len(names), state.step, float(beta1), float(beta2), float(eps), stream),

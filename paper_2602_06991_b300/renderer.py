@@ -42,7 +42,7 @@ class TopKRenderer:
     """One configuration (cameras, K, D, tile, feature dtype) and its workspace."""
 
     def __init__(self, cameras: Sequence, K: int, D: int, tile=(16, 16), feat_dtype: str = "f32",
-                 max_instances: int = 0, device=None, check_overflow: bool = True):
+                 max_instances: int = 0, device=None, check_overflow: bool = True, max_feature_rows: int = 0):
         self.lib = A.load()
         self.cams = A.make_cameras(list(cameras))
         self.n_cams = len(cameras)
@@ -52,7 +52,8 @@ class TopKRenderer:
         self.feat_torch_dtype = _TORCH_DT[self.dtype]
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.check_overflow = check_overflow
-        self.cfg = A.GsConfig(self.K, self.D, self.tile[0], self.tile[1], self.dtype, int(max_instances))
+        self.cfg = A.GsConfig(self.K, self.D, self.tile[0], self.tile[1], self.dtype, int(max_instances),
+                              int(max_feature_rows))
         self.P = int(self.lib.gs_pixel_count(self.cams, self.n_cams))
         if self.P < 0:
             raise ValueError("bad cameras")
@@ -74,6 +75,19 @@ class TopKRenderer:
 
     def _stream(self):
         return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def set_wait_limit(self, cycles: int):
+        """Bound (SM clock cycles) of the device-side pipeline waits of the current
+        render (gs_set_wait_limit); the next forward resets it to the default."""
+        A.check(self.lib.gs_set_wait_limit(_p(self.ws), self.ws.numel(), int(cycles), self._stream()),
+                "gs_set_wait_limit")
+
+    def counts(self):
+        """(instances of the last binning, partial feature rows the last backward needed)."""
+        n, m = ctypes.c_int64(0), ctypes.c_int64(0)
+        A.check(self.lib.gs_workspace_counts(_p(self.ws), self.ws.numel(), self._stream(), ctypes.byref(n),
+                                             ctypes.byref(m)), "gs_workspace_counts")
+        return int(n.value), int(m.value)
 
     def sync_status(self):
         n = ctypes.c_int64(0)
@@ -221,20 +235,20 @@ class TopKRenderer:
 
         run(A.GS_BWD_H_FROM_LOSS if h_reuse else 0)
         if self.check_overflow:
-            # the per-block partial feature rows have a capacity that grows with
-            # max_instances: on overflow, grow it, redo a1-a3 into the new workspace (same
+            # the per-block partial feature rows have a capacity: on overflow, size it to
+            # the rows needed (with a margin), redo a1-a3 into the new workspace (same
             # Top-K, deterministic) and the adjoint
             code, _ = self.sync_status()
-            while code == A.GS_ERR_OVERFLOW:
-                cur = self.cfg.max_instances if self.cfg.max_instances > 0 else 32 * self.n_cams * N
-                if cur >= 2 ** 31 - 1:
-                    break
-                self.cfg.max_instances = int(min(2 ** 31 - 1, 2 * cur))
+            tries = 0
+            while code == A.GS_ERR_OVERFLOW and tries < 4:
+                _, need = self.counts()
+                self.cfg.max_feature_rows = int(min(2 ** 31 - 1, max(need + need // 4, 2 * self.cfg.max_feature_rows)))
                 self.ws = None
                 self._ensure_ws(N)
                 self._select_into(N, st["mean3d"], st["cov3d"], st["opacity"], st["rgb"], o)
                 run(0)                  # the new workspace holds no h from the loss
                 code, _ = self.sync_status()
+                tries += 1
             A.check(code, "backward")
         return g
 

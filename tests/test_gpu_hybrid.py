@@ -89,6 +89,24 @@ def test_fused_adam_vs_oracle():
         np.testing.assert_allclose(st.m[k].cpu().numpy(), ref[k][1], rtol=1e-5, atol=1e-7)
 
 
+def test_fused_adam_bf16_copy():
+    """float32 master weights with a bf16 renderer copy: the same launch writes the copy,
+    the updated master rounded to nearest (both the float4 and the scalar path)."""
+    from paper_2602_06991_b300.hybrid import AdamState, adam_step
+    rng = np.random.default_rng(4)
+    params = {k: torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda() for k, n in (("f", 4096 + 6),
+                                                                                                   ("g", 13))}
+    copies = {k: torch.empty(v.numel(), dtype=torch.bfloat16, device="cuda") for k, v in params.items()}
+    st = AdamState(params)
+    for _ in range(2):
+        grads = {k: torch.from_numpy(rng.standard_normal(v.numel()).astype(np.float32)).cuda()
+                 for k, v in params.items()}
+        adam_step(params, grads, st, {"f": 1e-2, "g": 1e-3}, bf16_copies=copies)
+    torch.cuda.synchronize()
+    for k, v in params.items():
+        assert torch.equal(copies[k], v.to(torch.bfloat16)), k
+
+
 def test_hybrid_loop_runs_and_lowers_the_loss():
     """Twelve iterations of the hybrid schedule (semantics every third) with Adam on the
     small scene: every loss finite, the geometric loss lower at the end."""

@@ -1,0 +1,112 @@
+"""GPU parity of the mapping-iteration workload at full size, against the FP64 oracle on
+sampled pixels of every keyframe: 3M Gaussians (70% on 20 planes and boxes, 30% clutter),
+8 keyframes of 1200x680 on an orbit, D = 768 bf16 feature rows, K = 16 (the map sizes of
+Sec. 3.4 / Tab. 6 scaled up; the Top-K rendering of Sec. 3.2).
+
+Forward: contributor counts, Top-K index sets (flagged near-decisions excluded and
+counted) and transmittance against the oracle; F at per-pixel cosine >= 0.999 both
+against the oracle fed the bf16 rows the GPU reads and against the oracle fed the
+original float32 rows.  Backward: upstream gradients at the sampled pixels only (seeded,
+zero elsewhere), every per-Gaussian gradient group to relative L2 <= 1e-4; the feature
+gradient is compared on the Gaussians selected at the sampled pixels, and is exactly zero
+on the GPU for every other Gaussian."""
+import gc
+
+import numpy as np
+import pytest
+import torch
+
+import gs_scenes as S
+import oracle
+import parity_util as U
+
+pytestmark = pytest.mark.gpu
+
+INSTANCES = 1_150_000_000       # the workload's (Gaussian, tile) instances are about 1.0e9
+
+
+def _cos_min(Fg, Fo):
+    Fg, Fo = np.asarray(Fg, np.float64), np.asarray(Fo, np.float64)
+    nz = np.linalg.norm(Fo, axis=1) > 0
+    c = (Fg[nz] * Fo[nz]).sum(1) / (np.linalg.norm(Fg[nz], axis=1) * np.linalg.norm(Fo[nz], axis=1))
+    return float(c.min()) if c.size else 1.0
+
+
+def test_mapping_sampled_forward_and_backward():
+    gc.collect()
+    torch.cuda.empty_cache()
+    sc, cams, K, tile, fdt = S.make_config("mapping", 0)
+    assert (sc.n, sc.d, K, fdt, len(cams)) == (3_000_000, 768, 16, "bf16", 8)
+    r, ts, out = U.gpu_forward(sc, cams, K, tile, feat_dtype="bf16", max_instances=INSTANCES)
+    n_inst, _ = r.counts()
+    # the oracle reads the bf16 rows exactly, as float64 (converted once)
+    feats64 = ts[4].float().cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(12)
+    pix = [np.sort(rng.choice(c.n_pix, 12, replace=False)) for c in cams]
+    o = U.oracle_forward(sc, cams, K, pixels_per_cam=pix, feats=feats64)
+    idx = torch.from_numpy(o["gidx"]).cuda()
+    g = {k: out[k].index_select(0, idx).float().cpu().numpy() for k in ("n_contrib", "topk_idx", "T", "F")}
+    fragile = (o["flags"] & U.FRAGILE_SET) != 0
+    ok = ~fragile
+    assert fragile.sum() <= max(2, 0.02 * ok.size), int(fragile.sum())
+    assert np.array_equal(g["n_contrib"][ok].astype(np.int64), o["n"][ok])
+    sets_ok = ok & ((o["flags"] & oracle.F_NEAR_TIE) == 0)
+    assert np.array_equal(np.sort(g["topk_idx"][sets_ok].astype(np.int64), axis=1), np.sort(o["idx"][sets_ok], axis=1))
+    np.testing.assert_allclose(g["T"][ok], o["T"][ok], rtol=1e-5, atol=1e-7)
+    cos_bf16 = _cos_min(g["F"][ok], o["F"][ok])
+    # the same pixels with the original float32 rows (the FP64 reference of the form)
+    o32 = U.oracle_forward(sc, cams, K, pixels_per_cam=pix, feats=sc.feats.astype(np.float64))
+    cos_f32 = _cos_min(g["F"][ok], o32["F"][ok])
+    assert cos_bf16 >= 0.999 and cos_f32 >= 0.999, (cos_bf16, cos_f32)
+
+    # backward: upstream gradients at the sampled, unflagged pixels only
+    P = r.P
+    keep = ~((o["flags"] & U.FRAGILE_ANY) != 0)
+    sel = o["gidx"][keep]
+    m = sel.size
+    dF_rows = rng.standard_normal((m, sc.d)).astype(np.float32)
+    dC_rows = rng.standard_normal((m, 3)).astype(np.float32)
+    dD_rows = rng.standard_normal(m).astype(np.float32)
+    dF = torch.zeros(P, sc.d, dtype=torch.bfloat16, device="cuda")
+    dC = torch.zeros(P, 3, device="cuda")
+    dD = torch.zeros(P, device="cuda")
+    sel_t = torch.from_numpy(sel).cuda()
+    dF[sel_t] = torch.from_numpy(dF_rows).cuda().to(torch.bfloat16)
+    dC[sel_t] = torch.from_numpy(dC_rows).cuda()
+    dD[sel_t] = torch.from_numpy(dD_rows).cuda()
+    dF_exact = dF[sel_t].float().cpu().numpy().astype(np.float64)
+    gr = r.backward(dF, dC, dD)
+    torch.cuda.synchronize()
+    members = np.unique(o["idx"][keep][o["idx"][keep] >= 0])
+    zero_elsewhere = torch.ones(sc.n, dtype=torch.bool, device="cuda")
+    zero_elsewhere[torch.from_numpy(members).cuda()] = False
+    assert float(gr["feat"][zero_elsewhere].abs().max()) == 0.0
+    g_feat = gr["feat"][torch.from_numpy(members).cuda()].cpu().numpy()
+    geo = {k: gr[k].cpu().numpy() for k in ("opacity", "rgb", "mean3d", "cov3d")}
+    del gr, dF, out, r, ts
+    gc.collect()
+    torch.cuda.empty_cache()
+
+    tot = {k: 0.0 for k in ("opac", "rgb", "mean3d", "cov3d")}
+    tot_feat = np.zeros((members.size, sc.d))
+    dC_all, dD_all = dC[sel_t].cpu().numpy(), dD[sel_t].cpu().numpy()
+    off = 0
+    pos = {int(p): i for i, p in enumerate(sel)}
+    for cam, base in U.cam_slices(cams):
+        mine = [(int(p) - base) for p in sel if base <= p < base + cam.n_pix]
+        if not mine:
+            continue
+        rows = [pos[base + q] for q in mine]
+        og = oracle.backward(sc, cam, K, dF_exact[rows], dC_all[rows], dD_all[rows], pixels=np.asarray(mine),
+                             feats=feats64)
+        for k in tot:
+            tot[k] = tot[k] + og[k]
+        tot_feat += og["feat"][members]
+        del og
+    errs = {"feat": U.rel_l2(g_feat, tot_feat)}
+    for gk, ok_ in (("opacity", "opac"), ("rgb", "rgb"), ("mean3d", "mean3d"), ("cov3d", "cov3d")):
+        errs[gk] = U.rel_l2(geo[gk], tot[ok_])
+    print("mapping: instances", n_inst, "flagged", int(fragile.sum()), "of", ok.size, "cos min (bf16 rows)", cos_bf16,
+          "(f32 rows)", cos_f32, "grad rel-L2", errs)
+    for k, e in errs.items():
+        assert e <= U.GRAD_TOL, (k, e)
