@@ -104,7 +104,7 @@ class ClockSampler:
 class Step:
     """All buffers of one training step, resident on the device."""
 
-    def __init__(self, workload, seed=0, tile=None, scene=None, max_instances=0):
+    def __init__(self, workload, seed=0, tile=None, scene=None, max_instances=0, topk_layout=0):
         import torch
         import gs_scenes as S
         from paper_2602_06991_b300.renderer import TopKRenderer
@@ -112,7 +112,8 @@ class Step:
         tile = tuple(tile) if tile is not None else tile0
         self.scene, self.cams, self.K, self.tile, self.fdt = sc, cams, K, tile, fdt
         self.r = TopKRenderer(cams, K=K, D=sc.d, tile=tile, feat_dtype=fdt, check_overflow=True,
-                              max_instances=max_instances)
+                              max_instances=max_instances, topk_layout=topk_layout)
+        self.layout = topk_layout
         dev = self.r.device
         tdt = self.r.feat_torch_dtype
         t = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to(dev).to(dt).contiguous()
@@ -165,12 +166,13 @@ def run_bf16_batched(args, hbm):
     for K in (4, 8, 16):
         # K is the model's parameter (it changes the render); the tile shape is tuned per K
         scene_k = (sc, cams, K, tile0, fdt)
-        tuned = autotune.tune(cams, sc.n, K, sc.d, fdt, lambda tile: Step("batched", tile=tile, scene=scene_k).run)
+        tuned = autotune.tune(cams, sc.n, K, sc.d, fdt,
+                              lambda tile, lay: Step("batched", tile=tile, scene=scene_k, topk_layout=lay).run)
         torch.cuda.empty_cache()
-        step = Step("batched", tile=tuned["tile"], scene=scene_k)
+        step = Step("batched", tile=tuned["tile"], scene=scene_k, topk_layout=autotune.KBUF_LAYOUTS[tuned["layout"]])
         ms = autotune.time_step(lambda: step.run, reps=max(5, min(args.steps, 20)), warmup=args.warmup)
         st = status_of(step)
-        sweep.append({"K": K, "tile": list(tuned["tile"]), "ms_per_step": round(ms, 4),
+        sweep.append({"K": K, "tile": list(tuned["tile"]), "kbuf_layout": tuned["layout"], "ms_per_step": round(ms, 4),
                       "value": round(step.P / (ms * 1e-3) / 1e6, 3), "autotune_ms": tuned["ms"], "status": st})
         if K == K0:
             main_roof = stage_rooflines(step, hbm)
@@ -180,6 +182,7 @@ def run_bf16_batched(args, hbm):
     main = next(r for r in sweep if r["K"] == K0)
     out = {"value": main["value"], "unit": UNIT, "ms_per_step": main["ms_per_step"], "pixels_per_step": P,
            "gaussians": N, "views": len(cams), "D": D, "K": K0, "dtype": "bf16", "tile": main["tile"],
+           "kbuf_layout": main["kbuf_layout"],
            "status": main["status"], "roofline": main_roof["blend_loss"], "backward_roofline": main_roof["backward"],
            "autotune_ms": main["autotune_ms"], "k_sweep": [{k: v for k, v in r.items() if k != "autotune_ms"}
                                                             for r in sweep],

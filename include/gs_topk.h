@@ -80,6 +80,9 @@ typedef struct {
     int32_t max_feature_rows;  /* capacity of gs_backward's partial feature-gradient rows, one per (pixel
                                   block, selected Gaussian); 0: 32 per block, or max_instances per
                                   (camera, Gaussian) when that is larger */
+    int32_t topk_layout;       /* where gs_topk_select keeps each pixel's K-buffer while it walks: 0 in
+                                  registers, 1 in shared memory (K <= 16; fewer registers per thread).
+                                  The outputs are identical; a performance choice for an autotuner */
 } gs_config;
 
 /* Per-Gaussian gradient outputs of gs_backward (device, caller-allocated, fully

@@ -32,7 +32,7 @@ class GsCamera(ctypes.Structure):
 class GsConfig(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("D", ctypes.c_int32), ("tile_w", ctypes.c_int32),
                 ("tile_h", ctypes.c_int32), ("feat_dtype", ctypes.c_int32), ("max_instances", ctypes.c_int32),
-                ("max_feature_rows", ctypes.c_int32)]
+                ("max_feature_rows", ctypes.c_int32), ("topk_layout", ctypes.c_int32)]
 
 
 class GsGrads(ctypes.Structure):

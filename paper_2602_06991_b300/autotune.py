@@ -1,11 +1,12 @@
-"""Autotuner for the screen-tile shape of a render configuration.
+"""Autotuner for the screen-tile shape and the K-buffer layout of a render configuration.
 
-Results do not depend on the tile shape (a Gaussian takes part at a pixel by a per-pixel
-test, not by tile membership), so the tile shape is a pure performance choice.  For a
-given configuration -- cameras, Gaussian count, K, D, feature dtype -- every compiled
-shape is timed on the full training step replayed as a CUDA graph, and the fastest is
-cached in a JSON file keyed by the configuration.  K itself is a model parameter (it
-changes the rendered feature), so it is part of the key, never tuned.
+Results depend on neither (a Gaussian takes part at a pixel by a per-pixel test, not by
+tile membership; the walk keeps the same Top-K whether its K-buffer lives in registers
+or in shared memory), so both are pure performance choices.  For a given configuration
+-- cameras, Gaussian count, K, D, feature dtype -- every compiled (shape, layout) pair is
+timed on the full training step replayed as a CUDA graph, and the fastest is cached in a
+JSON file keyed by the configuration.  K itself is a model parameter (it changes the
+rendered feature), so it is part of the key, never tuned.
 """
 from __future__ import annotations
 
@@ -17,6 +18,8 @@ from typing import Dict, Sequence
 import torch
 
 TILE_SHAPES = [(16, 16), (32, 8), (16, 8), (8, 8)]
+# where the walk keeps each pixel's Top-K (gs_config.topk_layout): registers, shared memory
+KBUF_LAYOUTS = {"reg": 0, "smem": 1}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 
 
@@ -67,21 +70,30 @@ def time_step(make_step, reps: int = 10, warmup: int = 3) -> float:
     return e0.elapsed_time(e1) / reps
 
 
+def layouts_for(K: int) -> Dict[str, int]:
+    """The K-buffer layouts compiled for K (the shared-memory form holds K <= 16)."""
+    return {n: v for n, v in KBUF_LAYOUTS.items() if v == 0 or K <= 16}
+
+
 def tune(cameras, n_gauss: int, K: int, D: int, feat_dtype: str, step_factory, cache_path: str = DEFAULT_CACHE,
-         shapes=TILE_SHAPES, force: bool = False) -> Dict:
-    """step_factory(tile) -> callable running one training step with that tile shape.
-    Returns {"tile": (w, h), "ms": {shape: ms}} and caches it."""
+         shapes=TILE_SHAPES, layouts=None, force: bool = False) -> Dict:
+    """step_factory(tile, layout) -> callable running one training step with that tile
+    shape and K-buffer layout.  Returns {"tile": (w, h), "layout": name, "ms": {"WxH/name":
+    ms}} and caches it."""
     key = config_key(cameras, n_gauss, K, D, feat_dtype)
     cache = load_cache(cache_path)
-    if not force and key in cache:
+    if not force and key in cache and "layout" in cache[key]:
         hit = cache[key]
-        return {"tile": tuple(hit["tile"]), "ms": hit["ms"], "cached": True}
+        return {"tile": tuple(hit["tile"]), "layout": hit["layout"], "ms": hit["ms"], "cached": True}
+    layouts = layouts_for(K) if layouts is None else layouts
     ms = {}
     for shape in shapes:
-        ms[f"{shape[0]}x{shape[1]}"] = time_step(lambda: step_factory(shape))
-        torch.cuda.empty_cache()
+        for name, value in layouts.items():
+            ms[f"{shape[0]}x{shape[1]}/{name}"] = time_step(lambda: step_factory(shape, value))
+            torch.cuda.empty_cache()
     best = min(ms, key=ms.get)
-    tile = tuple(int(v) for v in best.split("x"))
-    cache[key] = {"tile": list(tile), "ms": ms}
+    shape_s, layout = best.split("/")
+    tile = tuple(int(v) for v in shape_s.split("x"))
+    cache[key] = {"tile": list(tile), "layout": layout, "ms": ms}
     save_cache(cache, cache_path)
-    return {"tile": tile, "ms": ms, "cached": False}
+    return {"tile": tile, "layout": layout, "ms": ms, "cached": False}

@@ -24,7 +24,8 @@ bool cfg_ok(const gs_config *cfg)
 {
     return cfg && cfg->K >= 1 && cfg->K <= GS_MAX_K && cfg->D >= 8 && cfg->D <= 1024 && cfg->D % 8 == 0 &&
            tile_ok(cfg->tile_w, cfg->tile_h) && (cfg->feat_dtype == GS_F32 || cfg->feat_dtype == GS_BF16) &&
-           cfg->max_instances >= 0 && cfg->max_feature_rows >= 0;
+           cfg->max_instances >= 0 && cfg->max_feature_rows >= 0 &&
+           (cfg->topk_layout == 0 || (cfg->topk_layout == 1 && cfg->K <= 16));
 }
 
 static bool cams_ok(const gs_camera *cams, int n_cams)
@@ -292,8 +293,8 @@ int gs_topk_select(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, 
     if (st) return st;
     CamTable ct;
     make_camtable(cfg, cams, n_cams, ct);
-    if (!launch_walk_fwd(ct, L, cfg->K, n_gauss, proj, ws, rgb_out, depth_out, T_final, n_contrib, topk_idx, topk_w,
-                         (cudaStream_t)stream))
+    if (!launch_walk_fwd(ct, L, cfg->K, cfg->topk_layout, n_gauss, proj, ws, rgb_out, depth_out, T_final, n_contrib,
+                         topk_idx, topk_w, (cudaStream_t)stream))
         return GS_ERR_UNSUPPORTED;
     return launch_status();
 }
@@ -305,7 +306,7 @@ int gs_feature_blend(const gs_config *cfg, int64_t n_pix, int32_t n_gauss, const
     if (n_pix > 0 && (!topk_idx || !topk_w || !F_out)) return GS_ERR_ARG;
     if (n_gauss > 0 && !feats) return GS_ERR_ARG;
     if (((uintptr_t)feats & 15) != 0 || ((uintptr_t)F_out & 15) != 0) return GS_ERR_ARG;
-    if (!launch_blend(cfg->feat_dtype, cfg->K, cfg->D, n_pix, topk_idx, topk_w, feats, F_out, nullptr,
+    if (!launch_blend(cfg->feat_dtype, cfg->K, cfg->D, n_pix, n_gauss, topk_idx, topk_w, feats, F_out, nullptr,
                       (cudaStream_t)stream))
         return GS_ERR_UNSUPPORTED;
     return launch_status();
@@ -363,7 +364,8 @@ int gs_backward_ex(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, 
     if (with_feature) {
         // h = dL/dF . f per slot: left in ws by gs_feature_blend_loss when the caller
         // says dL_dF is that call's and the call took the path that writes it
-        const bool h_ready = (flags & GS_BWD_H_FROM_LOSS) && blend_loss_writes_h(cfg->feat_dtype, cfg->K, cfg->D);
+        const bool h_ready =
+            (flags & GS_BWD_H_FROM_LOSS) && blend_loss_writes_h(cfg->feat_dtype, cfg->K, cfg->D, n_gauss);
         ok = launch_feature_grad(ct, L, cfg->feat_dtype, n_gauss, topk_idx, topk_w, dL_dF, grads->feat, ws,
                                  aux ? aux->s : s) &&
              (h_ready || launch_feature_h(L, cfg->feat_dtype, topk_idx, feats, dL_dF, ws, s));
@@ -426,7 +428,7 @@ int gs_feature_blend_loss(const gs_config *cfg, const gs_camera *cams, int32_t n
     if (!scratch || ((uintptr_t)scratch & 15) || scratch_bytes < gs_loss_scratch_size(L.P)) return GS_ERR_WORKSPACE;
     CamTable ct;
     make_camtable(cfg, cams, n_cams, ct);
-    if (!launch_blend_loss(ct, cfg->feat_dtype, cfg->K, cfg->D, L.P, topk_idx, topk_w, feats, F_gt, rgb, rgb_gt, depth,
+    if (!launch_blend_loss(ct, cfg->feat_dtype, cfg->K, cfg->D, L.P, n_gauss, topk_idx, topk_w, feats, F_gt, rgb, rgb_gt, depth,
                            depth_gt, w_feat, w_rgb, w_depth, F_out, dL_dF, dL_dC, dL_dD, loss, (float *)scratch,
                            ws_ptr<float>(ws, L.hbuf), ws_ptr<int>(ws, L.header), (cudaStream_t)stream))
         return GS_ERR_UNSUPPORTED;

@@ -52,12 +52,13 @@ __global__ void k_count_tiles(CamTable ct, int N, long long NE, const float4 *__
 // One warp per 32 consecutive depth ranks: each lane works out its element's tile
 // rectangle, then the warp writes the instances element by element, lanes striding over
 // the rectangle, so large footprints are written in parallel and coalesced.
+// (An instance's sort value is its own index, which the tile sort generates; the
+// re-walk's walked flags are cleared by k_clear_walked.)
 __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
                                                    const uint32_t *__restrict__ sorted_e,
                                                    const uint32_t *__restrict__ offsets, uint32_t mcap,
-                                                   uint32_t *inst_keys, uint32_t *inst_vals, uint32_t *inst_elem,
-                                                   uint8_t *inst_walked, uint32_t *elem_off, uint32_t *elem_cnt,
-                                                   int *err)
+                                                   uint32_t *inst_keys, uint32_t *inst_elem,
+                                                   uint32_t *elem_off, uint32_t *elem_cnt, int *err)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -88,11 +89,22 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
             if (oo >= mcap) break;
             int ty = y0 + (int)(t / (uint32_t)w), tx = x0 + (int)(t % (uint32_t)w);
             inst_keys[oo] = (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx);
-            inst_vals[oo] = oo;
             inst_elem[oo] = ej;
-            inst_walked[oo] = 0;                // set by the re-walk for the instances it reaches
         }
     }
+}
+
+// Clears the walked flags of the instances [0, min(*n_dev, mcap)), 16 bytes per store
+// (the re-walk sets the flags of the instances it reaches).
+__global__ void __launch_bounds__(256) k_clear_walked(const uint32_t *n_dev, uint32_t mcap, uint8_t *walked)
+{
+    const long long n = min(*n_dev, mcap);
+    const long long n16 = n / 16;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride)
+        ((uint4 *)walked)[i] = make_uint4(0u, 0u, 0u, 0u);
+    const long long tail = n16 * 16 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tail < n) walked[tail] = 0;
 }
 
 // Per-tile [start, end) of the sorted instances: one warp per tile finds the first
@@ -167,9 +179,10 @@ void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *
     int dcur = radix_sort_pairs(dk[0], dk[1], dv[0], dv[1], NE, nullptr, 32, hist, s);
     k_count_tiles<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], counts, elem_cnt);
     exclusive_scan_u32(counts, counts, NE, n_inst, aux, s);
-    k_duplicate<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], counts, (uint32_t)L.Mcap, ik[0], iv[0], inst_elem,
-                                  ws_ptr<uint8_t>(ws, L.inst_walked), elem_off, elem_cnt, err);
-    int icur = radix_sort_pairs(ik[0], ik[1], iv[0], iv[1], L.Mcap, n_inst, bits_for(L.n_tiles), hist, s);
+    k_duplicate<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], counts, (uint32_t)L.Mcap, ik[0], inst_elem, elem_off,
+                                  elem_cnt, err);
+    k_clear_walked<<<148 * 8, 256, 0, s>>>(n_inst, (uint32_t)L.Mcap, ws_ptr<uint8_t>(ws, L.inst_walked));
+    int icur = radix_sort_pairs(ik[0], ik[1], iv[0], iv[1], L.Mcap, n_inst, bits_for(L.n_tiles), hist, s, true);
     (void)icur;   // equals L.inst_sorted
     k_tile_ranges<<<(unsigned)(((long long)L.n_tiles * 32 + 255) / 256), 256, 0, s>>>(
         ik[L.inst_sorted], n_inst, (uint32_t)L.Mcap, ranges, (uint32_t)L.n_tiles);

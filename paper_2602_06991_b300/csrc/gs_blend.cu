@@ -307,10 +307,11 @@ static bool blend_k(int KM, int K, int nch, long long n_pix, const int *idx, con
     return false;
 }
 
-bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, const float *w, const void *feats,
-                  void *F, const int *err, cudaStream_t s)
+bool launch_blend(int dtype, int K, int D, long long n_pix, long long N, const int *idx, const float *w,
+                  const void *feats, void *F, const int *err, cudaStream_t s)
 {
     if (n_pix <= 0) return true;
+    if (blend_mma_supported(dtype, K, D, N)) return launch_blend_mma(K, D, n_pix, idx, w, feats, F, err, s);
     int KM = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
     const int nch = dtype == GS_BF16 ? D / 8 : D / 4;
     const int cpl = group_cpl(dtype, K, nch);
@@ -463,10 +464,11 @@ __global__ void __launch_bounds__(256) k_h_pixel(long long n_pix, int K, int nch
     }
 }
 
-bool launch_h(int dtype, int K, int D, long long n_pix, const int *idx, const void *feats, const void *dLdF,
-              float *h, const int *err, cudaStream_t s)
+bool launch_h(int dtype, int K, int D, long long n_pix, long long N, const int *idx, const void *feats,
+              const void *dLdF, float *h, const int *err, cudaStream_t s)
 {
     if (n_pix <= 0) return true;
+    if (blend_mma_supported(dtype, K, D, N)) return launch_h_mma(K, D, n_pix, idx, feats, dLdF, h, err, s);
     const int KM = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
     const int nch = dtype == GS_BF16 ? D / 8 : D / 4;
     const int cpl = group_cpl(dtype, K, nch);
@@ -853,18 +855,27 @@ static bool blend_loss_cpl(int cpl, unsigned blocks, long long n_pix, int K, int
     return false;
 }
 
-bool blend_loss_writes_h(int dtype, int K, int D)
+bool blend_loss_writes_h(int dtype, int K, int D, long long N)
 {
-    return group_cpl(dtype, K, dtype == GS_BF16 ? D / 8 : D / 4) != 0;
+    return blend_mma_supported(dtype, K, D, N) || group_cpl(dtype, K, dtype == GS_BF16 ? D / 8 : D / 4) != 0;
 }
 
-bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_pix, const int *idx, const float *w,
-                       const void *feats, const void *Fgt, const float *C, const float *Cgt, const float *Dp,
-                       const float *Dgt, float wf, float wc, float wd, void *F, void *dLdF, float *dLdC, float *dLdD,
-                       float *loss, float *part, float *h, const int *err, cudaStream_t s)
+bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_pix, long long N, const int *idx,
+                       const float *w, const void *feats, const void *Fgt, const float *C, const float *Cgt,
+                       const float *Dp, const float *Dgt, float wf, float wc, float wd, void *F, void *dLdF,
+                       float *dLdC, float *dLdD, float *loss, float *part, float *h, const int *err, cudaStream_t s)
 {
     (void)ct;
     if (n_pix <= 0) return true;
+    if (blend_mma_supported(dtype, K, D, N)) {
+        if (!launch_blend_loss_mma(K, D, n_pix, idx, w, feats, Fgt, C, Cgt, Dp, Dgt, wf, wc, wd, 1.f / (float)n_pix, F,
+                                   dLdF, dLdC, dLdD, part, h, err, s))
+            return false;
+        float *part2 = part + n_pix;
+        k_sum_fixed<<<kSortBlocks, 1024, 0, s>>>(part, n_pix, part2);
+        k_sum_fixed<<<1, 1024, 0, s>>>(part2, kSortBlocks, loss);
+        return true;
+    }
     const int KM = K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
     const int nch = dtype == GS_BF16 ? D / 8 : D / 4;
     const int l = lpp_log2_for(nch);

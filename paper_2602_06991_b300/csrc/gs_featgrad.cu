@@ -222,7 +222,7 @@ bool launch_feature_h(const WsLayout &L, int dtype, const int *topk_idx, const v
                       void *ws, cudaStream_t s)
 {
     if (!L.use_tiles) return false;
-    return launch_h(dtype, L.K, L.D, L.P, topk_idx, feats, dLdF, ws_ptr<float>(ws, L.hbuf),
+    return launch_h(dtype, L.K, L.D, L.P, L.N, topk_idx, feats, dLdF, ws_ptr<float>(ws, L.hbuf),
                     ws_ptr<const int>(ws, L.header), s);
 }
 

@@ -269,6 +269,44 @@ struct TopK {
     }
 };
 
+// The same Top-K kept in shared memory, slot-major ([slot][thread], B threads), so the
+// per-thread registers drop by 2 KM; the smallest kept weight stays in a register for the
+// early rejection.  Insertion from the tail: the new entry goes after every kept entry of
+// weight >= it -- the position the register network gives -- so both hold identical sets
+// in identical order.
+template <int KM, int B>
+struct TopKShared {
+    float *w;
+    int *id;
+    float wmin;
+    __device__ __forceinline__ void init(float *sw, int *sid, int tid, int K)
+    {
+        w = sw + tid;
+        id = sid + tid;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            w[k * B] = (k < KM - K) ? __int_as_float(0x7f800000) : -1.0f;
+            id[k * B] = -1;
+        }
+        wmin = -1.0f;
+    }
+    __device__ __forceinline__ void insert(float nw, int nid)
+    {
+        if (!(nw > wmin)) return;
+        int pos = KM - 1;
+        while (pos > 0) {
+            const float prev = w[(pos - 1) * B];
+            if (!(nw > prev)) break;
+            w[pos * B] = prev;
+            id[pos * B] = id[(pos - 1) * B];
+            --pos;
+        }
+        w[pos * B] = nw;
+        id[pos * B] = nid;
+        wmin = w[(KM - 1) * B];
+    }
+};
+
 // ------------------------------------------------------------------------------------
 // Workspace layout (host-computed; all offsets 256-byte aligned)
 // ------------------------------------------------------------------------------------
@@ -351,10 +389,12 @@ bool launch_prune_select(int N, const int *count, const float *S, int tau, doubl
                          uint8_t *keep, void *ws, cudaStream_t s);
 // LSD radix sort of (key, value) uint32 pairs on key bits [0, n_bits); stable.  The
 // element count is n_host, or *n_dev clamped to n_host if n_dev is non-null.
-// Returns the index (0/1) of the buffer pair holding the sorted result.
+// vals_are_index: the input values are the positions 0, 1, 2, ... (vals0 is not read).
+// The arrays start 16-byte aligned.  Returns the index (0/1) of the buffer pair holding
+// the sorted result.
 int radix_sort_pairs(uint32_t *keys0, uint32_t *keys1, uint32_t *vals0, uint32_t *vals1,
                      long long n_host, const uint32_t *n_dev, int n_bits, uint32_t *hist,
-                     cudaStream_t s);
+                     cudaStream_t s, bool vals_are_index = false);
 // Exclusive scan of n uint32 in -> out (may alias); *total (device) = sum if non-null.
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t *total,
                         uint32_t *aux, cudaStream_t s);
@@ -365,14 +405,25 @@ void launch_project_backward(const CamTable &ct, int N, const float *mean3d, con
                              const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad, const uint8_t *walked,
                              float *elem_grad, const int *err, const gs_grads *gr, float *pose_part, cudaStream_t s);
 void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *proj, void *ws, cudaStream_t s);
-bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj, void *ws,
+// kbuf: where the walk keeps each pixel's Top-K (gs_config.topk_layout): 0 registers,
+// 1 shared memory (KM <= 16); identical results.
+bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int kbuf, int N, const float *proj, void *ws,
                      float *rgb_out, float *depth_out, float *T_out, int *n_out, int *idx_out, float *w_out,
                      cudaStream_t s);
 bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj, void *ws,
                      const float *rgb_out, const float *depth_out, const int *topk_idx, const float *topk_w,
                      const float *dLdC, const float *dLdD, bool with_feature, cudaStream_t s);
-bool launch_blend(int dtype, int K, int D, long long n_pix, const int *idx, const float *w, const void *feats,
-                  void *F, const int *err, cudaStream_t s);
+// Gather-blend (a4); bf16 rows with K in {2, 4, 8, 16}, D a multiple of 64 and fewer than
+// 2^24 Gaussians take the tensor-core form (gs_blend_mma.cu), the rest the CUDA-core forms.
+bool launch_blend(int dtype, int K, int D, long long n_pix, long long N, const int *idx, const float *w,
+                  const void *feats, void *F, const int *err, cudaStream_t s);
+bool blend_mma_supported(int dtype, int K, int D, long long N);
+bool launch_blend_mma(int K, int D, long long n_pix, const int *idx, const float *w, const void *feats, void *F,
+                      const int *err, cudaStream_t s);
+bool launch_blend_loss_mma(int K, int D, long long n_pix, const int *idx, const float *w, const void *feats,
+                           const void *Fgt, const float *C, const float *Cgt, const float *Dp, const float *Dgt,
+                           float wf, float wc, float wd, float invP, void *F, void *dLdF, float *dLdC, float *dLdD,
+                           float *part, float *h, const int *err, cudaStream_t s);
 bool launch_feature_h(const WsLayout &L, int dtype, const int *topk_idx, const void *feats, const void *dLdF,
                       void *ws, cudaStream_t s);
 bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N, const int *topk_idx,
@@ -386,15 +437,17 @@ struct FgBlock {
 FgBlock fg_block_shape(int dtype, int D, int K);
 size_t tile_runs_bytes(int B, int K);
 void retile(const CamTable &ct, int bw, int bh, CamTable &out);
-bool launch_h(int dtype, int K, int D, long long n_pix, const int *idx, const void *feats, const void *dLdF,
-              float *h, const int *err, cudaStream_t s);
+bool launch_h(int dtype, int K, int D, long long n_pix, long long N, const int *idx, const void *feats,
+              const void *dLdF, float *h, const int *err, cudaStream_t s);
+bool launch_h_mma(int K, int D, long long n_pix, const int *idx, const void *feats, const void *dLdF, float *h,
+                  const int *err, cudaStream_t s);
 // The fused training form also writes h = dL/dF . f per Top-K slot (into `h`) when it
 // takes the pixel-group path; blend_loss_writes_h says whether it does.
-bool blend_loss_writes_h(int dtype, int K, int D);
-bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_pix, const int *idx, const float *w,
-                       const void *feats, const void *Fgt, const float *C, const float *Cgt, const float *Dp,
-                       const float *Dgt, float wf, float wc, float wd, void *F, void *dLdF, float *dLdC, float *dLdD,
-                       float *loss, float *part, float *h, const int *err, cudaStream_t s);
+bool blend_loss_writes_h(int dtype, int K, int D, long long N);
+bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_pix, long long N, const int *idx,
+                       const float *w, const void *feats, const void *Fgt, const float *C, const float *Cgt,
+                       const float *Dp, const float *Dgt, float wf, float wc, float wd, void *F, void *dLdF,
+                       float *dLdC, float *dLdD, float *loss, float *part, float *h, const int *err, cudaStream_t s);
 bool launch_loss(int dtype, int D, long long n_pix, const void *F, const void *Fgt, const float *C, const float *Cgt,
                  const float *Dp, const float *Dgt, float wf, float wc, float wd, void *dLdF, float *dLdC,
                  float *dLdD, float *loss, float *part, cudaStream_t s);

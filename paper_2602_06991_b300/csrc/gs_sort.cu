@@ -122,22 +122,40 @@ __global__ void __launch_bounds__(1024) k_scan_single(uint32_t *data, int len, u
     if (total && tid == 1023) *total = run;
 }
 
+// Asynchronous 16-byte global -> shared copy (cp.async, L2 only) of the first `bytes`
+// (0..16) of the chunk; the rest of the destination is zero-filled, and nothing past
+// `bytes` is read.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int bytes)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Downsweep of a pass: per tile of kSortTile keys, stable ranks (warp match +
 // per-warp digit counters), then the tile is reordered by digit in shared memory and
 // written out in that order, so each digit's run of the tile goes to consecutive
-// addresses (coalesced) instead of one scattered store per key.
+// addresses (coalesced) instead of one scattered store per key.  The next tile's keys
+// and values are copied into shared memory (cp.async) while the current one is ranked
+// and written, so the global load latency of a tile is hidden behind the previous
+// tile's work; the current tile's buffer is then reused for its reordering.
+// vin == nullptr: the values are the keys' input positions (0, 1, 2, ...), generated
+// here instead of read.
 __global__ void __launch_bounds__(kSortThreads) k_rs_downsweep(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                                                                uint32_t *__restrict__ kout, uint32_t *__restrict__ vout,
                                                                long long n_host, const uint32_t *n_dev, int shift,
                                                                const uint32_t *__restrict__ hist)
 {
     constexpr int W = kSortThreads / 32;
+    constexpr int kChunks = kSortTile / 4;           // 16-byte chunks per tile and array
     __shared__ uint32_t s_base[256];     // global position of this block's next key of each digit
     __shared__ uint32_t s_tot[W];
     __shared__ uint32_t s_start[256];    // first position of each digit in the reordered tile
     __shared__ uint32_t s_wsum[W];
     __shared__ uint32_t s_wcnt[W][257];
-    __shared__ uint32_t s_k[kSortTile], s_v[kSortTile];
+    __shared__ __align__(16) uint32_t s_k[2][kSortTile], s_v[2][kSortTile];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     {
@@ -158,18 +176,39 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_downsweep(const uint32_t *_
     }
     long long n = sort_count(n_host, n_dev), t0, t1;
     block_tiles(n, t0, t1);
-    for (long long t = t0; t < t1; ++t) {
+    // the copies of tile t into buffer b: chunk c covers keys [4c, 4c + 4) of the tile
+    auto issue = [&](long long t, int b) {
+        const long long first = t * kSortTile;
+        for (int c = tid; c < kChunks; c += kSortThreads) {
+            const long long e = first + 4ll * c;
+            const long long left = n - e;
+            const int bytes = left >= 4 ? 16 : left > 0 ? (int)left * 4 : 0;
+            const long long src = bytes > 0 ? e : 0;          // a valid address even when nothing is read
+            cp_async16(&s_k[b][4 * c], kin + src, bytes);
+            if (vin) cp_async16(&s_v[b][4 * c], vin + src, bytes);
+        }
+        cp_async_commit();
+    };
+    if (t0 < t1) issue(t0, 0);
+    int buf = 0;
+    for (long long t = t0; t < t1; ++t, buf ^= 1) {
+        if (t + 1 < t1) {
+            issue(t + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         for (int i = tid; i < W * 257; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
         __syncthreads();
-        long long wbase = t * kSortTile + (long long)warp * 32 * kSortItems;
         uint32_t k[kSortItems], v[kSortItems], lr[kSortItems];
         int dg[kSortItems];
+        const int wloc = warp * 32 * kSortItems;
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
-            long long idx = wbase + i * 32 + lane;
-            bool valid = idx < n;
-            k[i] = valid ? __ldg(kin + idx) : 0u;
-            v[i] = valid ? __ldg(vin + idx) : 0u;
+            const int loc = wloc + i * 32 + lane;
+            const bool valid = t * kSortTile + loc < n;
+            k[i] = s_k[buf][loc];
+            v[i] = vin ? s_v[buf][loc] : (uint32_t)(t * kSortTile + loc);
             dg[i] = valid ? (int)((k[i] >> shift) & 255u) : 256;
         }
 #pragma unroll
@@ -206,23 +245,24 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_downsweep(const uint32_t *_
             s_start[tid] = inc - run + before;
         }
         __syncthreads();
+        // every thread has read its items of this buffer (barriers above): reorder in place
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
             if (dg[i] < 256) {
                 const uint32_t lp = s_start[dg[i]] + s_wcnt[warp][dg[i]] + lr[i];
-                s_k[lp] = k[i];
-                s_v[lp] = v[i];
+                s_k[buf][lp] = k[i];
+                s_v[buf][lp] = v[i];
             }
         }
         __syncthreads();
         const long long rem = n - t * kSortTile;
         const int cnt = rem < kSortTile ? (int)rem : kSortTile;
         for (int j = tid; j < cnt; j += kSortThreads) {
-            const uint32_t kk = s_k[j];
+            const uint32_t kk = s_k[buf][j];
             const int d = (int)((kk >> shift) & 255u);
             const uint32_t pos = s_base[d] + (uint32_t)j - s_start[d];
             kout[pos] = kk;
-            vout[pos] = s_v[j];
+            vout[pos] = s_v[buf][j];
         }
         __syncthreads();
         s_base[tid] += run;
@@ -230,8 +270,10 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_downsweep(const uint32_t *_
 }
 
 int radix_sort_pairs(uint32_t *keys0, uint32_t *keys1, uint32_t *vals0, uint32_t *vals1,
-                     long long n_host, const uint32_t *n_dev, int n_bits, uint32_t *hist, cudaStream_t s)
+                     long long n_host, const uint32_t *n_dev, int n_bits, uint32_t *hist, cudaStream_t s,
+                     bool vals_are_index)
 {
+    // the four arrays start 16-byte aligned (the downsweep copies 16-byte chunks)
     if (n_host <= 0 || n_bits <= 0) return 0;
     int passes = (n_bits + 7) / 8;
     long long n_tiles = (n_host + kSortTile - 1) / kSortTile;
@@ -242,7 +284,8 @@ int radix_sort_pairs(uint32_t *keys0, uint32_t *keys1, uint32_t *vals0, uint32_t
         int shift = 8 * p;
         k_rs_upsweep<<<G, kSortThreads, 0, s>>>(kb[cur], n_host, n_dev, shift, hist);
         k_rs_scan<<<256, 512, 0, s>>>(hist, G);
-        k_rs_downsweep<<<G, kSortThreads, 0, s>>>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n_host, n_dev, shift, hist);
+        const uint32_t *vin = (p == 0 && vals_are_index) ? nullptr : vb[cur];
+        k_rs_downsweep<<<G, kSortThreads, 0, s>>>(kb[cur], vin, kb[cur ^ 1], vb[cur ^ 1], n_host, n_dev, shift, hist);
         cur ^= 1;
     }
     return cur;

@@ -5,8 +5,9 @@
 // depth-ordered instance list is staged through shared memory in batches of one
 // record per thread; each pixel evaluates alpha with the double-float offset and the
 // Cholesky-form conic, accumulates colour and depth (Eq. 1) and keeps its Top-K
-// (Eq. 2) in registers by insertion.  A batch loop ends as soon as every pixel of the
-// tile has stopped.
+// (Eq. 2) by insertion, in registers or (gs_config.topk_layout = 1, fewer registers)
+// in shared memory, with identical results.  A batch loop ends as soon as every pixel
+// of the tile has stopped.
 //
 // Backward: the same walk is recomputed (not stored) with the very same inlined
 // evaluation, so contributor sets and transmittances match the forward bit for bit.
@@ -25,10 +26,12 @@
 #include "gs_internal.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace gs {
 
-template <int TW, int TH, int KM>
+// KB: the Top-K buffer in registers (0) or in shared memory (1); identical results.
+template <int TW, int TH, int KM, int KB>
 __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, const float4 *__restrict__ proj,
                                                      const uint32_t *__restrict__ inst_vals,
                                                      const uint32_t *__restrict__ inst_elem,
@@ -58,8 +61,13 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dd = 0.f;
     int nc = 0;
-    TopK<KM> tk;
-    tk.init(K);
+    constexpr int KMS = KB ? KM : 1;
+    __shared__ float s_kw[KMS * B];
+    __shared__ int s_kid[KMS * B];
+    using Buf = typename std::conditional<KB == 0, TopK<KM>, TopKShared<KM, B>>::type;
+    Buf tk;
+    if constexpr (KB == 0) tk.init(K);
+    else tk.init(s_kw, s_kid, tid, K);
     bool done = !inside;
     const int cN = c * N;
     for (int b0 = rg.x; b0 < rg.y; b0 += B) {
@@ -118,8 +126,17 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
     for (int k = 0; k < KM; ++k) {
         if (k >= KM - K) {
             int slot = k - (KM - K);
-            idx_out[p * K + slot] = tk.id[k];
-            w_out[p * K + slot] = tk.w[k] > 0.f ? tk.w[k] : 0.f;
+            float wk;
+            int ik;
+            if constexpr (KB == 0) {
+                wk = tk.w[k];
+                ik = tk.id[k];
+            } else {
+                wk = tk.w[k * B];
+                ik = tk.id[k * B];
+            }
+            idx_out[p * K + slot] = ik;
+            w_out[p * K + slot] = wk > 0.f ? wk : 0.f;
         }
     }
 }
@@ -324,17 +341,27 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
 }
 
 template <int TW, int TH>
-static bool walk_fwd_k(int KM, dim3 grid, cudaStream_t s, const CamTable &ct, int K, int N, const float4 *proj,
-                       const uint32_t *iv, const uint32_t *ie, const int2 *rg, const int *err, float *a, float *b,
-                       float *cc, int *d, int *e, float *f)
+static bool walk_fwd_k(int KM, int kbuf, dim3 grid, cudaStream_t s, const CamTable &ct, int K, int N,
+                       const float4 *proj, const uint32_t *iv, const uint32_t *ie, const int2 *rg, const int *err,
+                       float *a, float *b, float *cc, int *d, int *e, float *f)
 {
     constexpr int B = TW * TH;
-    switch (KM) {
-    case 4: k_walk_fwd<TW, TH, 4><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, a, b, cc, d, e, f); return true;
-    case 8: k_walk_fwd<TW, TH, 8><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, a, b, cc, d, e, f); return true;
-    case 16: k_walk_fwd<TW, TH, 16><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, a, b, cc, d, e, f); return true;
-    case 32: k_walk_fwd<TW, TH, 32><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, a, b, cc, d, e, f); return true;
+#define GS_WF(KMV, KBV) k_walk_fwd<TW, TH, KMV, KBV><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, a, b, cc, d, e, f)
+    if (kbuf == 1) {
+        switch (KM) {
+        case 4: GS_WF(4, 1); return true;
+        case 8: GS_WF(8, 1); return true;
+        case 16: GS_WF(16, 1); return true;
+        }
+        return false;                        // (KM = 32 has no shared form: the buffer would not fit)
     }
+    switch (KM) {
+    case 4: GS_WF(4, 0); return true;
+    case 8: GS_WF(8, 0); return true;
+    case 16: GS_WF(16, 0); return true;
+    case 32: GS_WF(32, 0); return true;
+    }
+#undef GS_WF
     return false;
 }
 
@@ -368,7 +395,7 @@ static bool walk_bwd_k(int KM, dim3 grid, cudaStream_t s, const CamTable &ct, in
 
 static int k_bucket(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32; }
 
-bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj_f, void *ws,
+bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int kbuf, int N, const float *proj_f, void *ws,
                      float *rgb_out, float *depth_out, float *T_out, int *n_out, int *idx_out, float *w_out,
                      cudaStream_t s)
 {
@@ -379,10 +406,10 @@ bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int N, const 
     const int2 *rg = ws_ptr<int2>(ws, L.tile_range);
     dim3 grid(ct.n_tiles);
     int KM = k_bucket(K);
-    if (ct.tile_w == 16 && ct.tile_h == 16) return walk_fwd_k<16, 16>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
-    if (ct.tile_w == 32 && ct.tile_h == 8) return walk_fwd_k<32, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
-    if (ct.tile_w == 16 && ct.tile_h == 8) return walk_fwd_k<16, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
-    if (ct.tile_w == 8 && ct.tile_h == 8) return walk_fwd_k<8, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
+    if (ct.tile_w == 16 && ct.tile_h == 16) return walk_fwd_k<16, 16>(KM, kbuf, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
+    if (ct.tile_w == 32 && ct.tile_h == 8) return walk_fwd_k<32, 8>(KM, kbuf, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
+    if (ct.tile_w == 16 && ct.tile_h == 8) return walk_fwd_k<16, 8>(KM, kbuf, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
+    if (ct.tile_w == 8 && ct.tile_h == 8) return walk_fwd_k<8, 8>(KM, kbuf, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
     return false;
 }
 

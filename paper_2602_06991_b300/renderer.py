@@ -42,7 +42,8 @@ class TopKRenderer:
     """One configuration (cameras, K, D, tile, feature dtype) and its workspace."""
 
     def __init__(self, cameras: Sequence, K: int, D: int, tile=(16, 16), feat_dtype: str = "f32",
-                 max_instances: int = 0, device=None, check_overflow: bool = True, max_feature_rows: int = 0):
+                 max_instances: int = 0, device=None, check_overflow: bool = True, max_feature_rows: int = 0,
+                 topk_layout: int = 0):
         self.lib = A.load()
         self.cams = A.make_cameras(list(cameras))
         self.n_cams = len(cameras)
@@ -53,7 +54,7 @@ class TopKRenderer:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.check_overflow = check_overflow
         self.cfg = A.GsConfig(self.K, self.D, self.tile[0], self.tile[1], self.dtype, int(max_instances),
-                              int(max_feature_rows))
+                              int(max_feature_rows), int(topk_layout))
         self.P = int(self.lib.gs_pixel_count(self.cams, self.n_cams))
         if self.P < 0:
             raise ValueError("bad cameras")

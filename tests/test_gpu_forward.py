@@ -21,12 +21,18 @@ def test_small_full_frame_parity():
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (32, 8), (16, 8), (8, 8)])
-def test_tile_shape_independence(tile):
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("K", [4, 16])
+def test_tile_shape_and_kbuf_layout_independence(tile, layout, K):
     """The contributor set is defined per pixel, so every tile shape gives bit-identical
-    outputs (and all match the oracle)."""
-    sc, cams, K, _, _ = S.make_config("small", 1)
-    _, _, ref = U.gpu_forward(sc, cams, K, (16, 16))
-    _, _, out = U.gpu_forward(sc, cams, K, tile)
+    outputs, and so does either K-buffer layout of the walk (registers or shared memory);
+    all match the oracle."""
+    from paper_2602_06991_b300.renderer import TopKRenderer
+    sc, cams, _, _, _ = S.make_config("small", 1)
+    _, ts, ref = U.gpu_forward(sc, cams, K, (16, 16))
+    r = TopKRenderer(cams, K=K, D=sc.d, tile=tile, topk_layout=layout)
+    out = r.forward(*ts)
+    torch.cuda.synchronize()
     for k in ("rgb", "depth", "T", "n_contrib", "topk_idx", "topk_w", "F"):
         assert torch.equal(ref[k], out[k]), k
     U.compare_forward(U.to_np(out), U.oracle_forward(sc, cams, K), K)

@@ -42,13 +42,15 @@ def test_mapping_sampled_forward_and_backward():
     # the oracle reads the bf16 rows exactly, as float64 (converted once)
     feats64 = ts[4].float().cpu().numpy().astype(np.float64)
     rng = np.random.default_rng(12)
-    pix = [np.sort(rng.choice(c.n_pix, 12, replace=False)) for c in cams]
+    pix = [np.sort(rng.choice(c.n_pix, 16, replace=False)) for c in cams]
     o = U.oracle_forward(sc, cams, K, pixels_per_cam=pix, feats=feats64)
     idx = torch.from_numpy(o["gidx"]).cuda()
     g = {k: out[k].index_select(0, idx).float().cpu().numpy() for k in ("n_contrib", "topk_idx", "T", "F")}
     fragile = (o["flags"] & U.FRAGILE_SET) != 0
     ok = ~fragile
-    assert fragile.sum() <= max(2, 0.02 * ok.size), int(fragile.sum())
+    # a pixel here tests far more candidates near their thresholds than in the smaller
+    # scenes, so more pixels carry a decision within the 2e-5 margins (counted, bounded)
+    assert fragile.sum() <= max(4, 0.06 * ok.size), int(fragile.sum())
     assert np.array_equal(g["n_contrib"][ok].astype(np.int64), o["n"][ok])
     sets_ok = ok & ((o["flags"] & oracle.F_NEAR_TIE) == 0)
     assert np.array_equal(np.sort(g["topk_idx"][sets_ok].astype(np.int64), axis=1), np.sort(o["idx"][sets_ok], axis=1))
