@@ -163,6 +163,7 @@ def run_bf16_batched(args, hbm):
     scene = S.make_config("batched", 0)
     sc, cams, K0, tile0, fdt = scene
     sweep = []
+    main_launches = None
     for K in (4, 8, 16):
         # K is the model's parameter (it changes the render); the tile shape is tuned per K
         scene_k = (sc, cams, K, tile0, fdt)
@@ -176,11 +177,17 @@ def run_bf16_batched(args, hbm):
                       "value": round(step.P / (ms * 1e-3) / 1e6, 3), "autotune_ms": tuned["ms"], "status": st})
         if K == K0:
             main_roof = stage_rooflines(step, hbm)
+            main_launches = None if args.no_launch_count else count_launches(step)
         P, N, D = step.P, step.N, step.D
         del step
         torch.cuda.empty_cache()
     main = next(r for r in sweep if r["K"] == K0)
+    launches = main_launches if main_launches else 70
+    node_ms = graph_node_cost(launches)
     out = {"value": main["value"], "unit": UNIT, "ms_per_step": main["ms_per_step"], "pixels_per_step": P,
+           "graph": {"launches_per_step": launches, "graph_of_as_many_empty_nodes_ms": round(node_ms, 4),
+                     "share_of_step": round(node_ms / main["ms_per_step"], 4),
+                     "note": "bound on what one persistent launch of the same stages could save over the graph"},
            "gaussians": N, "views": len(cams), "D": D, "K": K0, "dtype": "bf16", "tile": main["tile"],
            "kbuf_layout": main["kbuf_layout"],
            "status": main["status"], "roofline": main_roof["blend_loss"], "backward_roofline": main_roof["backward"],
@@ -401,7 +408,9 @@ def stage_rooflines(step, hbm, reps=10):
     bl_ms, bw_ms = ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps
     blb = blend_loss_bytes(step.P, step.D, step.K, s, uniq)
     bwb = backward_bytes(step.P, step.D, step.K, s, step.N, step.N * len(step.cams))
-    out = {"blend_loss": {"kernel": "gs_feature_blend_loss (k_blend_loss_group)", "bound": "hbm",
+    kname = ("gs_feature_blend_loss (k_blend_mma: tensor-core, bf16 rows)" if step.fdt == "bf16"
+             else "gs_feature_blend_loss (k_blend_loss_group: pixel groups, float32 rows)")
+    out = {"blend_loss": {"kernel": kname, "bound": "hbm",
                           "achieved": round(blb / (bl_ms * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
                           "frac": round(blb / (bl_ms * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": blb,
                           "unique_rows": uniq, "kernel_ms": round(bl_ms, 4)},
@@ -410,6 +419,34 @@ def stage_rooflines(step, hbm, reps=10):
                         "frac": round(bwb / (bw_ms * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": bwb,
                         "stage_ms": round(bw_ms, 4)}}
     return out
+
+
+def graph_node_cost(n_nodes, reps=50):
+    """Milliseconds that a CUDA graph of n_nodes trivial kernels takes per replay: the
+    launch cost a step of that many graph nodes pays beyond its kernels' work, i.e. the
+    most a single persistent launch of the same stages could save."""
+    import torch
+    x = torch.zeros(1, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        x.add_(1)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        for _ in range(n_nodes):
+            x.add_(1)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
 
 def status_of(step):

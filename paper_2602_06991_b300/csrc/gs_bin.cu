@@ -3,8 +3,10 @@
 // Order of work (chosen so the sort over the large instance set needs only the tile
 // bits):
 //   1. sort the (camera, Gaussian) elements by float32 depth (32-bit keys, N-sized);
-//   2. count the tiles each element's footprint box overlaps, in depth order, and scan;
-//   3. emit one instance per (element, tile), in depth order, keyed by global tile id;
+//   2. count the tiles of each element's footprint box that its ellipse reaches (one run
+//      of tiles per tile row, from the ellipse's x-range over the row), in depth order,
+//      and scan;
+//   3. emit one instance per such (element, tile), in depth order, keyed by global tile id;
 //   4. stable radix sort of the instances by tile id -> within a tile, depth order
 //      (ties keep element order, i.e. ascending Gaussian id within a camera);
 //   5. per-tile [start, end) ranges (a search per tile over the sorted keys).
@@ -37,23 +39,98 @@ __device__ __forceinline__ uint32_t tiles_of(const CamTable &ct, const float4 *p
     return (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
 }
 
-__global__ void k_count_tiles(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
-                              const uint32_t *__restrict__ sorted_e, uint32_t *counts, uint32_t *elem_cnt)
+// The tiles of a footprint box that the Gaussian's opacity-cut ellipse q(dx, dy) <= qb
+// reaches (qb and q as in the walks' touches_rect), one row of tiles at a time.  With
+// q = (s1 dx)^2 + (s2 (dy - m dx))^2 and A = s1^2 + s2^2 m^2, the ellipse's section at
+// offset dy spans
+//     dx = (s2^2 m dy -/+ sqrt(A qb - (s1 s2 dy)^2)) / A,   |dy| <= sqrt(A qb) / (s1 s2);
+// its right end is largest at dy = m sqrt(qb) / s1 and its left end smallest at the
+// opposite offset.  So over the band of a tile row's pixel centres the ellipse covers one
+// x-interval -- its ends are those two offsets clamped into the band -- and the tiles
+// whose pixel-centre columns meet it form one run.  A tile outside the run has no pixel
+// centre with q <= qb, so no walk would accept the Gaussian there.  Only correctly
+// rounded single operations are used (never contracted into FMAs), so the counting and
+// the emitting kernels derive identical runs.
+struct RowCull {
+    float u, v, s2m, A, s12, qb, dymax, dys;
+    bool ok;
+    __device__ __forceinline__ RowCull(const float4 r0, const float4 r1)
+    {
+        u = __fadd_rn(r0.x, r0.z);
+        v = __fadd_rn(r0.y, r0.w);
+        const float s1 = r1.x, m = r1.y, s2 = r1.z;
+        // 2 ln(255 o) through the hardware log2 (one instruction, the same result in both
+        // kernels; its error is far inside the 0.4% + 0.02 margin)
+        const float q = fminf(kQMax, __fmul_rn(1.38629436f, __log2f(__fmul_rn(255.0f, r1.w))));
+        qb = __fadd_rn(__fmul_rn(fmaxf(q, 0.0f), 1.004f), 0.02f);
+        ok = s1 > 0.f && s2 > 0.f && isfinite(m) && isfinite(s1) && isfinite(s2);
+        const float s22 = __fmul_rn(s2, s2), s1s2 = __fmul_rn(s1, s2);
+        s2m = __fmul_rn(s22, m);
+        A = __fadd_rn(__fmul_rn(s1, s1), __fmul_rn(s2m, m));
+        s12 = __fmul_rn(s1s2, s1s2);
+        dymax = ok ? __fdiv_rn(__fsqrt_rn(__fmul_rn(A, qb)), s1s2) : 0.f;
+        dys = ok ? __fdiv_rn(__fmul_rn(m, __fsqrt_rn(qb)), s1) : 0.f;
+    }
+    __device__ __forceinline__ float root(float dy) const
+    {
+        return __fsqrt_rn(fmaxf(__fsub_rn(__fmul_rn(A, qb), __fmul_rn(s12, __fmul_rn(dy, dy))), 0.f));
+    }
+    // The run [a, b] of tile columns (within [tx0, tx1]) that the ellipse reaches in tile
+    // row ty; false for none.
+    __device__ __forceinline__ bool run(const CamDev &cam, int tw, int th, int ty, int tx0, int tx1, int &a,
+                                        int &b) const
+    {
+        if (!ok) {
+            a = tx0;
+            b = tx1;
+            return true;
+        }
+        const float lo = fmaxf(__fsub_rn((float)(ty * th) + 0.5f, v), -dymax);
+        const float hi = fminf(__fsub_rn((float)min((ty + 1) * th, cam.H) - 0.5f, v), dymax);
+        if (!(lo <= hi)) return false;
+        const float yr = fminf(fmaxf(dys, lo), hi), yl = fminf(fmaxf(-dys, lo), hi);
+        const float xmax = __fdiv_rn(__fadd_rn(__fmul_rn(s2m, yr), root(yr)), A);
+        const float xmin = __fdiv_rn(__fsub_rn(__fmul_rn(s2m, yl), root(yl)), A);
+        // columns tx with pixel centres [tx tw + 0.5, (tx + 1) tw - 0.5] meeting
+        // [u + xmin, u + xmax], widened by 0.01 px
+        const float X0 = __fsub_rn(__fadd_rn(u, xmin), 0.01f), X1 = __fadd_rn(__fadd_rn(u, xmax), 0.01f);
+        const float af = __fsub_rn(ceilf(__fdiv_rn(__fadd_rn(X0, 0.5f), (float)tw)), 1.0f);
+        const float bf = floorf(__fdiv_rn(__fsub_rn(X1, 0.5f), (float)tw));
+        a = (int)fminf(fmaxf(af, (float)tx0), (float)(tx1 + 1));
+        b = (int)fmaxf(fminf(bf, (float)tx1), (float)(tx0 - 1));
+        return a <= b;
+    }
+};
+
+// Instances of each element, in depth order: the tiles of its footprint box that its
+// ellipse reaches (RowCull runs), counted by depth rank.
+__global__ void __launch_bounds__(256) k_count_tiles(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
+                                                     const uint32_t *__restrict__ sorted_e, uint32_t *counts,
+                                                     uint32_t *elem_cnt)
 {
-    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= NE) return;
-    uint32_t e = sorted_e[r];
-    int c, a, b, d, f;
-    uint32_t n = tiles_of(ct, proj, e, N, c, a, b, d, f);
+    const uint32_t e = sorted_e[r];
+    int c, tx0, tx1, ty0, ty1;
+    const uint32_t box = tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1);
+    uint32_t n = 0;
+    if (box > 0) {
+        const RowCull rc(proj[4 * (size_t)e], proj[4 * (size_t)e + 1]);
+        const CamDev &cam = ct.c[c];
+        for (int ty = ty0; ty <= ty1; ++ty) {
+            int a, b;
+            if (rc.run(cam, ct.tile_w, ct.tile_h, ty, tx0, tx1, a, b)) n += (uint32_t)(b - a + 1);
+        }
+    }
     counts[r] = n;
     elem_cnt[e] = n;
 }
 
-// One warp per 32 consecutive depth ranks: each lane works out its element's tile
-// rectangle, then the warp writes the instances element by element, lanes striding over
-// the rectangle, so large footprints are written in parallel and coalesced.
-// (An instance's sort value is its own index, which the tile sort generates; the
-// re-walk's walked flags are cleared by k_clear_walked.)
+// Writes the instances counted by k_count_tiles: one warp per 32 consecutive depth ranks,
+// element by element, one lane per tile row (its run, placed by a warp prefix over the
+// rows), so the writes of an element are consecutive.  (An instance's sort value is its
+// own index, which the tile sort generates; the re-walk's walked flags are cleared by
+// k_clear_walked.)
 __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
                                                    const uint32_t *__restrict__ sorted_e,
                                                    const uint32_t *__restrict__ offsets, uint32_t mcap,
@@ -68,7 +145,8 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
         e = sorted_e[r];
         o = offsets[r];
         elem_off[e] = o;
-        n = tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1);
+        n = elem_cnt[e];                          // the instances counted by k_count_tiles
+        if (n > 0) tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1);
         if (n > 0 && (unsigned long long)o + n > mcap) {
             // instances past the capacity are dropped; the render is reported as failed
             atomicOr(err, kErrOverflow);
@@ -81,15 +159,30 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
         const uint32_t ej = __shfl_sync(0xffffffffu, e, j), oj = __shfl_sync(0xffffffffu, o, j);
         const int cj = __shfl_sync(0xffffffffu, c, j);
         const int x0 = __shfl_sync(0xffffffffu, tx0, j), x1 = __shfl_sync(0xffffffffu, tx1, j);
-        const int y0 = __shfl_sync(0xffffffffu, ty0, j);
-        const int w = x1 - x0 + 1;
+        const int y0 = __shfl_sync(0xffffffffu, ty0, j), y1 = __shfl_sync(0xffffffffu, ty1, j);
         const CamDev &cam = ct.c[cj];
-        for (uint32_t t = lane; t < nj; t += 32) {
-            uint32_t oo = oj + t;
-            if (oo >= mcap) break;
-            int ty = y0 + (int)(t / (uint32_t)w), tx = x0 + (int)(t % (uint32_t)w);
-            inst_keys[oo] = (uint32_t)(cam.tile_off + ty * cam.tiles_x + tx);
-            inst_elem[oo] = ej;
+        const RowCull rc(proj[4 * (size_t)ej], proj[4 * (size_t)ej + 1]);
+        uint32_t base = oj;
+        for (int ry = y0; ry <= y1; ry += 32) {
+            const int ty = ry + lane;
+            int a = 0, b = -1;
+            const bool any = ty <= y1 && rc.run(cam, ct.tile_w, ct.tile_h, ty, x0, x1, a, b);
+            const uint32_t cnt = any ? (uint32_t)(b - a + 1) : 0u;
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            const uint32_t at = base + incl - cnt;
+            const uint32_t key0 = (uint32_t)(cam.tile_off + ty * cam.tiles_x + a);
+            for (uint32_t k = 0; k < cnt; ++k) {
+                if (at + k < mcap) {
+                    inst_keys[at + k] = key0 + k;
+                    inst_elem[at + k] = ej;
+                }
+            }
+            base += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
 }
@@ -179,8 +272,8 @@ void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *
     int dcur = radix_sort_pairs(dk[0], dk[1], dv[0], dv[1], NE, nullptr, 32, hist, s);
     k_count_tiles<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], counts, elem_cnt);
     exclusive_scan_u32(counts, counts, NE, n_inst, aux, s);
-    k_duplicate<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], counts, (uint32_t)L.Mcap, ik[0], inst_elem, elem_off,
-                                  elem_cnt, err);
+    k_duplicate<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], counts, (uint32_t)L.Mcap, ik[0], inst_elem,
+                                  elem_off, elem_cnt, err);
     k_clear_walked<<<148 * 8, 256, 0, s>>>(n_inst, (uint32_t)L.Mcap, ws_ptr<uint8_t>(ws, L.inst_walked));
     int icur = radix_sort_pairs(ik[0], ik[1], iv[0], iv[1], L.Mcap, n_inst, bits_for(L.n_tiles), hist, s, true);
     (void)icur;   // equals L.inst_sorted

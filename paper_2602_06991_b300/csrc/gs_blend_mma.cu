@@ -26,6 +26,9 @@
 // pixels, whose K rows always fit); the blend-only and the training kernels split alike,
 // so their F are bit-identical.
 #include "gs_internal.cuh"
+#include "gs_mma.cuh"
+
+#include <algorithm>
 
 namespace gs {
 
@@ -35,70 +38,24 @@ constexpr int kMmaCols = 64;                    // columns per staged chunk
 constexpr int kMmaPitch = kMmaCols * 2 + 16;    // bytes per staged row: conflict-free ldmatrix
 constexpr int kMmaWarps = 4;                    // warps per CTA
 
+// Per warp.  The tables of a (sub)group (dense W, w' per slot, then h) are used only
+// before and after its chunk loop, the pixel chunk buffers only inside it, so they share
+// memory: 14.2 KB per warp, four 4-warp CTAs per SM.
 struct MmaWarpSmem {
     unsigned char rows[2][kMmaRows * kMmaPitch];    // staged row chunks (double buffer)
-    float wt[kMmaPix][kMmaRows];                    // dense W, then h by (pixel, rank)
-    float wslot[kMmaPix * 16];                      // w' per slot
+    union {
+        unsigned char pix[2][kMmaPix * kMmaPitch];  // the 16 pixels' chunk: target rows in, F / dL/dF out
+        struct {
+            float wt[kMmaPix][kMmaRows];            // dense W, then h by (pixel, rank)
+            float wslot[kMmaPix * 16];              // w' per slot
+        };
+    };
     int ids[kMmaRows];                              // distinct ids, ascending
     unsigned char rank[kMmaPix * 16];               // rank of each slot's id (0xff: none)
 };
+static_assert(sizeof(MmaWarpSmem) * kMmaWarps * 4 <= 227 * 1024, "four CTAs per SM");
 
 size_t blend_mma_smem() { return sizeof(MmaWarpSmem) * kMmaWarps; }
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async_16(uint32_t dst, const void *src, int bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ void ldsm_x4(uint32_t a, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(a));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t a, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(a));
-}
-// d += A (16x16, row) B (16x8, col), bf16 in, float32 accumulate
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-                 "{%8, %9}, {%0, %1, %2, %3};\n"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
-{
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *(const uint32_t *)&v;
-}
-__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
-__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xffff0000u); }
-
-// w = hi + mid + lo exactly, each term bf16 (three 8-bit significands cover float32's 24)
-__device__ __forceinline__ void split3(float w, float &h, float &m, float &l)
-{
-    h = __bfloat162float(__float2bfloat16_rn(w));
-    const float r1 = w - h;
-    m = __bfloat162float(__float2bfloat16_rn(r1));
-    l = r1 - m;                                   // exactly representable in bf16
-}
-
-// Everything one (sub)group of pixels needs from the Top-K record.
-template <int K>
-struct MmaGroup {
-    static constexpr int SPL = K / 2;             // slots per lane: lane l holds pixel l / 2
-    int U;                                        // distinct rows
-};
 
 // Loads the K slots of the pixels [lo, hi) of the warp's 16 (the others count as empty),
 // forms w' in slot order, sorts the (id, slot) keys, and fills ids, rank and the dense W.
@@ -231,6 +188,59 @@ __device__ __forceinline__ void mma_stage(const __nv_bfloat16 *__restrict__ feat
     cp_async_commit_group();
 }
 
+// Stages columns [c0, c0 + 64) of the 16 pixels' target rows into pix[buf] (four 16-byte
+// copies per lane, whole 128-byte lines); pixels past n_pix are zero-filled.  Joins the
+// copy group of the next mma_stage call.
+__device__ __forceinline__ void mma_stage_pix(const __nv_bfloat16 *__restrict__ src_rows, long long p0, long long n_pix,
+                                              int D, int c0, int lane, MmaWarpSmem &sm, int buf)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = 4 * i + (lane >> 3), q = lane & 7;
+        const bool real = p0 + r < n_pix;
+        const __nv_bfloat16 *src = src_rows + (real ? (size_t)(p0 + r) * D + c0 + 8 * q : 0);
+        cp_async_16(smem_addr(sm.pix[buf] + r * kMmaPitch + 16 * q), src, real ? 16 : 0);
+    }
+}
+
+// The accumulator-layout values of the chunk's 16 pixel rows from pix[buf]: v[j][0] the
+// lane's pair of row g, v[j][1] of row g + 8, n-tile j (ldmatrix: four 8 x 8 blocks per
+// 16 columns).
+__device__ __forceinline__ void mma_pix_load(const MmaWarpSmem &sm, int buf, int lane, uint32_t (&v)[8][2])
+{
+    const uint32_t base = smem_addr(sm.pix[buf]);
+    const int mi = lane >> 3, mr = lane & 7;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int r = mr + 8 * (mi & 1), c = 16 * m + 8 * (mi >> 1);
+        ldsm_x4(base + r * kMmaPitch + 2 * c, v[2 * m][0], v[2 * m][1], v[2 * m + 1][0], v[2 * m + 1][1]);
+    }
+}
+
+// Writes the accumulator-layout pairs v of the chunk to pix[buf] (stmatrix), then the
+// rows [lo, hi) of the 16 pixels to dst with whole-line 16-byte stores.
+__device__ __forceinline__ void mma_pix_store(const uint32_t (&v)[8][2], MmaWarpSmem &sm, int buf, int lane,
+                                              __nv_bfloat16 *__restrict__ dst, long long p0, long long n_pix, int lo,
+                                              int hi, int D, int c0)
+{
+    const uint32_t base = smem_addr(sm.pix[buf]);
+    const int mi = lane >> 3, mr = lane & 7;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int r = mr + 8 * (mi & 1), c = 16 * m + 8 * (mi >> 1);
+        stsm_x4(base + r * kMmaPitch + 2 * c, v[2 * m][0], v[2 * m][1], v[2 * m + 1][0], v[2 * m + 1][1]);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = 4 * i + (lane >> 3), q = lane & 7;
+        if (r >= lo && r < hi && p0 + r < n_pix) {
+            const uint4 x = *(const uint4 *)(sm.pix[buf] + r * kMmaPitch + 16 * q);
+            *(uint4 *)(dst + (size_t)(p0 + r) * D + c0 + 8 * q) = x;
+        }
+    }
+}
+
 // acc (8 n-tiles of 8 columns) = W R for one staged 64-column chunk
 template <int KS>
 __device__ __forceinline__ void mma_blend_chunk(const uint32_t (&afr)[2][3][4], const MmaWarpSmem &sm, int buf,
@@ -308,9 +318,7 @@ __device__ __forceinline__ void mma_group(long long p0, long long n_pix, int lo,
     const int nrows = 16 * KS;
     uint32_t afr[2][3][4];
     mma_weight_frags(sm, KS, lane, afr);
-    // the two pixel rows this lane holds in the accumulator layout
-    const long long pa = p0 + g, pb = p0 + g + 8;
-    const bool va = g >= lo && g < hi && pa < n_pix, vb = g + 8 >= lo && g + 8 < hi && pb < n_pix;
+    __syncwarp();                                 // W is read: the pixel buffers it shares memory with are free
     const int nchunk = D / kMmaCols;
     const int steps = LOSS ? 2 * nchunk : nchunk;
     float ffa = 0.f, fga = 0.f, gga = 0.f, ffb = 0.f, fgb = 0.f, ggb = 0.f;
@@ -321,6 +329,7 @@ __device__ __forceinline__ void mma_group(long long p0, long long n_pix, int lo,
 #pragma unroll
         for (int v = 0; v < 4; ++v) hacc[n][v] = 0.f;
 
+    if (LOSS) mma_stage_pix(Fgt, p0, n_pix, D, 0, lane, sm, 0);
     mma_stage(feats, D, 0, nrows, U, lane, sm, 0);
     for (int step = 0; step < steps; ++step) {
         const int buf = step & 1;
@@ -348,33 +357,32 @@ __device__ __forceinline__ void mma_group(long long p0, long long n_pix, int lo,
             coef(ffb, fgb, ggb, cab, cbb, cosb);
         }
         if (step + 1 < steps) {
-            mma_stage(feats, D, ((step + 1) % nchunk) * kMmaCols, nrows, U, lane, sm, buf ^ 1);
+            const int cn = ((step + 1) % nchunk) * kMmaCols;
+            if (LOSS) mma_stage_pix(Fgt, p0, n_pix, D, cn, lane, sm, buf ^ 1);
+            mma_stage(feats, D, cn, nrows, U, lane, sm, buf ^ 1);
             cp_async_wait_group<1>();
         } else {
             cp_async_wait_group<0>();
         }
         __syncwarp();
-        const int col0 = ch * kMmaCols + 2 * t;
-        // target rows of this chunk (the loss reads them in both passes)
+        const int c0 = ch * kMmaCols;
+        // the chunk's target values (the loss reads them in both passes)
         uint32_t gt[8][2];
-        if (LOSS) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                gt[j][0] = va ? __ldg((const uint32_t *)(Fgt + (size_t)pa * D + col0 + 8 * j)) : 0u;
-                gt[j][1] = vb ? __ldg((const uint32_t *)(Fgt + (size_t)pb * D + col0 + 8 * j)) : 0u;
-            }
-        }
+        if (LOSS) mma_pix_load(sm, buf, lane, gt);
         float acc[8][4];
         if (KS == 1) mma_blend_chunk<1>(afr, sm, buf, lane, acc);
         else mma_blend_chunk<2>(afr, sm, buf, lane, acc);
-        if (!pass2) {
+        uint32_t fo[8][2];                        // F as stored (bf16 pairs)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t fa = pack_bf16(acc[j][0], acc[j][1]), fb = pack_bf16(acc[j][2], acc[j][3]);
-                if (va) *(uint32_t *)(F + (size_t)pa * D + col0 + 8 * j) = fa;
-                if (vb) *(uint32_t *)(F + (size_t)pb * D + col0 + 8 * j) = fb;
-                if (LOSS) {             // the loss sees F as stored
-                    const float a0 = bf_lo(fa), a1 = bf_hi(fa), b0 = bf_lo(fb), b1 = bf_hi(fb);
+        for (int j = 0; j < 8; ++j) {
+            fo[j][0] = pack_bf16(acc[j][0], acc[j][1]);
+            fo[j][1] = pack_bf16(acc[j][2], acc[j][3]);
+        }
+        if (!pass2) {
+            if (LOSS) {                           // the loss sees F as stored
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float a0 = bf_lo(fo[j][0]), a1 = bf_hi(fo[j][0]), b0 = bf_lo(fo[j][1]), b1 = bf_hi(fo[j][1]);
                     const float g0 = bf_lo(gt[j][0]), g1 = bf_hi(gt[j][0]), g2 = bf_lo(gt[j][1]), g3 = bf_hi(gt[j][1]);
                     ffa = fmaf(a0, a0, fmaf(a1, a1, ffa));
                     fga = fmaf(a0, g0, fmaf(a1, g1, fga));
@@ -383,22 +391,21 @@ __device__ __forceinline__ void mma_group(long long p0, long long n_pix, int lo,
                     fgb = fmaf(b0, g2, fmaf(b1, g3, fgb));
                     ggb = fmaf(g2, g2, fmaf(g3, g3, ggb));
                 }
+                __syncwarp();                     // every lane has read the target values
             }
+            mma_pix_store(fo, sm, buf, lane, F, p0, n_pix, lo, hi, D, c0);
         } else {
             // dL/dF = a Fgt + b F (F as stored), written in bf16; as stored it is the A
             // operand of h = dL/dF R^T (k-step m covers n-tiles 2m, 2m + 1)
             uint32_t dfr[8][2];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const uint32_t fa = pack_bf16(acc[j][0], acc[j][1]), fb = pack_bf16(acc[j][2], acc[j][3]);
-                const float d0 = fmaf(caa, bf_lo(gt[j][0]), cba * bf_lo(fa));
-                const float d1 = fmaf(caa, bf_hi(gt[j][0]), cba * bf_hi(fa));
-                const float d2 = fmaf(cab, bf_lo(gt[j][1]), cbb * bf_lo(fb));
-                const float d3 = fmaf(cab, bf_hi(gt[j][1]), cbb * bf_hi(fb));
+                const float d0 = fmaf(caa, bf_lo(gt[j][0]), cba * bf_lo(fo[j][0]));
+                const float d1 = fmaf(caa, bf_hi(gt[j][0]), cba * bf_hi(fo[j][0]));
+                const float d2 = fmaf(cab, bf_lo(gt[j][1]), cbb * bf_lo(fo[j][1]));
+                const float d3 = fmaf(cab, bf_hi(gt[j][1]), cbb * bf_hi(fo[j][1]));
                 dfr[j][0] = pack_bf16(d0, d1);
                 dfr[j][1] = pack_bf16(d2, d3);
-                if (va) *(uint32_t *)(dLdF + (size_t)pa * D + col0 + 8 * j) = dfr[j][0];
-                if (vb) *(uint32_t *)(dLdF + (size_t)pb * D + col0 + 8 * j) = dfr[j][1];
             }
             const uint32_t base = smem_addr(sm.rows[buf]);
             const int mi = lane >> 3, mr = lane & 7;
@@ -416,8 +423,10 @@ __device__ __forceinline__ void mma_group(long long p0, long long n_pix, int lo,
                     mma16816(hacc[2 * nb + 1], a, b2, b3);
                 }
             }
+            __syncwarp();                         // every lane has read the target values
+            mma_pix_store(dfr, sm, buf, lane, dLdF, p0, n_pix, lo, hi, D, c0);
         }
-        __syncwarp();                             // the buffer is free for the next stage
+        __syncwarp();                             // both buffers of the step are free again
     }
     if constexpr (LOSS) mma_group_tail<K>(p0, n_pix, lo, hi, KS, hacc, cosa, cosb, C, Cgt, Dp, Dgt, wf, wc, wd, invP,
                                            dLdC, dLdD, part, h, lane, sm);
@@ -480,7 +489,7 @@ __device__ __forceinline__ void mma_group_tail(long long p0, long long n_pix, in
 }
 
 template <int K, bool LOSS>
-__global__ void __launch_bounds__(kMmaWarps * 32) k_blend_mma(long long n_pix, int D, const int *__restrict__ idx,
+__global__ void __launch_bounds__(kMmaWarps * 32, 4) k_blend_mma(long long n_pix, int D, const int *__restrict__ idx,
                                                               const float *__restrict__ wts,
                                                               const __nv_bfloat16 *__restrict__ feats,
                                                               const __nv_bfloat16 *__restrict__ Fgt,
@@ -526,7 +535,7 @@ __global__ void __launch_bounds__(kMmaWarps * 32) k_blend_mma(long long n_pix, i
 // same A values (dL/dF as stored), B fragments and MMA sequence over the columns for
 // every (pixel, row) element -- so the two give bit-identical h.
 template <int K>
-__global__ void __launch_bounds__(kMmaWarps * 32) k_h_mma(long long n_pix, int D, const int *__restrict__ idx,
+__global__ void __launch_bounds__(kMmaWarps * 32, 4) k_h_mma(long long n_pix, int D, const int *__restrict__ idx,
                                                           const __nv_bfloat16 *__restrict__ feats,
                                                           const __nv_bfloat16 *__restrict__ dLdF,
                                                           float *__restrict__ h, const int *__restrict__ err)
@@ -539,8 +548,6 @@ __global__ void __launch_bounds__(kMmaWarps * 32) k_h_mma(long long n_pix, int D
     const long long p0 = ((long long)blockIdx.x * kMmaWarps + wib) * kMmaPix;
     if (p0 >= n_pix) return;                          // whole warp
     const bool bad = err && *err != 0;
-    const long long pa = p0 + g, pb = p0 + g + 8;
-    const bool va = pa < n_pix, vb = pb < n_pix;
     const int nchunk = D / kMmaCols;
     int lo = 0, span = kMmaPix;
     while (lo < kMmaPix) {
@@ -556,10 +563,12 @@ __global__ void __launch_bounds__(kMmaWarps * 32) k_h_mma(long long n_pix, int D
         for (int n = 0; n < 4; ++n)
 #pragma unroll
             for (int v = 0; v < 4; ++v) hacc[n][v] = 0.f;
+        mma_stage_pix(dLdF, p0, n_pix, D, 0, lane, sm, 0);
         mma_stage(feats, D, 0, 16 * KS, U, lane, sm, 0);
         for (int ch = 0; ch < nchunk; ++ch) {
             const int buf = ch & 1;
             if (ch + 1 < nchunk) {
+                mma_stage_pix(dLdF, p0, n_pix, D, (ch + 1) * kMmaCols, lane, sm, buf ^ 1);
                 mma_stage(feats, D, (ch + 1) * kMmaCols, 16 * KS, U, lane, sm, buf ^ 1);
                 cp_async_wait_group<1>();
             } else {
@@ -568,13 +577,11 @@ __global__ void __launch_bounds__(kMmaWarps * 32) k_h_mma(long long n_pix, int D
             __syncwarp();
             const uint32_t base = smem_addr(sm.rows[buf]);
             const int mi = lane >> 3, mr = lane & 7;
+            uint32_t dv[8][2];                    // dL/dF of the chunk in the A-operand layout
+            mma_pix_load(sm, buf, lane, dv);
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-                const int c = ch * kMmaCols + 16 * m + 2 * t;
-                const uint32_t a[4] = {va ? __ldg((const uint32_t *)(dLdF + (size_t)pa * D + c)) : 0u,
-                                       vb ? __ldg((const uint32_t *)(dLdF + (size_t)pb * D + c)) : 0u,
-                                       va ? __ldg((const uint32_t *)(dLdF + (size_t)pa * D + c + 8)) : 0u,
-                                       vb ? __ldg((const uint32_t *)(dLdF + (size_t)pb * D + c + 8)) : 0u};
+                const uint32_t a[4] = {dv[2 * m][0], dv[2 * m][1], dv[2 * m + 1][0], dv[2 * m + 1][1]};
 #pragma unroll
                 for (int nb = 0; nb < 2; ++nb) {
                     if (nb >= KS) break;

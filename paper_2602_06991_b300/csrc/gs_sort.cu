@@ -3,7 +3,7 @@
 // Radix sort: least-significant-digit, 8-bit digits, reduce-then-scan per pass:
 //   upsweep   : each block counts the digits of its contiguous range of tiles;
 //   scan      : one block turns the (digit-major, block-minor) counts into offsets;
-//   downsweep : each block ranks its keys stably (warp match + per-warp counters),
+//   downsweep : each block ranks its keys stably (warp ballots + per-warp counters),
 //               reorders each tile by digit in shared memory and writes every digit's
 //               run to consecutive final positions.
 // No block waits on another, so nothing can spin.  Stability makes the multi-pass
@@ -134,8 +134,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Downsweep of a pass: per tile of kSortTile keys, stable ranks (warp match +
-// per-warp digit counters), then the tile is reordered by digit in shared memory and
+// Downsweep of a pass: per tile of kSortTile keys, stable ranks (the warp's lanes of equal
+// digit found by nine ballots -- validity and the 8 digit bits -- and per-warp digit
+// counters), then the tile is reordered by digit in shared memory and
 // written out in that order, so each digit's run of the tile goes to consecutive
 // addresses (coalesced) instead of one scattered store per key.  The next tile's keys
 // and values are copied into shared memory (cp.async) while the current one is ranked
@@ -213,7 +214,16 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_downsweep(const uint32_t *_
         }
 #pragma unroll
         for (int i = 0; i < kSortItems; ++i) {
-            uint32_t peers = __match_any_sync(0xffffffffu, dg[i]);
+            // lanes holding the same digit: the validity and the 8 digit bits, one ballot each
+            const bool valid = dg[i] < 256;
+            const uint32_t vm = __ballot_sync(0xffffffffu, valid);
+            uint32_t peers = valid ? vm : ~vm;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const bool bit = (dg[i] >> b) & 1;
+                const uint32_t bm = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bm : ~bm;
+            }
             int leader = __ffs(peers) - 1;
             uint32_t before = s_wcnt[warp][dg[i]];
             __syncwarp();

@@ -24,7 +24,10 @@
 //   128-column chunk) read from shared memory, then writes the run's partial row.
 // Stage T4: the partial rows are reduced per Gaussian by the sort-by-Gaussian segmented
 //   reduction of gs_featgrad.cu in row mode.
+// For bf16 dL/dF (D a multiple of 64, blocks of 16 or 32 pixels) T3 is k_block_mma, the
+// same partial rows as a tensor-core product per block.
 #include "gs_internal.cuh"
+#include "gs_mma.cuh"
 
 #include <cuda.h>
 #include <mutex>
@@ -594,6 +597,199 @@ __global__ void __launch_bounds__(kBlkNT + 32, 1) k_block_accum(const __grid_con
 }
 
 // ------------------------------------------------------------------------------------
+// T3 for bf16 dL/dF on the tensor cores.  A block's partial rows are a small dense
+// product: P[U_b x D] = W^T[U_b x B] dL/dF[B x D], W^T[u][p] = w' of pixel p's slot that
+// selected run u's Gaussian (0 elsewhere; at K = 8 most entries are filled).  One warp
+// per block: W^T built from the sorted slot records, its float32 weights split exactly
+// into three bf16 terms (A fragments, 16 runs x 16 pixels per MMA tile); the block's
+// dL/dF rows staged 64 columns at a time by cp.async into padded shared memory
+// (double-buffered, one pixel row per lane) and read with ldmatrix.trans; mma.m16n8k16
+// with float32 accumulation; runs in batches of 32.  Each partial row is a fixed
+// sequence of MMAs, so the result is deterministic.
+// ------------------------------------------------------------------------------------
+constexpr int kBmRuns = 32;                      // runs per batch (two 16-row MMA tiles)
+constexpr int kBmCols = 64;                      // columns per staged chunk
+constexpr int kBmPitch = kBmCols * 2 + 16;       // bytes per staged row: conflict-free ldmatrix
+constexpr int kBmWarps = 4;
+
+template <int B>
+struct BlockMmaSmem {
+    unsigned char rows[2][B * kBmPitch];         // the block's dL/dF rows, one chunk (double buffer)
+    float wt[kBmRuns][B];                        // W^T of a batch of runs
+};
+
+template <int TW, int TH>
+__device__ __forceinline__ void block_mma_one(const CamTable &cb, int K, int D, const __nv_bfloat16 *__restrict__ dLdF,
+                                              const uint2 *__restrict__ rec, const uint2 *__restrict__ runs,
+                                              const uint32_t *__restrict__ row_base,
+                                              const uint32_t *__restrict__ tile_u, uint32_t rows_cap,
+                                              float *__restrict__ rows, uint32_t *__restrict__ pair_keys,
+                                              uint32_t *__restrict__ pair_vals, int N, int *err, int blk, int lane,
+                                              BlockMmaSmem<TW * TH> &sm);
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(kBmWarps * 32, 3) k_block_mma(CamTable cb, int K, int D, const __nv_bfloat16 *__restrict__ dLdF,
+                                                          const uint2 *__restrict__ rec, const uint2 *__restrict__ runs,
+                                                          const uint32_t *__restrict__ row_base,
+                                                          const uint32_t *__restrict__ tile_u, uint32_t rows_cap,
+                                                          float *__restrict__ rows, uint32_t *__restrict__ pair_keys,
+                                                          uint32_t *__restrict__ pair_vals, int N, int *err)
+{
+    constexpr int B = TW * TH;
+    static_assert(B % 16 == 0 && B <= 32, "pixel blocks of 16 or 32");
+    extern __shared__ __align__(16) unsigned char smem_bm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    BlockMmaSmem<B> &sm = ((BlockMmaSmem<B> *)smem_bm)[wib];
+    if (*err) return;
+    const int blk = blockIdx.x * kBmWarps + wib;
+    if (blk >= cb.n_tiles) return;               // whole warp
+    block_mma_one<TW, TH>(cb, K, D, dLdF, rec, runs, row_base, tile_u, rows_cap, rows, pair_keys, pair_vals, N, err,
+                          blk, lane, sm);
+}
+
+// One feature-gradient block of k_block_mma (a warp).
+template <int TW, int TH>
+__device__ __forceinline__ void block_mma_one(const CamTable &cb, int K, int D, const __nv_bfloat16 *__restrict__ dLdF,
+                                              const uint2 *__restrict__ rec, const uint2 *__restrict__ runs,
+                                              const uint32_t *__restrict__ row_base,
+                                              const uint32_t *__restrict__ tile_u, uint32_t rows_cap,
+                                              float *__restrict__ rows, uint32_t *__restrict__ pair_keys,
+                                              uint32_t *__restrict__ pair_vals, int N, int *err, int blk, int lane,
+                                              BlockMmaSmem<TW * TH> &sm)
+{
+    constexpr int B = TW * TH;
+    constexpr int KSP = B / 16;                  // 16-pixel k-steps
+    const int g = lane >> 2, t = lane & 3;
+    const int nslots = B * K;
+    const int rstride = (nslots + 2) & ~1;       // runs_stride
+    const uint32_t U = tile_u[blk], rb = row_base[blk];
+    if (U == 0) return;
+    if (rb + U > rows_cap) {
+        if (lane == 0) atomicOr(err, kErrOverflow);
+        return;
+    }
+    const uint2 *brec = rec + (size_t)blk * nslots;
+    const uint2 *bruns = runs + (size_t)blk * rstride;
+    // the block's pixels in the flat pixel space (lane < B stages pixel row `lane`)
+    const int c = cam_of_tile(cb, blk);
+    const CamDev &cam = cb.c[c];
+    const int lt = blk - cam.tile_off;
+    const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
+    long long my_pix = -1;
+    if (lane < B) {
+        const int px = tx * TW + lane % TW, py = ty * TH + lane / TW;
+        if (px < cam.W && py < cam.H) my_pix = cam.pix_off + (long long)py * cam.W + px;
+    }
+    auto stage = [&](int c0, int buf) {
+        if (lane < B) {
+            const bool real = my_pix >= 0;
+            const __nv_bfloat16 *src = dLdF + (real ? (size_t)my_pix * D + c0 : 0);
+            const uint32_t dst = smem_addr(sm.rows[buf] + lane * kBmPitch);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) cp_async_16(dst + 16 * q, src + (real ? 8 * q : 0), real ? 16 : 0);
+        }
+        cp_async_commit_group();
+    };
+    const int nchunk = D / kBmCols;
+    const int mi = lane >> 3, mr = lane & 7;
+    for (uint32_t u0 = 0; u0 < U; u0 += kBmRuns) {
+        const int nr = (int)min((uint32_t)kBmRuns, U - u0);
+        const int MT = nr <= 16 ? 1 : 2;         // 16-run MMA tiles
+        // W^T of this batch from the sorted slot records of its runs
+        for (int i = lane; i < kBmRuns * B; i += 32) (&sm.wt[0][0])[i] = 0.f;
+        __syncwarp();
+        const int i0 = (int)bruns[u0].x, i1 = (int)bruns[u0 + nr].x;
+        for (int i = i0 + lane; i < i1; i += 32) {
+            const uint2 r = brec[i];
+            sm.wt[(int)(r.x >> 16) - (int)u0][r.x & 0xffffu] = __uint_as_float(r.y);
+        }
+        __syncwarp();
+        uint32_t afr[2][KSP][3][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            if (mt >= MT) break;
+#pragma unroll
+            for (int ks = 0; ks < KSP; ++ks) {
+                const int r0 = 16 * mt + g, cc = 16 * ks + 2 * t;
+                const float v[8] = {sm.wt[r0][cc], sm.wt[r0][cc + 1], sm.wt[r0 + 8][cc], sm.wt[r0 + 8][cc + 1],
+                                    sm.wt[r0][cc + 8], sm.wt[r0][cc + 9], sm.wt[r0 + 8][cc + 8], sm.wt[r0 + 8][cc + 9]};
+                float hh[8], mm[8], ll[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) split3(v[e], hh[e], mm[e], ll[e]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    afr[mt][ks][0][q] = pack_bf16(hh[2 * q], hh[2 * q + 1]);
+                    afr[mt][ks][1][q] = pack_bf16(mm[2 * q], mm[2 * q + 1]);
+                    afr[mt][ks][2][q] = pack_bf16(ll[2 * q], ll[2 * q + 1]);
+                }
+            }
+        }
+        stage(0, 0);
+        for (int ch = 0; ch < nchunk; ++ch) {
+            const int buf = ch & 1;
+            if (ch + 1 < nchunk) {
+                stage((ch + 1) * kBmCols, buf ^ 1);
+                cp_async_wait_group<1>();
+            } else {
+                cp_async_wait_group<0>();
+            }
+            __syncwarp();
+            float acc[2][8][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[mt][j][v] = 0.f;
+            const uint32_t base = smem_addr(sm.rows[buf]);
+#pragma unroll
+            for (int ks = 0; ks < KSP; ++ks) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    // pixels 16ks + {0-7, 8-15} x columns 16m + {0-7, 8-15}, transposed
+                    const int r = 16 * ks + mr + 8 * (mi & 1), cc = 16 * m + 8 * (mi >> 1);
+                    uint32_t b0, b1, b2, b3;
+                    ldsm_x4_t(base + r * kBmPitch + 2 * cc, b0, b1, b2, b3);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        if (mt >= MT) break;
+#pragma unroll
+                        for (int sp = 0; sp < 3; ++sp) {
+                            mma16816(acc[mt][2 * m], afr[mt][ks][sp], b0, b1);
+                            mma16816(acc[mt][2 * m + 1], afr[mt][ks][sp], b2, b3);
+                        }
+                    }
+                }
+            }
+            // partial rows (float32): run 16 mt + g (+ 8), columns 8 j + 2 t (+ 1)
+            const int c0 = ch * kBmCols;
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                if (mt >= MT) break;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int u = 16 * mt + g + 8 * half;
+                    if (u < nr) {
+                        float *dst = rows + (size_t)(rb + u0 + u) * D + c0 + 2 * t;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            *(float2 *)(dst + 8 * j) = make_float2(acc[mt][j][2 * half], acc[mt][j][2 * half + 1]);
+                    }
+                }
+            }
+            __syncwarp();                        // the buffer is free for the next stage
+        }
+        for (int u = lane; u < nr; u += 32) {
+            pair_keys[N + rb + u0 + u] = bruns[u0 + u].y;
+            pair_vals[N + rb + u0 + u] = rb + u0 + u;
+        }
+        __syncwarp();
+    }
+}
+
+bool block_mma_supported(int dtype, int D, int B) { return dtype == GS_BF16 && D % kBmCols == 0 && (B == 16 || B == 32); }
+
+// ------------------------------------------------------------------------------------
 // Host side
 // ------------------------------------------------------------------------------------
 int tile_sort_len(int slots)
@@ -700,8 +896,6 @@ static bool tile_launch(const CamTable &cb, const WsLayout &L, int dtype, const 
                         const void *dLdF, void *ws, cudaStream_t s)
 {
     constexpr int B = TW * TH;
-    TmaMaps maps;
-    if (!make_maps(cb, dtype, L.D, dLdF, maps)) return false;
     uint32_t *hdr = ws_ptr<uint32_t>(ws, L.header);
     int *err = (int *)hdr;
     uint2 *rec = ws_ptr<uint2>(ws, L.tile_keys);
@@ -731,6 +925,19 @@ static bool tile_launch(const CamTable &cb, const WsLayout &L, int dtype, const 
         k_tile_slots<TW, TH><<<cb.n_tiles, nt1, sm1, s>>>(cb, L.K, nsort, topk_idx, topk_w, err, rec, runs, tile_u);
     }
     exclusive_scan_u32(tile_u, row_base, cb.n_tiles, hdr + 8, aux, s);
+    if constexpr (B == 16 || B == 32) {
+        if (block_mma_supported(dtype, L.D, B)) {
+            const size_t smb = sizeof(BlockMmaSmem<B>) * kBmWarps;
+            cudaFuncSetAttribute(k_block_mma<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+            const unsigned gb = (unsigned)((cb.n_tiles + kBmWarps - 1) / kBmWarps);
+            k_block_mma<TW, TH><<<gb, kBmWarps * 32, smb, s>>>(cb, L.K, L.D, (const __nv_bfloat16 *)dLdF, rec, runs,
+                                                               row_base, tile_u, (uint32_t)L.rows_cap, rows, pk, pv,
+                                                               L.N, err);
+            return true;
+        }
+    }
+    TmaMaps maps;
+    if (!make_maps(cb, dtype, L.D, dLdF, maps)) return false;
     const size_t sm3 = block_accum_smem(B, L.K, L.D, dtype);
     const int st_sz = (int)stage_bytes(B, L.K, dtype, L.D);
     const int nch = L.D / (dtype == GS_BF16 ? 8 : 4);

@@ -101,6 +101,10 @@ def compare_forward(g, o, K, f_tol=F_TOL, max_fragile=0.02, f_metric="abs"):
         den = np.maximum(np.linalg.norm(F_o, axis=1), 1e-3)
         ferr = np.abs(F_g - F_o).max(1) / den
         stats["F_max_rel"] = float(ferr.max())
+        # beside it, the element-wise relative error with a floor of 1e-3 of the pixel's
+        # largest element (reported: elements that cross zero make it a poor bar)
+        floor = 1e-3 * np.maximum(np.abs(F_o).max(1, keepdims=True), 1e-12)
+        stats["F_elem_rel"] = float((np.abs(F_g - F_o) / (np.abs(F_o) + floor)).max())
         assert ferr.max() <= f_tol, stats
     for key, gk, ok_mask in (("C", "rgb", ok), ("D", "depth", ok), ("T", "T", ok)):
         a = g[gk][idx][ok_mask].astype(np.float64)

@@ -18,8 +18,10 @@ from paper_2602_06991_b300 import _abi as A
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("dtype", ["f32"])
 def test_wait_timeout_is_reported_and_recovered(dtype):
+    # (float32 rows take the TMA pipeline with its mbarrier waits; bf16 rows of these
+    # widths take the tensor-core block product, which waits on nothing)
     sc = S.planes_scene(7, 6000, 512)
     cams = [S.pinhole(160, 120, 131.25)]
     r, ts, out = U.gpu_forward(sc, cams, 8, (16, 16), feat_dtype=dtype, max_instances=1 << 22)
