@@ -153,7 +153,7 @@ class Step:
                                     _p(self.inp[4]), _p(o["F"]), self.r._stream())
 
 
-def run_bf16_batched(args, hbm):
+def run_bf16_batched(args, hbm, sm_mhz=None):
     """The BF16 multi-keyframe form: 1M Gaussians, BF16 rows, 8 orbit keyframes of mixed
     resolution rendered and back-propagated as one step (one launch per stage over all
     views, the whole step one CUDA graph), tile shape picked by the autotuner."""
@@ -177,6 +177,7 @@ def run_bf16_batched(args, hbm):
                       "value": round(step.P / (ms * 1e-3) / 1e6, 3), "autotune_ms": tuned["ms"], "status": st})
         if K == K0:
             main_roof = stage_rooflines(step, hbm)
+            main_kernels = kernel_rooflines(step, hbm, sm_mhz)
             main_launches = None if args.no_launch_count else count_launches(step)
         P, N, D = step.P, step.N, step.D
         del step
@@ -191,6 +192,7 @@ def run_bf16_batched(args, hbm):
            "gaussians": N, "views": len(cams), "D": D, "K": K0, "dtype": "bf16", "tile": main["tile"],
            "kbuf_layout": main["kbuf_layout"],
            "status": main["status"], "roofline": main_roof["blend_loss"], "backward_roofline": main_roof["backward"],
+           "kernels": main_kernels,
            "autotune_ms": main["autotune_ms"], "k_sweep": [{k: v for k, v in r.items() if k != "autotune_ms"}
                                                             for r in sweep],
            "workload": "batched: " + S.CONFIGS["batched"]}
@@ -202,7 +204,7 @@ def run_bf16_batched(args, hbm):
 MAPPING_INSTANCES = 1_150_000_000
 
 
-def run_mapping(args, hbm, iters=100):
+def run_mapping(args, hbm, iters=100, sm_mhz=None):
     """The mapping-iteration workload: 3M Gaussians (70% on 20 planes and boxes, 30%
     clutter), 8 keyframes of 1200x680, D=768 BF16 rows, K=16.  One iteration renders and
     back-propagates all 8 views (a1-a3, the fused a4 + loss, a5 with every per-Gaussian
@@ -262,12 +264,13 @@ def run_mapping(args, hbm, iters=100):
     status = status_of(step)
     ms = t0.elapsed_time(t1) / iters
     sr = stage_rooflines(step, hbm, reps=3)
+    kr = kernel_rooflines(step, hbm, sm_mhz, reps=2)
     out = {"value": round(step.P / (ms * 1e-3) / 1e6, 3), "unit": UNIT, "ms_per_iteration": round(ms, 3),
            "iterations": iters, "captured": "one CUDA graph of all iterations, replayed once after a warm-up replay",
            "pixels_per_iteration": step.P, "gaussians": step.N, "views": len(cams), "D": step.D, "K": step.K,
            "dtype": "bf16", "instances": n_inst, "instance_capacity": MAPPING_INSTANCES, "feature_rows": n_rows,
            "status": status, "stages": {k: round(v, 3) for k, v in stages.items()},
-           "roofline": sr["blend_loss"], "backward_roofline": sr["backward"],
+           "roofline": sr["blend_loss"], "backward_roofline": sr["backward"], "kernels": kr,
            "workload": "mapping: " + S.CONFIGS["mapping"]}
     if status != "ok":
         out["rejected"] = f"workspace status after the timed iterations: {status}"
@@ -421,6 +424,79 @@ def stage_rooflines(step, hbm, reps=10):
     return out
 
 
+# FP32-pipe operations per accepted (pixel, contributor) in the re-walk (k_walk_bwd), one
+# per lane-instruction (an FMA counts once): the offset and quadratic form 9, the cut-off
+# tests 4, alpha and transmittance 7, the weight 1, the colour/depth/feature term g_i 5,
+# the prefix and the alpha adjoint 6, the colour/depth partials 4, the opacity, conic and
+# mean partials 16.  Integer work (the Top-K slot match) and the two MUFU operations are
+# not counted; nor are candidates the walk rejects.
+REWALK_FP32_OPS = 52
+
+
+def kernel_times(step, reps=5):
+    """Device times of the timed stages from the library's kernel timers (a CUDA event
+    pair recorded around each timed launch on the stream it runs on), averaged over
+    `reps` steps of direct launches."""
+    import torch
+    from paper_2602_06991_b300 import _abi as A
+    names = {"binning": A.GS_TIMER_BINNING, "tile_sort": A.GS_TIMER_TILE_SORT, "walk_fwd": A.GS_TIMER_WALK_FWD,
+             "block_grad": A.GS_TIMER_BLOCK_GRAD, "walk_bwd": A.GS_TIMER_WALK_BWD, "complete": A.GS_TIMER_COMPLETE}
+    acc = {k: [] for k in names}
+    torch.cuda.synchronize()
+    A.timer_enable(True)
+    try:
+        for _ in range(reps):
+            step.run()
+            for k, t in names.items():
+                ms = A.timer_read(t)
+                if ms is not None:
+                    acc[k].append(ms)
+    finally:
+        A.timer_enable(False)
+    return {k: float(np.mean(v)) for k, v in acc.items() if v}
+
+
+def kernel_rooflines(step, hbm, sm_mhz, reps=5):
+    """The re-walk against the FP32 ALU peak, the per-block feature-gradient kernel
+    against HBM, and the binning and tile-sort times, all from kernel timers."""
+    import torch
+    kt = kernel_times(step, reps)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    mhz = sm_mhz or 2032.0
+    peak_ops = props.multi_processor_count * 128 * mhz * 1e6 / 1e12      # FP32 lanes x clock
+    contrib = int(step.out["n_contrib"].sum().item())
+    n_inst, n_rows = step.r.counts()
+    out = {"timer_reps": reps}
+    if "walk_bwd" in kt:
+        ach = REWALK_FP32_OPS * contrib / (kt["walk_bwd"] * 1e-3) / 1e12
+        out["rewalk"] = {"kernel": "k_walk_bwd (re-walk adjoint)", "bound": "alu", "achieved": round(ach, 3),
+                         "peak": round(peak_ops, 2), "unit": "Tops/s (FP32 lane operations)",
+                         "frac": round(ach / peak_ops, 4), "ops_per_contributor": REWALK_FP32_OPS,
+                         "contributors": contrib, "kernel_ms": round(kt["walk_bwd"], 4),
+                         "peak_derivation": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
+    if "block_grad" in kt:
+        s = 2 if step.fdt == "bf16" else 4
+        # dL/dF read, one 8-byte slot record read per Top-K slot, the partial rows written
+        # (float32) with their (Gaussian, row) pair
+        b = step.P * step.D * s + step.P * step.K * 8 + n_rows * (step.D * 4 + 8)
+        kname = "k_block_mma (tensor-core, bf16)" if (step.fdt == "bf16" and step.D % 64 == 0) else "k_block_accum (TMA pipeline)"
+        out["block_grad"] = {"kernel": kname, "bound": "hbm",
+                             "achieved": round(b / (kt["block_grad"] * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(b / (kt["block_grad"] * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": b,
+                             "partial_rows": n_rows, "kernel_ms": round(kt["block_grad"], 4)}
+    if "binning" in kt and "tile_sort" in kt:
+        bs = step.r.binning_stats()
+        out["binning"] = {"count_scan_emit_ms": round(kt["binning"], 4), "tile_sort_ms": round(kt["tile_sort"], 4),
+                          "completion_ms": round(kt.get("complete", 0.0), 4),
+                          "total_ms": round(kt["binning"] + kt["tile_sort"] + kt.get("complete", 0.0), 4),
+                          "instances": bs["instances"], "sorted_first": bs["sorted_first"],
+                          "sorted_second": bs["sorted_second"], "tiles_completed": bs["tiles_completed"],
+                          "depth_cut": bool(step.r.cfg.depth_cut)}
+    if "walk_fwd" in kt:
+        out["walk_fwd_ms"] = round(kt["walk_fwd"], 4)
+    return out
+
+
 def graph_node_cost(n_nodes, reps=50):
     """Milliseconds that a CUDA graph of n_nodes trivial kernels takes per replay: the
     launch cost a step of that many graph nodes pays beyond its kernels' work, i.e. the
@@ -549,6 +625,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
         "launches_per_step": launches_per_step,
     }
+    res["kernels"] = kernel_rooflines(step, hbm, clk.get("sm_mhz"))
     if rank == 0:
         res["hybrid"] = run_hybrid(step, ms)
         res["prune"] = run_prune(step)
@@ -560,11 +637,11 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_batched:
         del step
         torch.cuda.empty_cache()
-        res["bf16_batched"] = run_bf16_batched(args, hbm)
+        res["bf16_batched"] = run_bf16_batched(args, hbm, clk.get("sm_mhz"))
         res["bf16_batched"]["speedup_vs_f32_frame"] = round(res["bf16_batched"]["value"] / res["value"], 3)
     if rank == 0 and not args.no_mapping:
         torch.cuda.empty_cache()
-        res["mapping"] = run_mapping(args, hbm)
+        res["mapping"] = run_mapping(args, hbm, sm_mhz=clk.get("sm_mhz"))
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
     return res

@@ -80,9 +80,14 @@ typedef struct {
     int32_t max_feature_rows;  /* capacity of gs_backward's partial feature-gradient rows, one per (pixel
                                   block, selected Gaussian); 0: 32 per block, or max_instances per
                                   (camera, Gaussian) when that is larger */
-    int32_t topk_layout;       /* where gs_topk_select keeps each pixel's K-buffer while it walks: 0 in
-                                  registers, 1 in shared memory (K <= 16; fewer registers per thread).
-                                  The outputs are identical; a performance choice for an autotuner */
+    int32_t topk_layout;       /* how gs_topk_select keeps each pixel's K-buffer while it walks: 0 in
+                                  registers, 1 in shared memory (K <= 16; fewer registers per thread),
+                                  2 in shared memory with warp-level insertion (K <= 16: the warp
+                                  inserts each new member, one lane per slot).  The outputs are
+                                  identical; a performance choice for an autotuner */
+    int32_t depth_cut;         /* 1: the per-tile depth cut (see gs_bin_sort) carried from one render to
+                                  the next on the same workspace; 0: every instance sorted.  Every
+                                  output of a render is bit-identical either way */
 } gs_config;
 
 /* Per-Gaussian gradient outputs of gs_backward (device, caller-allocated, fully
@@ -125,9 +130,21 @@ int gs_preprocess(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, i
                   float *proj, void *ws, size_t ws_bytes, void *stream);
 
 /* a2. Tile binning: every (camera, Gaussian) is duplicated into each screen tile its
- * footprint box overlaps, and the instances are ordered by (tile, depth) with the
- * library's own device radix sort; per-tile instance ranges stay in ws.  Instance
- * overflow sets GS_ERR_OVERFLOW in the error word. */
+ * ellipse reaches (alpha >= 1/255 at some pixel centre of the tile is possible), and the
+ * instances are ordered by (tile, depth) with the library's own device radix sort;
+ * per-tile instance ranges stay in ws.  Instance overflow sets GS_ERR_OVERFLOW in the
+ * error word.
+ * Depth cut (cfg->depth_cut = 1): a tile's walk stops where its last pixel saturates,
+ * usually far in front of the tile's deepest instance.  Each render records, per tile,
+ * the depth where that happened (with a 6% margin, or none if the tile did not
+ * saturate), and the next render on the same workspace sorts only the instances in
+ * front of their tile's recorded depth.  gs_topk_select then completes, within the
+ * same render, every tile that this shorter list leaves unsaturated: it sorts that
+ * tile's remaining instances and walks the tile again over the whole list.  So every
+ * walk sees exactly the full list up to where it stops, and the outputs are identical
+ * to depth_cut = 0; only the amount of sorting changes.  A workspace's first render
+ * (or one whose tile grid changed) records and uses no cut.  The lists are complete
+ * for every later call once gs_topk_select has run. */
 int gs_bin_sort(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
                 const float *proj, void *ws, size_t ws_bytes, void *stream);
 
@@ -262,7 +279,8 @@ int gs_adam_step(const gs_adam_tensor *tensors, int32_t n_tensors, int32_t step,
  * way of rendering features): F_out[p] = sum over every contributor i of w_i f_i -- Eq. 1
  * applied to the feature rows, with the walk's own contributor rule, no Top-K and no
  * renormalisation.  F_out: P x D of cfg->feat_dtype (float32 accumulation).  Call after
- * gs_bin_sort on the same workspace (it walks the binned tile lists). */
+ * gs_topk_select on the same workspace (it walks the binned tile lists, which that call
+ * completes; with cfg->depth_cut = 0, gs_bin_sort is enough). */
 int gs_feature_blend_vanilla(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
                              const float *proj, const void *feats, void *F_out, void *ws, size_t ws_bytes,
                              void *stream);
@@ -314,6 +332,30 @@ int gs_workspace_counts(const void *ws, size_t ws_bytes, void *stream, int64_t *
  * clear).  If n_instances is not NULL it receives the instance count of the last
  * gs_bin_sort. */
 int gs_sync_status(const void *ws, size_t ws_bytes, void *stream, int64_t *n_instances);
+
+/* Binning statistics of the last render on ws (synchronises `stream`, reads the
+ * workspace header): out[0] the (Gaussian, tile) instances, out[1] those sorted by
+ * gs_bin_sort (in front of the depth cut; all of them without cuts), out[2] those sorted
+ * by gs_topk_select to complete unsaturated tiles, out[3] the tiles it completed. */
+int gs_binning_stats(const void *ws, size_t ws_bytes, void *stream, int64_t out[4]);
+
+/* Kernel timers, for measurement.  While enabled (gs_timer_enable(1)), each launch of a
+ * timed stage below that is not being captured into a graph is bracketed by a CUDA event
+ * pair recorded on the stream it runs on (the feature-gradient blocks run on the
+ * library's auxiliary stream).  gs_timer_read(id, &ms) waits for the end event of the
+ * stage's last recorded launch and returns its elapsed milliseconds in *ms; GS_ERR_ARG
+ * for an unknown id or when none was recorded since gs_timer_enable(1).  Process-wide
+ * state, for one device.  Recording adds two event records per timed stage; disabled (the
+ * default) it adds one flag test. */
+#define GS_TIMER_BINNING 0     /* gs_bin_sort: tile counts, their scan, instance emission */
+#define GS_TIMER_TILE_SORT 1   /* gs_bin_sort: radix sort of the instances by tile */
+#define GS_TIMER_WALK_FWD 2    /* gs_topk_select: the (first) forward walk */
+#define GS_TIMER_BLOCK_GRAD 3  /* gs_backward: per-block partial feature-gradient rows */
+#define GS_TIMER_WALK_BWD 4    /* gs_backward: the re-walk adjoint */
+#define GS_TIMER_COMPLETE 5    /* gs_topk_select: completing the tiles the depth cut left unsaturated */
+#define GS_TIMER_COUNT 6
+int gs_timer_enable(int on);
+int gs_timer_read(int id, float *ms);
 
 #ifdef __cplusplus
 }

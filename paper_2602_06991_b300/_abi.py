@@ -18,6 +18,10 @@ GS_MAX_CAMERAS = 16
 GS_MAX_K = 32
 GS_PROJ_FLOATS = 16
 GS_LOSS_NOALLOC_MAX_PIX = 1 << 22
+# kernel timers (gs_timer_enable / gs_timer_read)
+(GS_TIMER_BINNING, GS_TIMER_TILE_SORT, GS_TIMER_WALK_FWD, GS_TIMER_BLOCK_GRAD, GS_TIMER_WALK_BWD,
+ GS_TIMER_COMPLETE) = range(6)
+GS_TIMER_COUNT = 6
 
 c_float_p = ctypes.c_void_p
 vp = ctypes.c_void_p
@@ -32,7 +36,8 @@ class GsCamera(ctypes.Structure):
 class GsConfig(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("D", ctypes.c_int32), ("tile_w", ctypes.c_int32),
                 ("tile_h", ctypes.c_int32), ("feat_dtype", ctypes.c_int32), ("max_instances", ctypes.c_int32),
-                ("max_feature_rows", ctypes.c_int32), ("topk_layout", ctypes.c_int32)]
+                ("max_feature_rows", ctypes.c_int32), ("topk_layout", ctypes.c_int32),
+                ("depth_cut", ctypes.c_int32)]
 
 
 class GsGrads(ctypes.Structure):
@@ -100,6 +105,9 @@ PROTOTYPES = {
     "gs_workspace_counts": (ctypes.c_int, [vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int64)]),
     "gs_sync_status": (ctypes.c_int, [vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int64)]),
+    "gs_binning_stats": (ctypes.c_int, [vp, ctypes.c_size_t, vp, ctypes.POINTER(ctypes.c_int64)]),
+    "gs_timer_enable": (ctypes.c_int, [ctypes.c_int]),
+    "gs_timer_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
 }
 
 _lib = None
@@ -148,3 +156,18 @@ def make_cameras(cams):
         a.width, a.height = int(c.width), int(c.height)
         a.near_z = float(getattr(c, "near", getattr(c, "near_z", 0.2)))
     return arr
+
+
+def timer_enable(on: bool):
+    """Turn the library's kernel timers on (clearing earlier records) or off."""
+    check(load().gs_timer_enable(1 if on else 0), "gs_timer_enable")
+
+
+def timer_read(timer_id: int):
+    """Milliseconds of the last recorded launch of a timed stage, or None if none was recorded."""
+    ms = ctypes.c_float(0.0)
+    st = load().gs_timer_read(int(timer_id), ctypes.byref(ms))
+    if st == GS_ERR_ARG:
+        return None
+    check(st, "gs_timer_read")
+    return float(ms.value)

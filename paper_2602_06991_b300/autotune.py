@@ -19,7 +19,7 @@ import torch
 
 TILE_SHAPES = [(16, 16), (32, 8), (16, 8), (8, 8)]
 # where the walk keeps each pixel's Top-K (gs_config.topk_layout): registers, shared memory
-KBUF_LAYOUTS = {"reg": 0, "smem": 1}
+KBUF_LAYOUTS = {"reg": 0, "smem": 1, "warp": 2}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "autotune.json")
 
 
@@ -71,7 +71,7 @@ def time_step(make_step, reps: int = 10, warmup: int = 3) -> float:
 
 
 def layouts_for(K: int) -> Dict[str, int]:
-    """The K-buffer layouts compiled for K (the shared-memory form holds K <= 16)."""
+    """The K-buffer layouts compiled for K (the shared-memory forms hold K <= 16)."""
     return {n: v for n, v in KBUF_LAYOUTS.items() if v == 0 or K <= 16}
 
 

@@ -25,7 +25,8 @@ bool cfg_ok(const gs_config *cfg)
     return cfg && cfg->K >= 1 && cfg->K <= GS_MAX_K && cfg->D >= 8 && cfg->D <= 1024 && cfg->D % 8 == 0 &&
            tile_ok(cfg->tile_w, cfg->tile_h) && (cfg->feat_dtype == GS_F32 || cfg->feat_dtype == GS_BF16) &&
            cfg->max_instances >= 0 && cfg->max_feature_rows >= 0 &&
-           (cfg->topk_layout == 0 || (cfg->topk_layout == 1 && cfg->K <= 16));
+           (cfg->topk_layout == 0 || ((cfg->topk_layout == 1 || cfg->topk_layout == 2) && cfg->K <= 16)) &&
+           (cfg->depth_cut == 0 || cfg->depth_cut == 1);
 }
 
 static bool cams_ok(const gs_camera *cams, int n_cams)
@@ -77,6 +78,12 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     CamTable ct;
     make_camtable(cfg, cams, n_cams, ct);
     L.N = N; L.K = cfg->K; L.D = cfg->D; L.n_cams = n_cams; L.n_tiles = ct.n_tiles;
+    L.depth_cut = cfg->depth_cut != 0;
+    // identifies the tile grid the recorded cuts belong to (a first render, or another
+    // grid, records and uses none)
+    L.cut_sig = 0x9e3779b9u ^ ((uint32_t)ct.n_tiles * 2654435761u) ^ ((uint32_t)cfg->tile_w << 20) ^
+                ((uint32_t)cfg->tile_h << 12) ^ (uint32_t)n_cams;
+    if (L.cut_sig == 0u) L.cut_sig = 1u;
     L.NE = (long long)n_cams * N;
     L.P = 0;
     for (int c = 0; c < n_cams; ++c) L.P += (long long)cams[c].width * cams[c].height;
@@ -115,10 +122,16 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     L.elem_cnt = take(u * L.NE);
     L.elem_off = take(u * L.NE);
     L.counts = take(u * L.NE);
+    L.counts1 = take(u * L.NE);
     for (int i = 0; i < 2; ++i) L.inst_keys[i] = take(u * L.Mcap);
     for (int i = 0; i < 2; ++i) L.inst_vals[i] = take(u * L.Mcap);
     L.inst_elem = take(u * L.Mcap);
     L.tile_range = take(8 * (size_t)L.n_tiles);
+    L.tile_range2 = take(8 * (size_t)L.n_tiles);
+    L.cut_store = take(u * (size_t)L.n_tiles);
+    L.cut_cur = take(u * (size_t)L.n_tiles);
+    L.tile_incomplete = take(u * (size_t)L.n_tiles);
+    L.tile_sat = take(u * (size_t)L.n_tiles);
     L.sort_hist = take(u * 256 * (kRadixBlocks + 1));
     L.scan_aux = take(u * (kSortBlocks + 32));
     L.inst_grad = take(sizeof(float) * kGradVals * L.Mcap);
@@ -162,6 +175,43 @@ static int launch_status()
 {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+// Kernel timers: one event pair per timed stage, created on first use while enabled.
+struct Timers {
+    std::mutex m;
+    bool enabled = false;
+    cudaEvent_t ev[GS_TIMER_COUNT][2] = {};
+    bool recorded[GS_TIMER_COUNT] = {};
+};
+static Timers &timers()
+{
+    static Timers t;
+    return t;
+}
+
+TimerScope::TimerScope(int id_, cudaStream_t s_) : id(id_), s(s_), on(false)
+{
+    Timers &t = timers();
+    if (id < 0 || !t.enabled) return;             // (read without the lock: a flag set between renders)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    std::lock_guard<std::mutex> g(t.m);
+    if (!t.ev[id][0] && (cudaEventCreate(&t.ev[id][0]) != cudaSuccess || cudaEventCreate(&t.ev[id][1]) != cudaSuccess)) {
+        cudaGetLastError();
+        return;
+    }
+    on = cudaEventRecord(t.ev[id][0], s) == cudaSuccess;
+    if (!on) cudaGetLastError();
+}
+
+TimerScope::~TimerScope()
+{
+    if (!on) return;
+    Timers &t = timers();
+    std::lock_guard<std::mutex> g(t.m);
+    if (cudaEventRecord(t.ev[id][1], s) == cudaSuccess) t.recorded[id] = true;
+    else cudaGetLastError();
 }
 
 // Library-owned auxiliary stream of a device, with the fork and join events of one
@@ -293,9 +343,18 @@ int gs_topk_select(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, 
     if (st) return st;
     CamTable ct;
     make_camtable(cfg, cams, n_cams, ct);
+    cudaStream_t s = (cudaStream_t)stream;
     if (!launch_walk_fwd(ct, L, cfg->K, cfg->topk_layout, n_gauss, proj, ws, rgb_out, depth_out, T_final, n_contrib,
-                         topk_idx, topk_w, (cudaStream_t)stream))
+                         topk_idx, topk_w, 1, s))
         return GS_ERR_UNSUPPORTED;
+    if (L.depth_cut) {
+        // the tiles the depth cut left unsaturated: their remaining instances, then a
+        // second walk over their whole lists (no-ops when none was flagged)
+        TimerScope tm(GS_TIMER_COMPLETE, s);
+        launch_complete_lists(ct, L, n_gauss, proj, ws, s);
+        launch_walk_fwd(ct, L, cfg->K, cfg->topk_layout, n_gauss, proj, ws, rgb_out, depth_out, T_final, n_contrib,
+                        topk_idx, topk_w, 2, s);
+    }
     return launch_status();
 }
 
@@ -535,6 +594,47 @@ int gs_workspace_counts(const void *ws, size_t ws_bytes, void *stream, int64_t *
     if (cudaMemcpy(h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
     if (n_instances) *n_instances = (int64_t)h[1];
     if (n_feature_rows) *n_feature_rows = (int64_t)h[8];
+    return GS_OK;
+}
+
+int gs_binning_stats(const void *ws, size_t ws_bytes, void *stream, int64_t out[4])
+{
+    if (!ws || ws_bytes < 256) return GS_ERR_WORKSPACE;
+    if (!out) return GS_ERR_ARG;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GS_ERR_CUDA;
+    uint32_t h[8];
+    if (cudaMemcpy(h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
+    out[0] = (int64_t)h[1];
+    out[1] = (int64_t)h[kHdrN1];
+    out[2] = (int64_t)h[kHdrN2];
+    out[3] = (int64_t)h[kHdrIncomplete];
+    return GS_OK;
+}
+
+int gs_timer_enable(int on)
+{
+    Timers &t = timers();
+    std::lock_guard<std::mutex> g(t.m);
+    t.enabled = on != 0;
+    for (bool &r : t.recorded) r = false;
+    return GS_OK;
+}
+
+int gs_timer_read(int id, float *ms)
+{
+    if (id < 0 || id >= GS_TIMER_COUNT || !ms) return GS_ERR_ARG;
+    Timers &t = timers();
+    cudaEvent_t a, b;
+    {
+        std::lock_guard<std::mutex> g(t.m);
+        if (!t.recorded[id]) return GS_ERR_ARG;
+        a = t.ev[id][0];
+        b = t.ev[id][1];
+    }
+    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
     return GS_OK;
 }
 

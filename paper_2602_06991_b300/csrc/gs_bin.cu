@@ -52,8 +52,9 @@ __device__ __forceinline__ uint32_t tiles_of(const CamTable &ct, const float4 *p
 // rounded single operations are used (never contracted into FMAs), so the counting and
 // the emitting kernels derive identical runs.
 struct RowCull {
-    float u, v, s2m, A, s12, qb, dymax, dys;
-    bool ok;
+    float u, v, s2m, invA, Aqb, s12, dymax, dys;
+    int ok;
+    RowCull() = default;
     __device__ __forceinline__ RowCull(const float4 r0, const float4 r1)
     {
         u = __fadd_rn(r0.x, r0.z);
@@ -62,22 +63,42 @@ struct RowCull {
         // 2 ln(255 o) through the hardware log2 (one instruction, the same result in both
         // kernels; its error is far inside the 0.4% + 0.02 margin)
         const float q = fminf(kQMax, __fmul_rn(1.38629436f, __log2f(__fmul_rn(255.0f, r1.w))));
-        qb = __fadd_rn(__fmul_rn(fmaxf(q, 0.0f), 1.004f), 0.02f);
-        ok = s1 > 0.f && s2 > 0.f && isfinite(m) && isfinite(s1) && isfinite(s2);
+        const float qb = __fadd_rn(__fmul_rn(fmaxf(q, 0.0f), 1.004f), 0.02f);
+        ok = (s1 > 0.f && s2 > 0.f && isfinite(m) && isfinite(s1) && isfinite(s2)) ? 1 : 0;
         const float s22 = __fmul_rn(s2, s2), s1s2 = __fmul_rn(s1, s2);
         s2m = __fmul_rn(s22, m);
-        A = __fadd_rn(__fmul_rn(s1, s1), __fmul_rn(s2m, m));
+        const float A = __fadd_rn(__fmul_rn(s1, s1), __fmul_rn(s2m, m));
+        invA = __frcp_rn(A);
+        Aqb = __fmul_rn(A, qb);
         s12 = __fmul_rn(s1s2, s1s2);
-        dymax = ok ? __fdiv_rn(__fsqrt_rn(__fmul_rn(A, qb)), s1s2) : 0.f;
+        dymax = ok ? __fdiv_rn(__fsqrt_rn(Aqb), s1s2) : 0.f;
         dys = ok ? __fdiv_rn(__fmul_rn(m, __fsqrt_rn(qb)), s1) : 0.f;
     }
+    // lane j's record, in every lane
+    __device__ __forceinline__ RowCull from_lane(int j) const
+    {
+        RowCull o;
+        o.u = __shfl_sync(0xffffffffu, u, j);
+        o.v = __shfl_sync(0xffffffffu, v, j);
+        o.s2m = __shfl_sync(0xffffffffu, s2m, j);
+        o.invA = __shfl_sync(0xffffffffu, invA, j);
+        o.Aqb = __shfl_sync(0xffffffffu, Aqb, j);
+        o.s12 = __shfl_sync(0xffffffffu, s12, j);
+        o.dymax = __shfl_sync(0xffffffffu, dymax, j);
+        o.dys = __shfl_sync(0xffffffffu, dys, j);
+        o.ok = __shfl_sync(0xffffffffu, ok, j);
+        return o;
+    }
+    // sqrt(A qb - (s1 s2 dy)^2) as x rsqrt(x): the hardware reciprocal square root (a few
+    // ulp, far inside the margins, and the same instructions in both kernels)
     __device__ __forceinline__ float root(float dy) const
     {
-        return __fsqrt_rn(fmaxf(__fsub_rn(__fmul_rn(A, qb), __fmul_rn(s12, __fmul_rn(dy, dy))), 0.f));
+        const float x = __fsub_rn(Aqb, __fmul_rn(s12, __fmul_rn(dy, dy)));
+        return x > 0.f ? __fmul_rn(x, rsqrtf(x)) : 0.f;
     }
     // The run [a, b] of tile columns (within [tx0, tx1]) that the ellipse reaches in tile
-    // row ty; false for none.
-    __device__ __forceinline__ bool run(const CamDev &cam, int tw, int th, int ty, int tx0, int tx1, int &a,
+    // row ty; false for none.  itw = 1 / tile width (exact: a power of two).
+    __device__ __forceinline__ bool run(const CamDev &cam, int th, float itw, int ty, int tx0, int tx1, int &a,
                                         int &b) const
     {
         if (!ok) {
@@ -89,13 +110,13 @@ struct RowCull {
         const float hi = fminf(__fsub_rn((float)min((ty + 1) * th, cam.H) - 0.5f, v), dymax);
         if (!(lo <= hi)) return false;
         const float yr = fminf(fmaxf(dys, lo), hi), yl = fminf(fmaxf(-dys, lo), hi);
-        const float xmax = __fdiv_rn(__fadd_rn(__fmul_rn(s2m, yr), root(yr)), A);
-        const float xmin = __fdiv_rn(__fsub_rn(__fmul_rn(s2m, yl), root(yl)), A);
+        const float xmax = __fmul_rn(__fadd_rn(__fmul_rn(s2m, yr), root(yr)), invA);
+        const float xmin = __fmul_rn(__fsub_rn(__fmul_rn(s2m, yl), root(yl)), invA);
         // columns tx with pixel centres [tx tw + 0.5, (tx + 1) tw - 0.5] meeting
         // [u + xmin, u + xmax], widened by 0.01 px
         const float X0 = __fsub_rn(__fadd_rn(u, xmin), 0.01f), X1 = __fadd_rn(__fadd_rn(u, xmax), 0.01f);
-        const float af = __fsub_rn(ceilf(__fdiv_rn(__fadd_rn(X0, 0.5f), (float)tw)), 1.0f);
-        const float bf = floorf(__fdiv_rn(__fsub_rn(X1, 0.5f), (float)tw));
+        const float af = __fsub_rn(ceilf(__fmul_rn(__fadd_rn(X0, 0.5f), itw)), 1.0f);
+        const float bf = floorf(__fmul_rn(__fsub_rn(X1, 0.5f), itw));
         a = (int)fminf(fmaxf(af, (float)tx0), (float)(tx1 + 1));
         b = (int)fmaxf(fminf(bf, (float)tx1), (float)(tx0 - 1));
         return a <= b;
@@ -103,70 +124,176 @@ struct RowCull {
 };
 
 // Instances of each element, in depth order: the tiles of its footprint box that its
-// ellipse reaches (RowCull runs), counted by depth rank.
+// ellipse reaches (RowCull runs) -- n, the element's instance slots -- and n1, those in
+// front of their tile's depth cut (key <= cut; all of them without cuts), by depth rank.
 __global__ void __launch_bounds__(256) k_count_tiles(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
-                                                     const uint32_t *__restrict__ sorted_e, uint32_t *counts,
-                                                     uint32_t *elem_cnt)
+                                                     const uint32_t *__restrict__ sorted_e,
+                                                     const uint32_t *__restrict__ sorted_key,
+                                                     const uint32_t *__restrict__ cut, int use_cut, uint32_t *counts,
+                                                     uint32_t *counts1, uint32_t *elem_cnt)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= NE) return;
     const uint32_t e = sorted_e[r];
     int c, tx0, tx1, ty0, ty1;
     const uint32_t box = tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1);
-    uint32_t n = 0;
+    uint32_t n = 0, n1 = 0;
     if (box > 0) {
         const RowCull rc(proj[4 * (size_t)e], proj[4 * (size_t)e + 1]);
         const CamDev &cam = ct.c[c];
+        const uint32_t key = sorted_key[r];
+        const float itw = __frcp_rn((float)ct.tile_w);
         for (int ty = ty0; ty <= ty1; ++ty) {
             int a, b;
-            if (rc.run(cam, ct.tile_w, ct.tile_h, ty, tx0, tx1, a, b)) n += (uint32_t)(b - a + 1);
+            if (!rc.run(cam, ct.tile_h, itw, ty, tx0, tx1, a, b)) continue;
+            n += (uint32_t)(b - a + 1);
+            if (use_cut) {
+                const uint32_t *cr = cut + cam.tile_off + ty * cam.tiles_x;
+                for (int x = a; x <= b; ++x) n1 += key <= __ldg(cr + x) ? 1u : 0u;
+            }
         }
+        if (!use_cut) n1 = n;
     }
     counts[r] = n;
+    counts1[r] = n1;
     elem_cnt[e] = n;
 }
 
-// Writes the instances counted by k_count_tiles: one warp per 32 consecutive depth ranks,
-// element by element, one lane per tile row (its run, placed by a warp prefix over the
-// rows), so the writes of an element are consecutive.  (An instance's sort value is its
-// own index, which the tile sort generates; the re-walk's walked flags are cleared by
-// k_clear_walked.)
-__global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
-                                                   const uint32_t *__restrict__ sorted_e,
-                                                   const uint32_t *__restrict__ offsets, uint32_t mcap,
-                                                   uint32_t *inst_keys, uint32_t *inst_elem,
-                                                   uint32_t *elem_off, uint32_t *elem_cnt, int *err)
+// Second binning pass, after the first walk: per element, its instances in tiles that
+// walk left unsaturated and behind their cut (key > cut).  Elements whose footprint box
+// holds no such tile (a summed-area table of the flags) are skipped at once; with no
+// unsaturated tile the counts are zero.
+__global__ void __launch_bounds__(256) k_count_tiles2(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
+                                                      const uint32_t *__restrict__ sorted_e,
+                                                      const uint32_t *__restrict__ sorted_key,
+                                                      const uint32_t *__restrict__ cut,
+                                                      const uint32_t *__restrict__ incomplete,
+                                                      const uint32_t *__restrict__ sat, const uint32_t *hdr,
+                                                      uint32_t *counts2)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= NE) return;
+    uint32_t n2 = 0;
+    if (hdr[kHdrIncomplete] != 0) {
+        const uint32_t e = sorted_e[r];
+        int c, tx0, tx1, ty0, ty1;
+        if (tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1) > 0) {
+            const CamDev &cam = ct.c[c];
+            const uint32_t *S = sat + cam.tile_off;
+            const int W = cam.tiles_x;
+            auto at = [&](int x, int y) { return (x < 0 || y < 0) ? 0u : __ldg(S + y * W + x); };
+            const uint32_t inbox = at(tx1, ty1) - at(tx0 - 1, ty1) - at(tx1, ty0 - 1) + at(tx0 - 1, ty0 - 1);
+            if (inbox > 0) {
+                const RowCull rc(proj[4 * (size_t)e], proj[4 * (size_t)e + 1]);
+                const uint32_t key = sorted_key[r];
+                const float itw = __frcp_rn((float)ct.tile_w);
+                for (int ty = ty0; ty <= ty1; ++ty) {
+                    int a, b;
+                    if (!rc.run(cam, ct.tile_h, itw, ty, tx0, tx1, a, b)) continue;
+                    const int t0 = cam.tile_off + ty * W;
+                    for (int x = a; x <= b; ++x)
+                        n2 += (__ldg(incomplete + t0 + x) != 0u && key > __ldg(cut + t0 + x)) ? 1u : 0u;
+                }
+            }
+        }
+    }
+    counts2[r] = n2;
+}
+
+// Per camera, the inclusive 2D prefix sums of the unsaturated-tile flags over its tile
+// grid (one block per camera: rows, then columns).
+__global__ void __launch_bounds__(1024) k_incomplete_sat(CamTable ct, const uint32_t *__restrict__ incomplete,
+                                                         const uint32_t *hdr, uint32_t *sat)
+{
+    if (hdr[kHdrIncomplete] == 0) return;
+    const CamDev &cam = ct.c[blockIdx.x];
+    const int W = cam.tiles_x, H = cam.tiles_y;
+    const uint32_t *f = incomplete + cam.tile_off;
+    uint32_t *S = sat + cam.tile_off;
+    for (int y = threadIdx.x; y < H; y += blockDim.x) {
+        uint32_t run = 0;
+        for (int x = 0; x < W; ++x) {
+            run += f[y * W + x] != 0u ? 1u : 0u;
+            S[y * W + x] = run;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < W; x += blockDim.x) {
+        uint32_t run = 0;
+        for (int y = 0; y < H; ++y) {
+            run += S[y * W + x];
+            S[y * W + x] = run;
+        }
+    }
+}
+
+// Writes the instances of one binning pass: one warp per 32 consecutive depth ranks,
+// element by element, one lane per tile row to find the row runs, then the element's
+// instance slots walked flat by the warp.  Slot t of element e is instance o(e) + t (its
+// position among all the element's instances, whichever pass sorts it); the pass keeps
+// the slots whose tile passes its test -- PASS 1: in front of the tile's cut; PASS 2:
+// behind it in a tile the first walk left unsaturated -- and writes them compacted
+// (ballot prefix) from the element's offset among that pass's instances: key = tile,
+// value = instance, and the instance's element.  (The re-walk's walked flags are cleared
+// by k_clear_walked.)
+template <int PASS>
+__global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
+                                                   const uint32_t *__restrict__ sorted_e,
+                                                   const uint32_t *__restrict__ sorted_key,
+                                                   const uint32_t *__restrict__ cut,
+                                                   const uint32_t *__restrict__ incomplete, int use_cut,
+                                                   const uint32_t *__restrict__ offsets,
+                                                   const uint32_t *__restrict__ pass_off, const uint32_t *hdr,
+                                                   uint32_t mcap, uint32_t *keys_out, uint32_t *vals_out,
+                                                   uint32_t *inst_elem, uint32_t *elem_off, uint32_t *elem_cnt,
+                                                   int *err)
+{
+    if (PASS == 2 && hdr[kHdrIncomplete] == 0) return;
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    uint32_t e = 0, o = 0, n = 0;
+    const uint32_t pass_total = PASS == 1 ? hdr[kHdrN1] : hdr[kHdrN2];
+    uint32_t e = 0, o = 0, n = 0, po = 0, pn = 0, key = 0;
     int c = 0, tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+    RowCull own = {};                             // this lane's element's record
     if (r < NE) {
         e = sorted_e[r];
-        o = offsets[r];
-        elem_off[e] = o;
-        n = elem_cnt[e];                          // the instances counted by k_count_tiles
-        if (n > 0) tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1);
-        if (n > 0 && (unsigned long long)o + n > mcap) {
+        key = sorted_key[r];
+        if (PASS == 1) {
+            o = offsets[r];
+            elem_off[e] = o;
+        } else {
+            o = elem_off[e];
+        }
+        n = elem_cnt[e];                          // the instance slots counted by k_count_tiles
+        po = pass_off[r];
+        pn = (r + 1 < NE ? pass_off[r + 1] : pass_total) - po;
+        if (pn > 0) {
+            tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1);
+            own = RowCull(proj[4 * (size_t)e], proj[4 * (size_t)e + 1]);
+        }
+        if (PASS == 1 && n > 0 && (unsigned long long)o + n > mcap) {
             // instances past the capacity are dropped; the render is reported as failed
             atomicOr(err, kErrOverflow);
             elem_cnt[e] = o < mcap ? mcap - o : 0u;
         }
     }
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const float itw = __frcp_rn((float)ct.tile_w);
     for (int j = 0; j < 32; ++j) {
-        const uint32_t nj = __shfl_sync(0xffffffffu, n, j);
-        if (nj == 0) continue;
+        if (__shfl_sync(0xffffffffu, pn, j) == 0) continue;
         const uint32_t ej = __shfl_sync(0xffffffffu, e, j), oj = __shfl_sync(0xffffffffu, o, j);
+        const uint32_t kj = __shfl_sync(0xffffffffu, key, j);
+        uint32_t pbase = __shfl_sync(0xffffffffu, po, j);
         const int cj = __shfl_sync(0xffffffffu, c, j);
         const int x0 = __shfl_sync(0xffffffffu, tx0, j), x1 = __shfl_sync(0xffffffffu, tx1, j);
         const int y0 = __shfl_sync(0xffffffffu, ty0, j), y1 = __shfl_sync(0xffffffffu, ty1, j);
         const CamDev &cam = ct.c[cj];
-        const RowCull rc(proj[4 * (size_t)ej], proj[4 * (size_t)ej + 1]);
+        const RowCull rc = own.from_lane(j);
         uint32_t base = oj;
         for (int ry = y0; ry <= y1; ry += 32) {
             const int ty = ry + lane;
             int a = 0, b = -1;
-            const bool any = ty <= y1 && rc.run(cam, ct.tile_w, ct.tile_h, ty, x0, x1, a, b);
+            const bool any = ty <= y1 && rc.run(cam, ct.tile_h, itw, ty, x0, x1, a, b);
             const uint32_t cnt = any ? (uint32_t)(b - a + 1) : 0u;
             uint32_t incl = cnt;
 #pragma unroll
@@ -174,16 +301,63 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
                 const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
                 if (lane >= d) incl += y;
             }
-            const uint32_t at = base + incl - cnt;
-            const uint32_t key0 = (uint32_t)(cam.tile_off + ty * cam.tiles_x + a);
-            for (uint32_t k = 0; k < cnt; ++k) {
-                if (at + k < mcap) {
-                    inst_keys[at + k] = key0 + k;
-                    inst_elem[at + k] = ej;
+            const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+            const int tile_row0 = cam.tile_off + ry * cam.tiles_x;
+            // slot t's row is the number of rows whose inclusive count is <= t
+            for (uint32_t t0 = 0; t0 < tot; t0 += 32) {
+                const uint32_t t = t0 + lane;
+                int row = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1)
+                    if (__shfl_sync(0xffffffffu, incl, row + step - 1) <= t) row += step;
+                const uint32_t first = __shfl_sync(0xffffffffu, incl - cnt, row);
+                const int ar = __shfl_sync(0xffffffffu, a, row);
+                const uint32_t tile = (uint32_t)(tile_row0 + row * cam.tiles_x + ar + (int)(t - first));
+                bool keep = t < tot;
+                if (keep && use_cut) {
+                    const uint32_t ck = __ldg(cut + tile);
+                    keep = PASS == 1 ? kj <= ck : (__ldg(incomplete + tile) != 0u && kj > ck);
                 }
+                const uint32_t kept = __ballot_sync(0xffffffffu, keep);
+                const uint32_t slot = base + t, pos = pbase + __popc(kept & lt_mask);
+                if (keep && slot < mcap && pos < mcap) {
+                    keys_out[pos] = tile;
+                    vals_out[pos] = slot;
+                    inst_elem[slot] = ej;
+                }
+                pbase += __popc(kept);
             }
-            base += __shfl_sync(0xffffffffu, incl, 31);
+            base += tot;
         }
+    }
+}
+
+// The cut keys this render bins with: the recorded ones when depth cuts are on and the
+// workspace's record belongs to this tile grid, else none (and the record is reset).
+// Clears the second sort's ranges.
+__global__ void __launch_bounds__(256) k_cut_prepare(uint32_t n_tiles, const uint32_t *hdr, uint32_t sig,
+                                                     int enabled, uint32_t *cut_store, uint32_t *cut_cur,
+                                                     int2 *ranges2)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const bool recorded = hdr[kHdrCutSig] == sig;
+    if (!recorded) cut_store[t] = kNoCut;
+    cut_cur[t] = (enabled && recorded) ? cut_store[t] : kNoCut;
+    ranges2[t] = make_int2(0, 0);
+}
+
+__global__ void k_store_u32(uint32_t *dst, uint32_t v) { *dst = v; }
+
+// Copies the first min(*n_dev, mcap) (key, value) pairs.
+__global__ void __launch_bounds__(256) k_copy_pairs(const uint32_t *n_dev, uint32_t mcap,
+                                                    const uint32_t *__restrict__ ks, const uint32_t *__restrict__ vs,
+                                                    uint32_t *__restrict__ kd, uint32_t *__restrict__ vd)
+{
+    const uint32_t n = min(*n_dev, mcap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        kd[i] = ks[i];
+        vd[i] = vs[i];
     }
 }
 
@@ -243,6 +417,19 @@ int bits_for(long long v)
     return b < 1 ? 1 : b;
 }
 
+TileLists tile_lists(const WsLayout &L, void *ws)
+{
+    TileLists tl;
+    tl.v1 = ws_ptr<uint32_t>(ws, L.inst_vals[L.inst_sorted]);
+    tl.v2 = ws_ptr<uint32_t>(ws, L.inst_vals[1 - L.inst_sorted]);
+    tl.r1 = ws_ptr<int2>(ws, L.tile_range);
+    tl.r2 = ws_ptr<int2>(ws, L.tile_range2);
+    return tl;
+}
+
+// The first binning pass.  Instances are counted and given their slots (o(e) + t) as
+// without cuts; only those in front of their tile's cut are written and sorted.  Sorted
+// pairs end in buffer L.inst_sorted.
 void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *proj_f, void *ws, cudaStream_t s)
 {
     const float4 *proj = (const float4 *)proj_f;
@@ -257,11 +444,18 @@ void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *
     uint32_t *hist = ws_ptr<uint32_t>(ws, L.sort_hist);
     uint32_t *aux = ws_ptr<uint32_t>(ws, L.scan_aux);
     uint32_t *counts = ws_ptr<uint32_t>(ws, L.counts);
+    uint32_t *counts1 = ws_ptr<uint32_t>(ws, L.counts1);
     uint32_t *elem_cnt = ws_ptr<uint32_t>(ws, L.elem_cnt);
     uint32_t *elem_off = ws_ptr<uint32_t>(ws, L.elem_off);
     uint32_t *inst_elem = ws_ptr<uint32_t>(ws, L.inst_elem);
+    uint32_t *cut_cur = ws_ptr<uint32_t>(ws, L.cut_cur);
     int2 *ranges = ws_ptr<int2>(ws, L.tile_range);
 
+    cudaMemsetAsync(hdr + kHdrN1, 0, 3 * sizeof(uint32_t), s);     // N1, N2, incomplete tiles
+    k_cut_prepare<<<(unsigned)((L.n_tiles + 255) / 256), 256, 0, s>>>(
+        (uint32_t)L.n_tiles, hdr, L.cut_sig, L.depth_cut ? 1 : 0, ws_ptr<uint32_t>(ws, L.cut_store), cut_cur,
+        ws_ptr<int2>(ws, L.tile_range2));
+    k_store_u32<<<1, 1, 0, s>>>(hdr + kHdrCutSig, L.cut_sig);
     if (NE <= 0) {
         cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
         cudaMemsetAsync(n_inst, 0, sizeof(uint32_t), s);
@@ -270,15 +464,65 @@ void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *
     unsigned nb = (unsigned)((NE + 255) / 256);
     k_depth_keys<<<nb, 256, 0, s>>>(NE, proj, dk[0], dv[0]);
     int dcur = radix_sort_pairs(dk[0], dk[1], dv[0], dv[1], NE, nullptr, 32, hist, s);
-    k_count_tiles<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], counts, elem_cnt);
-    exclusive_scan_u32(counts, counts, NE, n_inst, aux, s);
-    k_duplicate<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], counts, (uint32_t)L.Mcap, ik[0], inst_elem,
-                                  elem_off, elem_cnt, err);
-    k_clear_walked<<<148 * 8, 256, 0, s>>>(n_inst, (uint32_t)L.Mcap, ws_ptr<uint8_t>(ws, L.inst_walked));
-    int icur = radix_sort_pairs(ik[0], ik[1], iv[0], iv[1], L.Mcap, n_inst, bits_for(L.n_tiles), hist, s, true);
-    (void)icur;   // equals L.inst_sorted
+    const int use_cut = L.depth_cut ? 1 : 0;
+    {
+        TimerScope tm(GS_TIMER_BINNING, s);
+        k_count_tiles<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], dk[dcur], cut_cur, use_cut, counts, counts1,
+                                         elem_cnt);
+        exclusive_scan_u32(counts, counts, NE, n_inst, aux, s);
+        exclusive_scan_u32(counts1, counts1, NE, hdr + kHdrN1, aux, s);
+        k_duplicate<1><<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], dk[dcur], cut_cur, nullptr, use_cut, counts,
+                                          counts1, hdr, (uint32_t)L.Mcap, ik[0], iv[0], inst_elem, elem_off, elem_cnt,
+                                          err);
+        k_clear_walked<<<148 * 8, 256, 0, s>>>(n_inst, (uint32_t)L.Mcap, ws_ptr<uint8_t>(ws, L.inst_walked));
+    }
+    {
+        TimerScope tm(GS_TIMER_TILE_SORT, s);
+        int icur = radix_sort_pairs(ik[0], ik[1], iv[0], iv[1], L.Mcap, hdr + kHdrN1, bits_for(L.n_tiles), hist, s);
+        (void)icur;   // equals L.inst_sorted
+    }
     k_tile_ranges<<<(unsigned)(((long long)L.n_tiles * 32 + 255) / 256), 256, 0, s>>>(
-        ik[L.inst_sorted], n_inst, (uint32_t)L.Mcap, ranges, (uint32_t)L.n_tiles);
+        ik[L.inst_sorted], hdr + kHdrN1, (uint32_t)L.Mcap, ranges, (uint32_t)L.n_tiles);
+}
+
+// The second binning pass, after the first walk has flagged the tiles it left
+// unsaturated with a cut: their instances behind the cut, sorted by (tile, depth) into
+// buffer 1 - L.inst_sorted (ping-ponging through the instance-partial array, which is
+// unused until the backward), with their runs in tile_range2.  Device-side counts make
+// every launch a no-op when no tile was flagged.
+void launch_complete_lists(const CamTable &ct, const WsLayout &L, int N, const float *proj_f, void *ws,
+                           cudaStream_t s)
+{
+    if (!L.depth_cut || L.NE <= 0) return;
+    const float4 *proj = (const float4 *)proj_f;
+    const long long NE = L.NE;
+    uint32_t *hdr = ws_ptr<uint32_t>(ws, L.header);
+    int *err = (int *)hdr;
+    const int dcur = sorted_buffer(32);
+    const uint32_t *dk = ws_ptr<uint32_t>(ws, L.depth_keys[dcur]);
+    const uint32_t *dv = ws_ptr<uint32_t>(ws, L.depth_vals[dcur]);
+    const int tb = 1 - L.inst_sorted;
+    uint32_t *ik = ws_ptr<uint32_t>(ws, L.inst_keys[tb]);
+    uint32_t *iv = ws_ptr<uint32_t>(ws, L.inst_vals[tb]);
+    uint32_t *scratch = ws_ptr<uint32_t>(ws, L.inst_grad);            // 10 Mcap words, free until the backward
+    uint32_t *counts2 = ws_ptr<uint32_t>(ws, L.counts1);
+    uint32_t *sat = ws_ptr<uint32_t>(ws, L.tile_sat);
+    const uint32_t *cut_cur = ws_ptr<uint32_t>(ws, L.cut_cur);
+    const uint32_t *incomplete = ws_ptr<uint32_t>(ws, L.tile_incomplete);
+    const unsigned nb = (unsigned)((NE + 255) / 256);
+    k_incomplete_sat<<<ct.n, 1024, 0, s>>>(ct, incomplete, hdr, sat);
+    k_count_tiles2<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv, dk, cut_cur, incomplete, sat, hdr, counts2);
+    exclusive_scan_u32(counts2, counts2, NE, hdr + kHdrN2, ws_ptr<uint32_t>(ws, L.scan_aux), s);
+    k_duplicate<2><<<nb, 256, 0, s>>>(ct, N, NE, proj, dv, dk, cut_cur, incomplete, 1, nullptr, counts2, hdr,
+                                      (uint32_t)L.Mcap, ik, iv, ws_ptr<uint32_t>(ws, L.inst_elem),
+                                      ws_ptr<uint32_t>(ws, L.elem_off), ws_ptr<uint32_t>(ws, L.elem_cnt), err);
+    uint32_t *scratch_v = scratch + ((L.Mcap + 3) & ~3ll);              // 16-byte aligned
+    const int cur = radix_sort_pairs(ik, scratch, iv, scratch_v, L.Mcap, hdr + kHdrN2, bits_for(L.n_tiles),
+                                     ws_ptr<uint32_t>(ws, L.sort_hist), s);
+    if (cur == 1)
+        k_copy_pairs<<<148 * 4, 256, 0, s>>>(hdr + kHdrN2, (uint32_t)L.Mcap, scratch, scratch_v, ik, iv);
+    k_tile_ranges<<<(unsigned)(((long long)L.n_tiles * 32 + 255) / 256), 256, 0, s>>>(
+        ik, hdr + kHdrN2, (uint32_t)L.Mcap, ws_ptr<int2>(ws, L.tile_range2), (uint32_t)L.n_tiles);
 }
 
 }  // namespace gs

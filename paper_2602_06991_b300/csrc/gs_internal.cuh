@@ -311,19 +311,43 @@ struct TopKShared {
 // Workspace layout (host-computed; all offsets 256-byte aligned)
 // ------------------------------------------------------------------------------------
 constexpr int kHdrWalkTiles = 16;   // header word: next tile of the persistent re-walk
+constexpr int kHdrN1 = 4;           // header word: instances in front of the depth cut (first sort)
+constexpr int kHdrN2 = 5;           // header word: instances of unsaturated tiles behind it (second sort)
+constexpr int kHdrIncomplete = 6;   // header word: tiles the first walk left unsaturated with a cut
+constexpr int kHdrCutSig = 7;       // header word: the tile grid the recorded cuts belong to
+constexpr uint32_t kNoCut = 0xffffffffu;
+constexpr float kCutMargin = 1.0625f;   // recorded cut = depth where the tile saturated x this
 constexpr int kHdrWaitLimitByte = 96;   // header bytes [96, 104): bound of the pipeline waits (0: default)
+
+// Kernel timers (gs_timer_*): a scope that brackets the launches it encloses with a CUDA
+// event pair on `s`, when timing is enabled and `s` is not capturing.
+struct TimerScope {
+    TimerScope(int id, cudaStream_t s);
+    ~TimerScope();
+    int id;
+    cudaStream_t s;
+    bool on;
+};
 
 struct WsLayout {
     size_t header;             // 256 B: [0] error word, [1] instance count, [2] pieces, [3] multi-piece
-                               // segments, [8] partial rows, [9] pairs, [16] re-walk tile counter,
-                               // [24..25] the wait limit (64-bit, SM cycles, 0 = default)
+                               // segments, [4] / [5] instances of the first / second tile sort,
+                               // [6] incomplete tiles, [7] cut grid signature, [8] partial rows,
+                               // [9] pairs, [16] re-walk tile counter, [24..25] the wait limit
+                               // (64-bit, SM cycles, 0 = default)
     size_t depth_keys[2], depth_vals[2];   // NE
     size_t elem_cnt;           // NE (tiles touched, per element)
     size_t elem_off;           // NE (first pre-sort instance of each element)
     size_t counts;             // NE (counts in depth order, scanned in place)
+    size_t counts1;            // NE (per element: instances of the first, then the second tile sort)
     size_t inst_keys[2], inst_vals[2];     // Mcap
     size_t inst_elem;          // Mcap
-    size_t tile_range;         // n_tiles x int2
+    size_t tile_range;         // n_tiles x int2: each tile's run in the first sorted instances
+    size_t tile_range2;        // n_tiles x int2: its run in the second (empty unless completed)
+    size_t cut_store;          // n_tiles: the depth-cut keys recorded for the next render
+    size_t cut_cur;            // n_tiles: the cut keys this render bins with (kNoCut: none)
+    size_t tile_incomplete;    // n_tiles: 1 where the first walk ended unsaturated with a cut
+    size_t tile_sat;           // n_tiles: per camera, 2D prefix sums of tile_incomplete
     size_t sort_hist;          // (kRadixBlocks + 1) x 256
     size_t scan_aux;           // scan block sums
     size_t inst_grad;          // Mcap x kGradVals floats (per-instance partial 2D gradients)
@@ -351,8 +375,43 @@ struct WsLayout {
     long long NE, P, PK, Mcap, n_pairs, max_multi_rows;
     long long rows_cap, max_pieces_rows;
     bool use_tiles;
+    bool depth_cut;
+    uint32_t cut_sig;
     long long n_fgblocks;      // feature-gradient pixel blocks (fg_block_shape) over all cameras
     int N, K, D, n_tiles, n_cams;
+};
+
+// The binned list of every tile: its run in the first sorted instances, then (for a
+// tile the depth cut left unsaturated) its run in the second -- together the tile's
+// instances in depth order.  Values are instance indices (inst_elem, partials).
+struct TileLists {
+    const uint32_t *v1, *v2;
+    const int2 *r1, *r2;
+};
+struct TileList {
+    const uint32_t *v1, *v2;
+    int s1, n1, s2, n;
+    __device__ __forceinline__ TileList(const TileLists &tl, int tile, bool empty)
+    {
+        const int2 a = tl.r1[tile], b = tl.r2[tile];
+        v1 = tl.v1;
+        v2 = tl.v2;
+        s1 = a.x;
+        s2 = b.x;
+        n1 = empty ? 0 : a.y - a.x;
+        n = empty ? 0 : n1 + (b.y - b.x);
+    }
+    __device__ __forceinline__ uint32_t at(int m) const { return m < n1 ? v1[s1 + m] : v2[s2 + (m - n1)]; }
+};
+// The first sort's pairs are in instance buffer L.inst_sorted, the second's in the other.
+TileLists tile_lists(const WsLayout &L, void *ws);
+// The forward walk's part in the depth cut (k_walk_fwd).
+struct WalkCut {
+    int phase;                 // 1: first walk of every tile; 2: the flagged tiles over their whole list
+    const uint32_t *cut_cur;   // the cut keys this render binned with
+    uint32_t *cut_store;       // the cut keys recorded for the next render
+    uint32_t *incomplete;      // per tile: flagged by phase 1
+    uint32_t *hdr;             // workspace header (the flagged-tile count)
 };
 
 // The argument rules every entry point applies to a gs_config (K, D, tile shape, dtype).
@@ -405,11 +464,13 @@ void launch_project_backward(const CamTable &ct, int N, const float *mean3d, con
                              const uint32_t *elem_off, const uint32_t *elem_cnt, const float *inst_grad, const uint8_t *walked,
                              float *elem_grad, const int *err, const gs_grads *gr, float *pose_part, cudaStream_t s);
 void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *proj, void *ws, cudaStream_t s);
+void launch_complete_lists(const CamTable &ct, const WsLayout &L, int N, const float *proj, void *ws,
+                           cudaStream_t s);
 // kbuf: where the walk keeps each pixel's Top-K (gs_config.topk_layout): 0 registers,
 // 1 shared memory (KM <= 16); identical results.
 bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int kbuf, int N, const float *proj, void *ws,
                      float *rgb_out, float *depth_out, float *T_out, int *n_out, int *idx_out, float *w_out,
-                     cudaStream_t s);
+                     int phase, cudaStream_t s);
 bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const float *proj, void *ws,
                      const float *rgb_out, const float *depth_out, const int *topk_idx, const float *topk_w,
                      const float *dLdC, const float *dLdD, bool with_feature, cudaStream_t s);

@@ -37,10 +37,8 @@ __global__ void __launch_bounds__(256) k_topk_count(long long PK, const int *__r
 // warps' maxima of w go to shared memory and the CTA's maximum to S (atomicMax on bits).
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH) k_walk_maxw(CamTable ct, int N, const float4 *__restrict__ proj,
-                                                      const uint32_t *__restrict__ inst_vals,
-                                                      const uint32_t *__restrict__ inst_elem,
-                                                      const int2 *__restrict__ ranges, const int *__restrict__ err,
-                                                      unsigned *__restrict__ S_bits)
+                                                      TileLists tl, const uint32_t *__restrict__ inst_elem,
+                                                      const int *__restrict__ err, unsigned *__restrict__ S_bits)
 {
     constexpr int B = TW * TH;
     constexpr int NW = B / 32;
@@ -56,23 +54,22 @@ __global__ void __launch_bounds__(TW *TH) k_walk_maxw(CamTable ct, int N, const 
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
     const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
     bool done = !(px < cam.W && py < cam.H);
-    int2 rg = ranges[tile];
-    if (*err) rg.y = rg.x;
+    const TileList lst(tl, tile, *err != 0);
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
     float T = 1.f;
     const int cN = c * N;
-    for (int b0 = rg.x; b0 < rg.y; b0 += B) {
+    for (int b0 = 0; b0 < lst.n; b0 += B) {
         if (__syncthreads_count(!done) == 0) break;
         const int m = b0 + tid;
-        if (m < rg.y) {
-            const uint32_t e = inst_elem[inst_vals[m]];
+        if (m < lst.n) {
+            const uint32_t e = inst_elem[lst.at(m)];
             const float4 *r = proj + 4 * (size_t)e;
             s_r0[tid] = r[0];
             s_r1[tid] = r[1];
             s_g[tid] = (int)e - cN;
         }
         __syncthreads();
-        const int cnt = min(B, rg.y - b0);
+        const int cnt = min(B, lst.n - b0);
         int j_end = cnt;
         for (int j = 0; j < cnt; ++j) {
             if (__all_sync(0xffffffffu, done)) {
@@ -117,8 +114,7 @@ template <int TW, int TH>
 static void walk_maxw_k(const CamTable &ct, const WsLayout &L, int N, const float4 *proj, void *ws, unsigned *S,
                         cudaStream_t s)
 {
-    k_walk_maxw<TW, TH><<<ct.n_tiles, TW * TH, 0, s>>>(ct, N, proj, ws_ptr<uint32_t>(ws, L.inst_vals[L.inst_sorted]),
-                                                       ws_ptr<uint32_t>(ws, L.inst_elem), ws_ptr<int2>(ws, L.tile_range),
+    k_walk_maxw<TW, TH><<<ct.n_tiles, TW * TH, 0, s>>>(ct, N, proj, tile_lists(L, ws), ws_ptr<uint32_t>(ws, L.inst_elem),
                                                        ws_ptr<int>(ws, L.header), S);
 }
 

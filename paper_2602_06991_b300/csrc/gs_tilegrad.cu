@@ -930,6 +930,7 @@ static bool tile_launch(const CamTable &cb, const WsLayout &L, int dtype, const 
             const size_t smb = sizeof(BlockMmaSmem<B>) * kBmWarps;
             cudaFuncSetAttribute(k_block_mma<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
             const unsigned gb = (unsigned)((cb.n_tiles + kBmWarps - 1) / kBmWarps);
+            TimerScope tm(GS_TIMER_BLOCK_GRAD, s);
             k_block_mma<TW, TH><<<gb, kBmWarps * 32, smb, s>>>(cb, L.K, L.D, (const __nv_bfloat16 *)dLdF, rec, runs,
                                                                row_base, tile_u, (uint32_t)L.rows_cap, rows, pk, pv,
                                                                L.N, err);
@@ -944,6 +945,7 @@ static bool tile_launch(const CamTable &cb, const WsLayout &L, int dtype, const 
     const int cpl = nch <= 32 ? 1 : nch <= 64 ? 2 : nch <= 128 ? 4 : 8;
     const unsigned grid = (unsigned)std::max(1, std::min(cb.n_tiles, sm_count()));
     const unsigned long long *wl = ws_ptr<const unsigned long long>(ws, L.header + kHdrWaitLimitByte);
+    TimerScope tm(GS_TIMER_BLOCK_GRAD, s);
     if (dtype == GS_BF16)
         accum_launch<TW, TH, true>(cpl, grid, sm3, s, maps, cb, L, st_sz, rec, runs, row_base, tile_u, rows, pk, pv,
                                    err, wl);

@@ -18,9 +18,8 @@ constexpr int kVanDC = 64;                       // feature columns per pass
 
 template <int TW, int TH, bool BF16>
 __global__ void __launch_bounds__(TW *TH) k_walk_vanilla(CamTable ct, int N, int D, const float4 *__restrict__ proj,
-                                                         const uint32_t *__restrict__ inst_vals,
-                                                         const uint32_t *__restrict__ inst_elem,
-                                                         const int2 *__restrict__ ranges, const int *__restrict__ err,
+                                                         TileLists tl, const uint32_t *__restrict__ inst_elem,
+                                                         const int *__restrict__ err,
                                                          const void *__restrict__ feats, void *__restrict__ F)
 {
     constexpr int B = TW * TH;
@@ -35,8 +34,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_vanilla(CamTable ct, int N, int
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
     const int px = tx * TW + (tid % TW), py = ty * TH + (tid / TW);
     const bool inside = px < cam.W && py < cam.H;
-    int2 rg = ranges[tile];
-    if (*err) rg.y = rg.x;
+    const TileList lst(tl, tile, *err != 0);
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
     const int cN = c * N;
     const long long p = inside ? cam.pix_off + (long long)py * cam.W + px : 0;
@@ -47,11 +45,11 @@ __global__ void __launch_bounds__(TW *TH) k_walk_vanilla(CamTable ct, int N, int
         for (int v = 0; v < DC; ++v) acc[v] = 0.f;
         float T = 1.f;
         bool done = !inside;
-        for (int b0 = rg.x; b0 < rg.y; b0 += B) {
+        for (int b0 = 0; b0 < lst.n; b0 += B) {
             if (__syncthreads_count(!done) == 0) break;
             const int m = b0 + tid;
-            if (m < rg.y) {
-                const uint32_t e = inst_elem[inst_vals[m]];
+            if (m < lst.n) {
+                const uint32_t e = inst_elem[lst.at(m)];
                 const float4 *r = proj + 4 * (size_t)e;
                 s_r0[tid] = r[0];
                 s_r1[tid] = r[1];
@@ -73,7 +71,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_vanilla(CamTable ct, int N, int
                 }
             }
             __syncthreads();
-            const int cnt = min(B, rg.y - b0);
+            const int cnt = min(B, lst.n - b0);
             for (int j = 0; j < cnt && !done; ++j) {
                 float dx, dy;
                 const float4 r1 = s_r1[j];
@@ -129,16 +127,15 @@ static void vanilla_k(int dtype, const CamTable &ct, const WsLayout &L, int N, c
 {
     constexpr int B = TW * TH;
     const size_t sm = sizeof(float) * B * kVanDC;
-    const uint32_t *iv = ws_ptr<uint32_t>(ws, L.inst_vals[L.inst_sorted]);
+    const TileLists tl = tile_lists(L, ws);
     const uint32_t *ie = ws_ptr<uint32_t>(ws, L.inst_elem);
-    const int2 *rg = ws_ptr<int2>(ws, L.tile_range);
     const int *err = ws_ptr<int>(ws, L.header);
     if (dtype == GS_BF16) {
         cudaFuncSetAttribute(k_walk_vanilla<TW, TH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_walk_vanilla<TW, TH, true><<<ct.n_tiles, B, sm, s>>>(ct, N, L.D, proj, iv, ie, rg, err, feats, F);
+        k_walk_vanilla<TW, TH, true><<<ct.n_tiles, B, sm, s>>>(ct, N, L.D, proj, tl, ie, err, feats, F);
     } else {
         cudaFuncSetAttribute(k_walk_vanilla<TW, TH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_walk_vanilla<TW, TH, false><<<ct.n_tiles, B, sm, s>>>(ct, N, L.D, proj, iv, ie, rg, err, feats, F);
+        k_walk_vanilla<TW, TH, false><<<ct.n_tiles, B, sm, s>>>(ct, N, L.D, proj, tl, ie, err, feats, F);
     }
 }
 

@@ -30,12 +30,15 @@
 
 namespace gs {
 
-// KB: the Top-K buffer in registers (0) or in shared memory (1); identical results.
+// KB: the Top-K buffer in registers (0), in shared memory with per-thread insertion (1),
+// or in shared memory with warp-level insertion (2); identical results.
+// wc.phase 1: every tile over its first list; records the tile's depth cut for the next
+// render and flags the tiles it leaves unsaturated behind a cut.  Phase 2: the flagged
+// tiles again, over their whole (completed) list.
 template <int TW, int TH, int KM, int KB>
 __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, const float4 *__restrict__ proj,
-                                                     const uint32_t *__restrict__ inst_vals,
-                                                     const uint32_t *__restrict__ inst_elem,
-                                                     const int2 *__restrict__ ranges, const int *__restrict__ err,
+                                                     TileLists tl, const uint32_t *__restrict__ inst_elem,
+                                                     WalkCut wc, const int *__restrict__ err,
                                                      float *__restrict__ rgb_out, float *__restrict__ depth_out,
                                                      float *__restrict__ T_out, int *__restrict__ n_out,
                                                      int *__restrict__ idx_out, float *__restrict__ w_out)
@@ -45,6 +48,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
     __shared__ int s_g[B];
     const int tid = threadIdx.x;
     const int tile = blockIdx.x;
+    if (wc.phase == 2 && (wc.hdr[kHdrIncomplete] == 0u || wc.incomplete[tile] == 0u)) return;   // whole CTA
     const int c = cam_of_tile(ct, tile);
     const CamDev &cam = ct.c[c];
     const int lt = tile - cam.tile_off;
@@ -56,8 +60,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
     const float wx0 = (float)(tx * TW) + 0.5f, wx1 = (float)(tx * TW + TW) - 0.5f;
     const float wy0 = (float)(ty * TH + (tid - lane) / TW) + 0.5f;
     const float wy1 = wy0 + (float)(32 / TW - 1);
-    int2 rg = ranges[tile];
-    if (*err) rg.y = rg.x;
+    const TileList lst(tl, tile, *err != 0);
     const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, Dd = 0.f;
     int nc = 0;
@@ -70,11 +73,13 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
     else tk.init(s_kw, s_kid, tid, K);
     bool done = !inside;
     const int cN = c * N;
-    for (int b0 = rg.x; b0 < rg.y; b0 += B) {
+    int last_b0 = 0;
+    for (int b0 = 0; b0 < lst.n; b0 += B) {
         if (__syncthreads_count(done) == B) break;
+        last_b0 = b0;
         int m = b0 + tid;
-        if (m < rg.y) {
-            uint32_t e = inst_elem[inst_vals[m]];
+        if (m < lst.n) {
+            uint32_t e = inst_elem[lst.at(m)];
             const float4 *r = proj + 4 * (size_t)e;
             s_r0[tid] = r[0];
             s_r1[tid] = r[1];
@@ -82,11 +87,76 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
             s_g[tid] = (int)e - cN;
         }
         __syncthreads();
-        const int cnt = min(B, rg.y - b0);
+        const int cnt = min(B, lst.n - b0);
         for (int jc = 0; jc < cnt && __any_sync(0xffffffffu, !done); jc += 32) {
             // Gaussians of this chunk that can reach a pixel of this warp's rows
             const int jl = jc + lane;
             unsigned live = __ballot_sync(0xffffffffu, jl < cnt && touches_rect(s_r0[jl], s_r1[jl], wx0, wx1, wy0, wy1));
+            if constexpr (KB == 2) {
+                // warp-level insertion: the lanes step through the staged Gaussians together,
+                // and each pixel that takes one into its Top-K is inserted by the warp, lane
+                // k < KM holding slot k of that pixel (a ballot finds the position, a
+                // shuffle shifts the slots behind it)
+                while (live) {
+                    if (__all_sync(0xffffffffu, done)) break;
+                    const int j = jc + __ffs(live) - 1;
+                    live &= live - 1;
+                    float w = 0.f;
+                    bool take = false;
+                    if (!done) {
+                        float dx, dy;
+                        const float4 r1 = s_r1[j];
+                        const float q = eval_q(pxf, pyf, s_r0[j], r1, dx, dy);
+                        if (q <= kQMax) {
+                            float G, ao;
+                            const float alpha = eval_alpha(q, r1.w, G, ao);
+                            if (alpha >= kAlphaMin) {
+                                const float test_T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+                                if (test_T < kTStop) {
+                                    done = true;
+                                } else {
+                                    w = __fmul_rn(alpha, T);
+                                    const float4 r2 = s_r2[j];
+                                    C0 = fmaf(w, r2.x, C0);
+                                    C1 = fmaf(w, r2.y, C1);
+                                    C2 = fmaf(w, r2.z, C2);
+                                    Dd = fmaf(w, r2.w, Dd);
+                                    T = test_T;
+                                    ++nc;
+                                    take = w > tk.wmin;
+                                }
+                            }
+                        }
+                    }
+                    unsigned ins = __ballot_sync(0xffffffffu, take);
+                    const int gid = s_g[j];
+                    while (ins) {
+                        const int ql = __ffs(ins) - 1;
+                        ins &= ins - 1;
+                        const float nw = __shfl_sync(0xffffffffu, w, ql);
+                        const int col = tid - lane + ql;
+                        float sw = -1.0f;
+                        int sid = -1;
+                        if (lane < KM) {
+                            sw = s_kw[lane * B + col];
+                            sid = s_kid[lane * B + col];
+                        }
+                        // slots that stay ahead: weight >= the new one (sorted descending)
+                        const int pos = __popc(__ballot_sync(0xffffffffu, lane < KM && !(nw > sw)));
+                        const float upw = __shfl_up_sync(0xffffffffu, sw, 1);
+                        const int upi = __shfl_up_sync(0xffffffffu, sid, 1);
+                        float nv = sw;
+                        if (lane < KM && lane >= pos) {
+                            nv = lane == pos ? nw : upw;
+                            s_kw[lane * B + col] = nv;
+                            s_kid[lane * B + col] = lane == pos ? gid : upi;
+                        }
+                        const float nmin = __shfl_sync(0xffffffffu, nv, KM - 1);
+                        if (lane == ql) tk.wmin = nmin;
+                    }
+                }
+                continue;
+            }
             while (live && !done) {
             const int j = jc + __ffs(live) - 1;
             live &= live - 1;
@@ -114,6 +184,21 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
             }
         }
     }
+    // the depth cut for the next render: where the tile saturated (the last staged
+    // Gaussian's depth, with the margin), or none; in phase 1 an unsaturated tile whose
+    // list was cut is flagged for completion
+    const bool saturated = __syncthreads_count(done) == B;
+    if (tid == 0 && *err == 0) {
+        uint32_t rec = kNoCut;
+        if (saturated && lst.n > 0) rec = __float_as_uint(s_r2[min(B, lst.n - last_b0) - 1].w * kCutMargin);
+        wc.cut_store[tile] = rec;
+        if (wc.phase == 1) {
+            const bool inc = !saturated && wc.cut_cur[tile] != kNoCut;
+            wc.incomplete[tile] = inc ? 1u : 0u;
+            if (inc) atomicAdd(wc.hdr + kHdrIncomplete, 1u);
+        }
+    }
+    if constexpr (KB == 2) __syncwarp();          // the slots other lanes wrote
     if (!inside) return;
     const long long p = cam.pix_off + (long long)py * cam.W + px;
     rgb_out[3 * p] = C0;
@@ -149,9 +234,9 @@ __host__ __device__ constexpr int bwd_ppt(int tw, int th) { return tw * th / kBw
 
 template <int TW, int TH, int KM>
 __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable ct, int K, int N, const float4 *__restrict__ proj,
-                                                              const uint32_t *__restrict__ inst_vals,
+                                                              TileLists tl,
                                                               const uint32_t *__restrict__ inst_elem,
-                                                              const int2 *__restrict__ ranges, const int *__restrict__ err,
+                                                              const int *__restrict__ err,
                                                               const float *__restrict__ rgb_out,
                                                               const float *__restrict__ depth_out,
                                                               const int *__restrict__ topk_idx,
@@ -184,8 +269,7 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
         const CamDev &cam = ct.c[c];
         const int lt = tile - cam.tile_off;
         const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-        int2 rg = ranges[tile];
-        if (*err) rg.y = rg.x;
+        const TileList lst(tl, tile, *err != 0);
         const int px = tx * TW + (tid % TW);
         const float pxf = (float)px + 0.5f;
         // pixel-centre rectangle of this warp: all TW columns, its thread rows x PPT rows
@@ -242,13 +326,13 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
             return d;
         };
         const int cN = c * N;
-        for (int b0 = rg.x; b0 < rg.y; b0 += BB) {
+        for (int b0 = 0; b0 < lst.n; b0 += BB) {
             // every pixel stopped: the remaining instances of this tile contribute nothing
             // (their walked flags stay 0, so the per-element sums skip them)
             if (__syncthreads_count(!all_done()) == 0) break;
             for (int t = tid; t < BB; t += NT) {
-                if (b0 + t < rg.y) {
-                    const uint32_t o = inst_vals[b0 + t];
+                if (b0 + t < lst.n) {
+                    const uint32_t o = lst.at(b0 + t);
                     const uint32_t e = inst_elem[o];
                     const float4 *rr = proj + 4 * (size_t)e;
                     s_r0[t] = rr[0];
@@ -260,7 +344,7 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
                 }
             }
             __syncthreads();
-            const int cnt = min(BB, rg.y - b0);
+            const int cnt = min(BB, lst.n - b0);
             // only the staged Gaussians that can reach a pixel of this warp's rectangle (the
             // exact ellipse-rectangle test of the forward walk), in list order; a warp whose
             // pixels have all stopped leaves the batch.  The per-tile sum below counts the
@@ -342,11 +426,11 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
 
 template <int TW, int TH>
 static bool walk_fwd_k(int KM, int kbuf, dim3 grid, cudaStream_t s, const CamTable &ct, int K, int N,
-                       const float4 *proj, const uint32_t *iv, const uint32_t *ie, const int2 *rg, const int *err,
+                       const float4 *proj, const TileLists &tl, const uint32_t *ie, const WalkCut &wc, const int *err,
                        float *a, float *b, float *cc, int *d, int *e, float *f)
 {
     constexpr int B = TW * TH;
-#define GS_WF(KMV, KBV) k_walk_fwd<TW, TH, KMV, KBV><<<grid, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, a, b, cc, d, e, f)
+#define GS_WF(KMV, KBV) k_walk_fwd<TW, TH, KMV, KBV><<<grid, B, 0, s>>>(ct, K, N, proj, tl, ie, wc, err, a, b, cc, d, e, f)
     if (kbuf == 1) {
         switch (KM) {
         case 4: GS_WF(4, 1); return true;
@@ -354,6 +438,14 @@ static bool walk_fwd_k(int KM, int kbuf, dim3 grid, cudaStream_t s, const CamTab
         case 16: GS_WF(16, 1); return true;
         }
         return false;                        // (KM = 32 has no shared form: the buffer would not fit)
+    }
+    if (kbuf == 2) {
+        switch (KM) {
+        case 4: GS_WF(4, 2); return true;
+        case 8: GS_WF(8, 2); return true;
+        case 16: GS_WF(16, 2); return true;
+        }
+        return false;
     }
     switch (KM) {
     case 4: GS_WF(4, 0); return true;
@@ -367,7 +459,7 @@ static bool walk_fwd_k(int KM, int kbuf, dim3 grid, cudaStream_t s, const CamTab
 
 template <int TW, int TH>
 static bool walk_bwd_k(int KM, dim3 grid, cudaStream_t s, const CamTable &ct, int K, int N, const float4 *proj,
-                       const uint32_t *iv, const uint32_t *ie, const int2 *rg, const int *err, const float *C,
+                       const TileLists &tl, const uint32_t *ie, const int *err, const float *C,
                        const float *Dp, const int *ti, const float *tw, const float *h, const float *dC,
                        const float *dD, float *ig, uint8_t *wk, unsigned *ctr)
 {
@@ -382,7 +474,7 @@ static bool walk_bwd_k(int KM, dim3 grid, cudaStream_t s, const CamTable &ct, in
         const long long want = (long long)sms * std::max(1, occ);
         const unsigned g = (unsigned)std::min<long long>(want, grid.x);
         cudaMemsetAsync(ctr, 0, sizeof(unsigned), s);
-        kern<<<g, B, 0, s>>>(ct, K, N, proj, iv, ie, rg, err, C, Dp, ti, tw, h, dC, dD, ig, wk, ctr);
+        kern<<<g, B, 0, s>>>(ct, K, N, proj, tl, ie, err, C, Dp, ti, tw, h, dC, dD, ig, wk, ctr);
     };
     switch (KM) {
     case 4: go(k_walk_bwd<TW, TH, 4>); return true;
@@ -397,19 +489,27 @@ static int k_bucket(int K) { return K <= 4 ? 4 : K <= 8 ? 8 : K <= 16 ? 16 : 32;
 
 bool launch_walk_fwd(const CamTable &ct, const WsLayout &L, int K, int kbuf, int N, const float *proj_f, void *ws,
                      float *rgb_out, float *depth_out, float *T_out, int *n_out, int *idx_out, float *w_out,
-                     cudaStream_t s)
+                     int phase, cudaStream_t s)
 {
+    TimerScope tm(phase == 1 ? GS_TIMER_WALK_FWD : -1, s);
     const float4 *proj = (const float4 *)proj_f;
     const int *err = ws_ptr<int>(ws, L.header);
-    const uint32_t *iv = ws_ptr<uint32_t>(ws, L.inst_vals[L.inst_sorted]);
+    const TileLists tl = tile_lists(L, ws);
     const uint32_t *ie = ws_ptr<uint32_t>(ws, L.inst_elem);
-    const int2 *rg = ws_ptr<int2>(ws, L.tile_range);
+    WalkCut wc;
+    wc.phase = phase;
+    wc.cut_cur = ws_ptr<uint32_t>(ws, L.cut_cur);
+    wc.cut_store = ws_ptr<uint32_t>(ws, L.cut_store);
+    wc.incomplete = ws_ptr<uint32_t>(ws, L.tile_incomplete);
+    wc.hdr = ws_ptr<uint32_t>(ws, L.header);
     dim3 grid(ct.n_tiles);
     int KM = k_bucket(K);
-    if (ct.tile_w == 16 && ct.tile_h == 16) return walk_fwd_k<16, 16>(KM, kbuf, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
-    if (ct.tile_w == 32 && ct.tile_h == 8) return walk_fwd_k<32, 8>(KM, kbuf, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
-    if (ct.tile_w == 16 && ct.tile_h == 8) return walk_fwd_k<16, 8>(KM, kbuf, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
-    if (ct.tile_w == 8 && ct.tile_h == 8) return walk_fwd_k<8, 8>(KM, kbuf, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out);
+#define GS_FWD(TW, TH) walk_fwd_k<TW, TH>(KM, kbuf, grid, s, ct, K, N, proj, tl, ie, wc, err, rgb_out, depth_out, T_out, n_out, idx_out, w_out)
+    if (ct.tile_w == 16 && ct.tile_h == 16) return GS_FWD(16, 16);
+    if (ct.tile_w == 32 && ct.tile_h == 8) return GS_FWD(32, 8);
+    if (ct.tile_w == 16 && ct.tile_h == 8) return GS_FWD(16, 8);
+    if (ct.tile_w == 8 && ct.tile_h == 8) return GS_FWD(8, 8);
+#undef GS_FWD
     return false;
 }
 
@@ -417,21 +517,23 @@ bool launch_walk_bwd(const CamTable &ct, const WsLayout &L, int K, int N, const 
                      const float *rgb_out, const float *depth_out, const int *topk_idx, const float *topk_w,
                      const float *dLdC, const float *dLdD, bool with_feature, cudaStream_t s)
 {
+    TimerScope tm(GS_TIMER_WALK_BWD, s);
     const float4 *proj = (const float4 *)proj_f;
     const int *err = ws_ptr<int>(ws, L.header);
-    const uint32_t *iv = ws_ptr<uint32_t>(ws, L.inst_vals[L.inst_sorted]);
+    const TileLists tl = tile_lists(L, ws);
     const uint32_t *ie = ws_ptr<uint32_t>(ws, L.inst_elem);
-    const int2 *rg = ws_ptr<int2>(ws, L.tile_range);
     const float *h = with_feature ? ws_ptr<float>(ws, L.hbuf) : nullptr;
     float *ig = ws_ptr<float>(ws, L.inst_grad);
     uint8_t *wk = ws_ptr<uint8_t>(ws, L.inst_walked);
     unsigned *ctr = ws_ptr<unsigned>(ws, L.header) + kHdrWalkTiles;
     dim3 grid(ct.n_tiles);
     int KM = k_bucket(K);
-    if (ct.tile_w == 16 && ct.tile_h == 16) return walk_bwd_k<16, 16>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, wk, ctr);
-    if (ct.tile_w == 32 && ct.tile_h == 8) return walk_bwd_k<32, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, wk, ctr);
-    if (ct.tile_w == 16 && ct.tile_h == 8) return walk_bwd_k<16, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, wk, ctr);
-    if (ct.tile_w == 8 && ct.tile_h == 8) return walk_bwd_k<8, 8>(KM, grid, s, ct, K, N, proj, iv, ie, rg, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, wk, ctr);
+#define GS_BWD(TW, TH) walk_bwd_k<TW, TH>(KM, grid, s, ct, K, N, proj, tl, ie, err, rgb_out, depth_out, topk_idx, topk_w, h, dLdC, dLdD, ig, wk, ctr)
+    if (ct.tile_w == 16 && ct.tile_h == 16) return GS_BWD(16, 16);
+    if (ct.tile_w == 32 && ct.tile_h == 8) return GS_BWD(32, 8);
+    if (ct.tile_w == 16 && ct.tile_h == 8) return GS_BWD(16, 8);
+    if (ct.tile_w == 8 && ct.tile_h == 8) return GS_BWD(8, 8);
+#undef GS_BWD
     return false;
 }
 

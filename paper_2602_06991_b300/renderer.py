@@ -43,7 +43,7 @@ class TopKRenderer:
 
     def __init__(self, cameras: Sequence, K: int, D: int, tile=(16, 16), feat_dtype: str = "f32",
                  max_instances: int = 0, device=None, check_overflow: bool = True, max_feature_rows: int = 0,
-                 topk_layout: int = 0):
+                 topk_layout: int = 0, depth_cut: bool = True):
         self.lib = A.load()
         self.cams = A.make_cameras(list(cameras))
         self.n_cams = len(cameras)
@@ -54,7 +54,7 @@ class TopKRenderer:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.check_overflow = check_overflow
         self.cfg = A.GsConfig(self.K, self.D, self.tile[0], self.tile[1], self.dtype, int(max_instances),
-                              int(max_feature_rows), int(topk_layout))
+                              int(max_feature_rows), int(topk_layout), 1 if depth_cut else 0)
         self.P = int(self.lib.gs_pixel_count(self.cams, self.n_cams))
         if self.P < 0:
             raise ValueError("bad cameras")
@@ -89,6 +89,13 @@ class TopKRenderer:
         A.check(self.lib.gs_workspace_counts(_p(self.ws), self.ws.numel(), self._stream(), ctypes.byref(n),
                                              ctypes.byref(m)), "gs_workspace_counts")
         return int(n.value), int(m.value)
+
+    def binning_stats(self):
+        """Of the last render: {instances, sorted_first, sorted_second, tiles_completed}."""
+        out = (ctypes.c_int64 * 4)()
+        A.check(self.lib.gs_binning_stats(_p(self.ws), self.ws.numel(), self._stream(), out), "gs_binning_stats")
+        return {"instances": int(out[0]), "sorted_first": int(out[1]), "sorted_second": int(out[2]),
+                "tiles_completed": int(out[3])}
 
     def sync_status(self):
         n = ctypes.c_int64(0)

@@ -65,7 +65,7 @@ def test_pixel_count_and_workspace(lib):
 
 @pytest.mark.parametrize("field,value", [("K", 0), ("K", 33), ("D", 12), ("D", 0), ("D", 2048),
                                          ("tile_w", 12), ("feat_dtype", 7), ("max_instances", -1),
-                                         ("max_feature_rows", -1)])
+                                         ("max_feature_rows", -1), ("depth_cut", 2), ("depth_cut", -1)])
 def test_bad_config_rejected_on_host(lib, field, value):
     from paper_2602_06991_b300 import _abi as A
     cams = _cams((64, 48))
@@ -115,3 +115,19 @@ def test_missing_library_fails_loudly(tmp_path):
             A.load(str(tmp_path / "nope.so"))
     finally:
         A._lib = saved
+
+
+def test_timers_without_records(lib):
+    """The kernel timers answer 'nothing recorded' (and reject unknown ids) without any
+    device work: enabling clears the records, reads need a recorded launch."""
+    from paper_2602_06991_b300 import _abi as A
+    A.timer_enable(True)
+    try:
+        for t in range(A.GS_TIMER_COUNT):
+            assert A.timer_read(t) is None
+        ms = ctypes.c_float(0.0)
+        assert lib.gs_timer_read(A.GS_TIMER_COUNT, ctypes.byref(ms)) == A.GS_ERR_ARG
+        assert lib.gs_timer_read(-1, ctypes.byref(ms)) == A.GS_ERR_ARG
+        assert lib.gs_timer_read(0, None) == A.GS_ERR_ARG
+    finally:
+        A.timer_enable(False)

@@ -21,12 +21,12 @@ def test_small_full_frame_parity():
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (32, 8), (16, 8), (8, 8)])
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 @pytest.mark.parametrize("K", [4, 16])
 def test_tile_shape_and_kbuf_layout_independence(tile, layout, K):
     """The contributor set is defined per pixel, so every tile shape gives bit-identical
-    outputs, and so does either K-buffer layout of the walk (registers or shared memory);
-    all match the oracle."""
+    outputs, and so does every K-buffer layout of the walk (registers, shared memory with
+    per-thread insertion, shared memory with warp-level insertion); all match the oracle."""
     from paper_2602_06991_b300.renderer import TopKRenderer
     sc, cams, _, _, _ = S.make_config("small", 1)
     _, ts, ref = U.gpu_forward(sc, cams, K, (16, 16))
@@ -36,6 +36,25 @@ def test_tile_shape_and_kbuf_layout_independence(tile, layout, K):
     for k in ("rgb", "depth", "T", "n_contrib", "topk_idx", "topk_w", "F"):
         assert torch.equal(ref[k], out[k]), k
     U.compare_forward(U.to_np(out), U.oracle_forward(sc, cams, K), K)
+
+
+@pytest.mark.parametrize("K", [3, 8, 16])
+def test_kbuf_layouts_identical_on_frame(K):
+    """'frame' (every pixel saturates after ~180 contributors, many Top-K replacements):
+    the three K-buffer layouts give bit-identical forward outputs."""
+    from paper_2602_06991_b300.renderer import TopKRenderer
+    sc, cams, _, tile, _ = S.make_config("frame", 0)
+    ts = U.tensors(sc)
+    outs = []
+    for layout in (0, 1, 2):
+        r = TopKRenderer(cams, K=K, D=sc.d, tile=tile, topk_layout=layout)
+        o = r.forward(*ts)
+        torch.cuda.synchronize()
+        outs.append({k: o[k].clone() for k in ("rgb", "depth", "T", "n_contrib", "topk_idx", "topk_w", "F")})
+        del r, o
+    for o in outs[1:]:
+        for k in outs[0]:
+            assert torch.equal(outs[0][k], o[k]), k
 
 
 @pytest.mark.parametrize("K", [1, 3, 5, 8, 10, 16, 32])
