@@ -104,7 +104,7 @@ class ClockSampler:
 class Step:
     """All buffers of one training step, resident on the device."""
 
-    def __init__(self, workload, seed=0, tile=None, scene=None, max_instances=0, topk_layout=0):
+    def __init__(self, workload, seed=0, tile=None, scene=None, max_instances=0, topk_layout=0, depth_cut=True):
         import torch
         import gs_scenes as S
         from paper_2602_06991_b300.renderer import TopKRenderer
@@ -112,7 +112,7 @@ class Step:
         tile = tuple(tile) if tile is not None else tile0
         self.scene, self.cams, self.K, self.tile, self.fdt = sc, cams, K, tile, fdt
         self.r = TopKRenderer(cams, K=K, D=sc.d, tile=tile, feat_dtype=fdt, check_overflow=True,
-                              max_instances=max_instances, topk_layout=topk_layout)
+                              max_instances=max_instances, topk_layout=topk_layout, depth_cut=depth_cut)
         self.layout = topk_layout
         dev = self.r.device
         tdt = self.r.feat_torch_dtype
@@ -538,7 +538,13 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     from paper_2602_06991_b300 import build
     build()
-    step = Step(args.workload, seed=rank)
+    scene = None
+    if args.views:
+        import gs_scenes as S
+        sc, cams, K, tile, fdt = S.make_config(args.workload, rank)
+        scene = (sc, [cams[int(i)] for i in args.views.split(",")], K, tile, fdt)
+    step = Step(args.workload, seed=rank, scene=scene, max_instances=args.max_instances,
+                depth_cut=not args.no_depth_cut)
     stream = torch.cuda.current_stream()
     launches_per_step = None if args.no_launch_count else count_launches(step)
     graph = None
@@ -607,7 +613,9 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if step.fdt == "f32" else "bf16", "data": "synthetic",
-        "config": workload_config(args.workload, world, step.N, step.P, step.D, step.K, step.tile),
+        "config": dict(workload_config(args.workload, world, step.N, step.P, step.D, step.K, step.tile),
+                       **({"views": args.views} if args.views else {}),
+                       **({"depth_cut": False} if args.no_depth_cut else {})),
         "graph": graph is not None, "status": status,
         "stages": {k: round(v, 4) for k, v in stages.items()},
         "backward_roofline": sr["backward"],
@@ -902,6 +910,10 @@ def main():
     ap.add_argument("--no-launch-count", action="store_true", help="skip the CUPTI launch count (for ncu runs)")
     ap.add_argument("--no-batched", action="store_true", help="skip the BF16 multi-keyframe measurement")
     ap.add_argument("--no-mapping", action="store_true", help="skip the mapping-iteration measurement")
+    ap.add_argument("--views", default="", help="comma-separated view indices of the workload to render "
+                    "(reduced cases for profiling captures; default: all)")
+    ap.add_argument("--max-instances", type=int, default=0, help="instance capacity (0: the library default)")
+    ap.add_argument("--no-depth-cut", action="store_true", help="sort every instance on every render")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))

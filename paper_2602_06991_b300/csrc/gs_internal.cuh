@@ -239,8 +239,10 @@ __device__ __forceinline__ float warp_reduce10(const float (&v)[10], int lane)
 
 // Top-K kept in registers, KM slots in descending weight.  Slots [0, KM - K) hold
 // +inf sentinels so that a runtime K <= KM keeps exactly its K largest in slots
-// [KM - K, KM); comparisons are strict, so among equal weights the earlier
-// contributor (depth order) stays ahead.
+// [KM - K, KM).  The new entry goes after every kept entry of weight >= it (a strict
+// comparison), and from there every entry moves back one slot, so among equal weights
+// the earlier contributor (depth order) stays ahead, also for entries displaced by an
+// insertion in front of them.
 template <int KM>
 struct TopK {
     float w[KM];
@@ -256,9 +258,11 @@ struct TopK {
     __device__ __forceinline__ void insert(float nw, int nid)
     {
         if (!(nw > w[KM - 1])) return;
+        bool shift = false;
 #pragma unroll
         for (int k = 0; k < KM; ++k) {
-            bool sw = nw > w[k];
+            const bool sw = shift || nw > w[k];
+            shift = sw;
             float tw = sw ? nw : w[k];
             int ti = sw ? nid : id[k];
             nw = sw ? w[k] : nw;
