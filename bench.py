@@ -652,6 +652,11 @@ def run_ours(args, rank, world, local_rank):
         res["mapping"] = run_mapping(args, hbm, sm_mhz=clk.get("sm_mhz"))
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
+        # the same leg checks the BF16-row form against the oracle on sampled pixels
+        try:
+            res["cpu_baseline"]["bf16_form_parity"] = bf16_form_parity()
+        except Exception as e:
+            res["cpu_baseline"]["bf16_form_parity"] = {"unavailable": f"{type(e).__name__}: {e}"}
     return res
 
 
@@ -852,6 +857,79 @@ def _cpu_pixels(workload, budget_s, seed=0, pixel_seed=0):
 
 def _cpu_worker(a):
     return _cpu_pixels(*a)
+
+
+def _rel_l2(a, b):
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def bf16_form_parity(n_pix=64, seed=0):
+    """Precision of the BF16-row form against the FP64 oracle on sampled pixels of the
+    'frame_1m_bf16' workload (1M Gaussians, 640x480, D=512 bf16 rows, K=8): per-pixel
+    cosine of F against the oracle fed the bf16 rows and against the oracle fed the
+    original float32 rows, the largest element error of F, the relative L2 error of each
+    gradient group (upstream gradients seeded at the sampled unflagged pixels only), and
+    the pixels the oracle flags as near a threshold (excluded) or near a Top-K tie."""
+    import torch
+    import gs_scenes as S
+    import oracle
+    from paper_2602_06991_b300.renderer import TopKRenderer
+    sc, cams, K, tile, fdt = S.make_config("frame_1m_bf16", seed)
+    cam = cams[0]
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    feats = t(sc.feats).float().to(torch.bfloat16).contiguous()
+    r = TopKRenderer(cams, K=K, D=sc.d, tile=tile, feat_dtype="bf16")
+    ins = [t(sc.mean3d), t(sc.cov3d), t(sc.opacity), t(sc.rgb)]
+    out = r.forward(*ins, feats)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed + 7)
+    pix = np.sort(rng.choice(cam.n_pix, n_pix, replace=False))
+    feats64 = feats.float().cpu().numpy().astype(np.float64)
+    proj = oracle.project(sc, cam)
+    o = oracle.render(sc, cam, K, pixels=pix, proj=proj, feats=feats64)
+    o32 = oracle.render(sc, cam, K, pixels=pix, proj=proj, feats=sc.feats)
+    fragile = (o["flags"] & oracle.F_SET_FRAGILE) != 0
+    near_tie = (o["flags"] & oracle.F_NEAR_TIE) != 0
+    ok = ~fragile
+    gF = out["F"][torch.from_numpy(pix).to(dev)].float().cpu().numpy().astype(np.float64)
+
+    def cos_min(a, b):
+        nz = np.linalg.norm(b, axis=1) > 0
+        c = (a[nz] * b[nz]).sum(1) / (np.linalg.norm(a[nz], axis=1) * np.linalg.norm(b[nz], axis=1) + 1e-300)
+        return float(c.min()) if c.size else 1.0
+
+    res = {"workload": "frame_1m_bf16: " + S.CONFIGS["frame_1m_bf16"], "pixels": int(n_pix),
+           "flagged_near_threshold": int(fragile.sum()), "flagged_near_tie": int(near_tie.sum()),
+           "F_cos_min_vs_bf16_rows": round(cos_min(gF[ok], o["F"][ok]), 7),
+           "F_cos_min_vs_f32_rows": round(cos_min(gF[ok], o32["F"][ok]), 7),
+           "F_max_abs_err_vs_bf16_rows": float(np.abs(gF[ok] - o["F"][ok]).max()) if ok.any() else 0.0}
+    keep = (o["flags"] & (oracle.F_SET_FRAGILE | oracle.F_NEAR_TIE | oracle.F_NEAR_CLAMP)) == 0
+    dF, dC, dD = S.upstream_grads(seed + 9, len(pix), sc.d)
+    dF = np.where(keep[:, None], dF, 0.0).astype(np.float32)
+    dC = np.where(keep[:, None], dC, 0.0).astype(np.float32)
+    dD = np.where(keep, dD, 0.0).astype(np.float32)
+    P = r.P
+    dF_t = torch.zeros(P, sc.d, dtype=torch.bfloat16, device=dev)
+    dC_t = torch.zeros(P, 3, device=dev)
+    dD_t = torch.zeros(P, device=dev)
+    sel = torch.from_numpy(pix).to(dev)
+    dF_t[sel] = t(dF).to(torch.bfloat16)
+    dC_t[sel] = t(dC)
+    dD_t[sel] = t(dD)
+    dF_exact = dF_t[sel].float().cpu().numpy().astype(np.float64)
+    g = r.backward(dF_t, dC_t, dD_t)
+    torch.cuda.synchronize()
+    og = oracle.backward(sc, cam, K, dF_exact, dC.astype(np.float64), dD.astype(np.float64), pixels=pix,
+                         proj=proj, feats=feats64)
+    res["grad_rel_l2"] = {gk: round(_rel_l2(g[gk].cpu().numpy(), og[ok_]), 9) for gk, ok_ in
+                          (("feat", "feat"), ("opacity", "opac"), ("rgb", "rgb"), ("mean3d", "mean3d"),
+                           ("cov3d", "cov3d"))}
+    res["bars"] = "cosine >= 0.999 against both; gradients relative L2 <= 1e-4 (the GPU tests assert these)"
+    del r, out, g, feats, ins
+    torch.cuda.empty_cache()
+    return res
 
 
 def cpu_baseline(workload, budget_s=15.0, seed=0, all_cores=True):

@@ -254,18 +254,22 @@ __device__ __forceinline__ void mma_blend_chunk(const uint32_t (&afr)[2][3][4], 
     const int mi = lane >> 3, mr = lane & 7;
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
+        uint32_t b[4][4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             // matrices: rows 16ks + {0-7, 8-15} x columns 16m + {0-7, 8-15}, transposed
             const int r = 16 * ks + mr + 8 * (mi & 1), c = 16 * m + 8 * (mi >> 1);
-            uint32_t b0, b1, b2, b3;
-            ldsm_x4_t(base + r * kMmaPitch + 2 * c, b0, b1, b2, b3);
-#pragma unroll
-            for (int sp = 0; sp < 3; ++sp) {
-                mma16816(acc[2 * m], afr[ks][sp], b0, b1);
-                mma16816(acc[2 * m + 1], afr[ks][sp], b2, b3);
-            }
+            ldsm_x4_t(base + r * kMmaPitch + 2 * c, b[m][0], b[m][1], b[m][2], b[m][3]);
         }
+        // each accumulator takes the three terms in order; the eight accumulators of a
+        // term are independent, so consecutive products do not wait on each other
+#pragma unroll
+        for (int sp = 0; sp < 3; ++sp)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                mma16816(acc[2 * m], afr[ks][sp], b[m][0], b[m][1]);
+                mma16816(acc[2 * m + 1], afr[ks][sp], b[m][2], b[m][3]);
+            }
     }
 }
 

@@ -35,10 +35,11 @@ __device__ __forceinline__ void stsm_x4(uint32_t a, uint32_t r0, uint32_t r1, ui
                  "r"(r2), "r"(r3)
                  : "memory");
 }
-// d += A (16x16, row) B (16x8, col), bf16 in, float32 accumulate
+// d += A (16x16, row) B (16x8, col), bf16 in, float32 accumulate (registers only, so not
+// volatile: the compiler may interleave independent products)
 __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
 {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
                  "{%8, %9}, {%0, %1, %2, %3};\n"
                  : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));

@@ -744,22 +744,25 @@ __device__ __forceinline__ void block_mma_one(const CamTable &cb, int K, int D, 
             const uint32_t base = smem_addr(sm.rows[buf]);
 #pragma unroll
             for (int ks = 0; ks < KSP; ++ks) {
+                uint32_t b[4][4];
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     // pixels 16ks + {0-7, 8-15} x columns 16m + {0-7, 8-15}, transposed
                     const int r = 16 * ks + mr + 8 * (mi & 1), cc = 16 * m + 8 * (mi >> 1);
-                    uint32_t b0, b1, b2, b3;
-                    ldsm_x4_t(base + r * kBmPitch + 2 * cc, b0, b1, b2, b3);
+                    ldsm_x4_t(base + r * kBmPitch + 2 * cc, b[m][0], b[m][1], b[m][2], b[m][3]);
+                }
+                // per accumulator the three terms in order, independent products between
+#pragma unroll
+                for (int sp = 0; sp < 3; ++sp)
 #pragma unroll
                     for (int mt = 0; mt < 2; ++mt) {
                         if (mt >= MT) break;
 #pragma unroll
-                        for (int sp = 0; sp < 3; ++sp) {
-                            mma16816(acc[mt][2 * m], afr[mt][ks][sp], b0, b1);
-                            mma16816(acc[mt][2 * m + 1], afr[mt][ks][sp], b2, b3);
+                        for (int m = 0; m < 4; ++m) {
+                            mma16816(acc[mt][2 * m], afr[mt][ks][sp], b[m][0], b[m][1]);
+                            mma16816(acc[mt][2 * m + 1], afr[mt][ks][sp], b[m][2], b[m][3]);
                         }
                     }
-                }
             }
             // partial rows (float32): run 16 mt + g (+ 8), columns 8 j + 2 t (+ 1)
             const int c0 = ch * kBmCols;
