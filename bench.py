@@ -619,15 +619,20 @@ def run_ours(args, rank, world, local_rank):
         "graph": graph is not None, "status": status,
         "stages": {k: round(v, 4) for k, v in stages.items()},
         "backward_roofline": sr["backward"],
-        "roofline": {"kernel": "gs_feature_blend_loss (k_blend_loss_group): the step's a4 stage", "bound": "hbm",
+        "roofline": {"kernel": ("gs_feature_blend_loss (k_blend_loss_group): the step's a4 stage" if step.fdt == "f32"
+                                else "gs_feature_blend_loss (k_blend_mma: tensor-core, bf16 rows): the step's a4 stage"),
+                     "bound": "hbm",
                      "achieved": round(achieved_bl, 1), "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved_bl / hbm, 4),
-                     "traffic": measured_traffic("k_blend_loss_group", "paper_2602_06991_b300/csrc/gs_blend.cu"),
+                     # the committed DRAM capture is of the 'frame' workload's kernel
+                     "traffic": (measured_traffic("k_blend_loss_group", "paper_2602_06991_b300/csrc/gs_blend.cu")
+                                 if args.workload == "frame" and not args.views else None),
                      "algorithmic_bytes": abl, "unique_rows": uniq, "kernel_ms": round(blend_loss_ms, 4)},
         "rooflines_other": [
             {"kernel": "gs_feature_blend (k_blend_group): a4 alone", "bound": "hbm", "achieved": round(achieved, 1),
              "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-             "traffic": measured_traffic("k_blend_group", "paper_2602_06991_b300/csrc/gs_blend.cu"),
+             "traffic": (measured_traffic("k_blend_group", "paper_2602_06991_b300/csrc/gs_blend.cu")
+                         if args.workload == "frame" and not args.views else None),
              "algorithmic_bytes": ab, "kernel_ms": round(blend_ms, 4)}],
         "clocks": clk,
         "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
