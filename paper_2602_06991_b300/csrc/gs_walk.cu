@@ -258,6 +258,14 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
     __shared__ float s_red[NW][BB][kGradVals];
     __shared__ unsigned long long s_wrote[NW];   // per warp: the staged Gaussians it reduced
     __shared__ int s_tile;
+    // the tile's Top-K ids as a set (open addressing), and per staged Gaussian whether it
+    // is in it: a Gaussian in no pixel's Top-K of the tile has no feature term anywhere
+    // in it, so its pixels skip the slot match
+    constexpr int kHset = 1024;
+    __shared__ int s_hset[kHset];
+    __shared__ unsigned char s_inu[BB];
+    __shared__ int s_hfull;
+    auto hslot = [](int id) { return (int)(((uint32_t)id * 2654435761u) >> 22); };
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // persistent: each CTA takes the next unprocessed tile until none is left
     for (;;) {
@@ -319,6 +327,32 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
                 for (int k = 0; k < KM; ++k) kfp[r][k] = (kfp[r][k] - H) * inv;
             }
         }
+        for (int i = tid; i < kHset; i += NT) s_hset[i] = -1;
+        if (tid == 0) s_hfull = 0;
+        __syncthreads();
+        // (the ids are read again from topk_idx, so the loop stays rolled and the
+        // registers holding kid are not touched)
+#pragma unroll 1
+        for (int q = 0; q < PPT * K; ++q) {
+            const int r = q / K, k = q - r * K;
+            const int py = ty * TH + (tid / TW) * PPT + r;
+            if (px >= cam.W || py >= cam.H) continue;
+            const int id = topk_idx[(cam.pix_off + (long long)py * cam.W + px) * K + k];
+            if (id < 0) continue;
+            {
+                int h = hslot(id);
+                for (int n = 0;; ++n) {
+                    const int old = atomicCAS(&s_hset[h], -1, id);
+                    if (old == -1 || old == id) break;
+                    h = (h + 1) & (kHset - 1);
+                    if (n == 63) {                      // crowded: every Gaussian counts as a member
+                        s_hfull = 1;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
         auto all_done = [&]() {
             bool d = true;
 #pragma unroll
@@ -339,8 +373,23 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
                     s_r1[t] = rr[1];
                     s_r2[t] = rr[2];
                     s_r3[t] = rr[3];
-                    s_g[t] = (int)e - cN;
+                    const int g = (int)e - cN;
+                    s_g[t] = g;
                     s_o[t] = o;
+                    bool inu = s_hfull != 0;
+                    if (!inu) {
+                        int h = hslot(g);
+                        for (int n = 0; n < 64; ++n) {
+                            const int v = s_hset[h];
+                            if (v == g || n == 63) {
+                                inu = true;
+                                break;
+                            }
+                            if (v == -1) break;
+                            h = (h + 1) & (kHset - 1);
+                        }
+                    }
+                    s_inu[t] = inu ? 1 : 0;
                 }
             }
             __syncthreads();
@@ -383,8 +432,10 @@ __global__ void __launch_bounds__(TW *TH / bwd_ppt(TW, TH)) k_walk_bwd(CamTable 
                     const float4 r2 = s_r2[j];
                     const int gid = s_g[j];
                     float fp = 0.f;
+                    if (s_inu[j]) {                     // the same for the whole CTA
 #pragma unroll
-                    for (int k = 0; k < KM; ++k) fp = (kid[r][k] == gid) ? kfp[r][k] : fp;
+                        for (int k = 0; k < KM; ++k) fp = (kid[r][k] == gid) ? kfp[r][k] : fp;
+                    }
                     const float gi = dC0[r] * r2.x + dC1[r] * r2.y + dC2[r] * r2.z + dD[r] * r2.w + fp;
                     prefix[r] = fmaf(gi, w, prefix[r]);
                     const float suffix = total[r] - prefix[r];
