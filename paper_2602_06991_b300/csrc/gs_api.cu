@@ -47,6 +47,7 @@ bool make_camtable(const gs_config *cfg, const gs_camera *cams, int n_cams, CamT
     ct.tile_w = cfg->tile_w;
     ct.tile_h = cfg->tile_h;
     int tile_off = 0;
+    int row_off = 0;
     long long pix_off = 0;
     for (int c = 0; c < n_cams; ++c) {
         const gs_camera &k = cams[c];
@@ -63,11 +64,14 @@ bool make_camtable(const gs_config *cfg, const gs_camera *cams, int n_cams, CamT
         d.tiles_x = (k.width + cfg->tile_w - 1) / cfg->tile_w;
         d.tiles_y = (k.height + cfg->tile_h - 1) / cfg->tile_h;
         d.tile_off = tile_off;
+        d.row_off = row_off;
         d.pix_off = pix_off;
         tile_off += d.tiles_x * d.tiles_y;
+        row_off += d.tiles_y;
         pix_off += (long long)k.width * k.height;
     }
     ct.n_tiles = tile_off;
+    ct.n_rows = row_off;
     return true;
 }
 
@@ -132,6 +136,8 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     L.cut_cur = take(u * (size_t)L.n_tiles);
     L.tile_incomplete = take(u * (size_t)L.n_tiles);
     L.tile_sat = take(u * (size_t)L.n_tiles);
+    L.cut_rowmin = take(u * (size_t)ct.n_rows);
+    L.cut_rowmax = take(u * (size_t)ct.n_rows);
     L.sort_hist = take(u * 256 * (kRadixBlocks + 1));
     L.scan_aux = take(u * (kSortBlocks + 32));
     L.inst_grad = take(sizeof(float) * kGradVals * L.Mcap);

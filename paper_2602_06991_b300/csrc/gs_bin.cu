@@ -129,7 +129,9 @@ struct RowCull {
 __global__ void __launch_bounds__(256) k_count_tiles(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
                                                      const uint32_t *__restrict__ sorted_e,
                                                      const uint32_t *__restrict__ sorted_key,
-                                                     const uint32_t *__restrict__ cut, int use_cut, uint32_t *counts,
+                                                     const uint32_t *__restrict__ cut,
+                                                     const uint32_t *__restrict__ rowmin,
+                                                     const uint32_t *__restrict__ rowmax, int use_cut, uint32_t *counts,
                                                      uint32_t *counts1, uint32_t *elem_cnt)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -148,8 +150,13 @@ __global__ void __launch_bounds__(256) k_count_tiles(CamTable ct, int N, long lo
             if (!rc.run(cam, ct.tile_h, itw, ty, tx0, tx1, a, b)) continue;
             n += (uint32_t)(b - a + 1);
             if (use_cut) {
-                const uint32_t *cr = cut + cam.tile_off + ty * cam.tiles_x;
-                for (int x = a; x <= b; ++x) n1 += key <= __ldg(cr + x) ? 1u : 0u;
+                const int row = cam.row_off + ty;
+                if (key <= __ldg(rowmin + row)) {
+                    n1 += (uint32_t)(b - a + 1);          // in front of every cut of the row
+                } else if (key <= __ldg(rowmax + row)) {
+                    const uint32_t *cr = cut + cam.tile_off + ty * cam.tiles_x;
+                    for (int x = a; x <= b; ++x) n1 += key <= __ldg(cr + x) ? 1u : 0u;
+                }
             }
         }
         if (!use_cut) n1 = n;
@@ -335,16 +342,33 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
 // The cut keys this render bins with: the recorded ones when depth cuts are on and the
 // workspace's record belongs to this tile grid, else none (and the record is reset).
 // Clears the second sort's ranges.
-__global__ void __launch_bounds__(256) k_cut_prepare(uint32_t n_tiles, const uint32_t *hdr, uint32_t sig,
-                                                     int enabled, uint32_t *cut_store, uint32_t *cut_cur,
-                                                     int2 *ranges2)
+// Also the smallest and largest cut key of each tile row (rowmin / rowmax, preset to
+// all ones / zero): an element at or in front of a row's smallest cut is in front of the
+// cut in every tile of that row, one behind its largest in none.
+__global__ void __launch_bounds__(256) k_cut_prepare(CamTable ct, const uint32_t *hdr, uint32_t sig, int enabled,
+                                                     uint32_t *cut_store, uint32_t *cut_cur, int2 *ranges2,
+                                                     uint32_t *rowmin, uint32_t *rowmax)
 {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_tiles) return;
-    const bool recorded = hdr[kHdrCutSig] == sig;
-    if (!recorded) cut_store[t] = kNoCut;
-    cut_cur[t] = (enabled && recorded) ? cut_store[t] : kNoCut;
-    ranges2[t] = make_int2(0, 0);
+    const bool live = t < (uint32_t)ct.n_tiles;
+    uint32_t cut = kNoCut;
+    int row = -1;
+    if (live) {
+        const bool recorded = hdr[kHdrCutSig] == sig;
+        if (!recorded) cut_store[t] = kNoCut;
+        cut = (enabled && recorded) ? cut_store[t] : kNoCut;
+        cut_cur[t] = cut;
+        ranges2[t] = make_int2(0, 0);
+        const int c = cam_of_tile(ct, (int)t);
+        row = ct.c[c].row_off + ((int)t - ct.c[c].tile_off) / ct.c[c].tiles_x;
+    }
+    // one atomic per distinct row of the warp
+    const unsigned same = __match_any_sync(0xffffffffu, row);
+    const uint32_t mn = __reduce_min_sync(same, cut), mx = __reduce_max_sync(same, cut);
+    if (live && (__ffs(same) - 1) == (int)(threadIdx.x & 31)) {
+        atomicMin(rowmin + row, mn);
+        atomicMax(rowmax + row, mx);
+    }
 }
 
 __global__ void k_store_u32(uint32_t *dst, uint32_t v) { *dst = v; }
@@ -452,9 +476,12 @@ void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *
     int2 *ranges = ws_ptr<int2>(ws, L.tile_range);
 
     cudaMemsetAsync(hdr + kHdrN1, 0, 3 * sizeof(uint32_t), s);     // N1, N2, incomplete tiles
+    uint32_t *rowmin = ws_ptr<uint32_t>(ws, L.cut_rowmin), *rowmax = ws_ptr<uint32_t>(ws, L.cut_rowmax);
+    cudaMemsetAsync(rowmin, 0xff, sizeof(uint32_t) * (size_t)ct.n_rows, s);
+    cudaMemsetAsync(rowmax, 0, sizeof(uint32_t) * (size_t)ct.n_rows, s);
     k_cut_prepare<<<(unsigned)((L.n_tiles + 255) / 256), 256, 0, s>>>(
-        (uint32_t)L.n_tiles, hdr, L.cut_sig, L.depth_cut ? 1 : 0, ws_ptr<uint32_t>(ws, L.cut_store), cut_cur,
-        ws_ptr<int2>(ws, L.tile_range2));
+        ct, hdr, L.cut_sig, L.depth_cut ? 1 : 0, ws_ptr<uint32_t>(ws, L.cut_store), cut_cur,
+        ws_ptr<int2>(ws, L.tile_range2), rowmin, rowmax);
     k_store_u32<<<1, 1, 0, s>>>(hdr + kHdrCutSig, L.cut_sig);
     if (NE <= 0) {
         cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
@@ -467,8 +494,8 @@ void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *
     const int use_cut = L.depth_cut ? 1 : 0;
     {
         TimerScope tm(GS_TIMER_BINNING, s);
-        k_count_tiles<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], dk[dcur], cut_cur, use_cut, counts, counts1,
-                                         elem_cnt);
+        k_count_tiles<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], dk[dcur], cut_cur, rowmin, rowmax, use_cut,
+                                         counts, counts1, elem_cnt);
         exclusive_scan_u32(counts, counts, NE, n_inst, aux, s);
         exclusive_scan_u32(counts1, counts1, NE, hdr + kHdrN1, aux, s);
         k_duplicate<1><<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], dk[dcur], cut_cur, nullptr, use_cut, counts,

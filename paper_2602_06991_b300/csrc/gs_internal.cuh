@@ -46,6 +46,7 @@ struct CamDev {
     int W, H;
     int tiles_x, tiles_y;
     int tile_off;              // first global tile id of this camera
+    int row_off;               // first global tile-row index of this camera
     long long pix_off;         // first flat pixel index of this camera
 };
 
@@ -53,6 +54,7 @@ struct CamTable {
     int n;
     int tile_w, tile_h;
     int n_tiles;               // total over cameras
+    int n_rows;                // tile rows, total over cameras
     CamDev c[GS_MAX_CAMERAS];
 };
 
@@ -352,6 +354,7 @@ struct WsLayout {
     size_t cut_cur;            // n_tiles: the cut keys this render bins with (kNoCut: none)
     size_t tile_incomplete;    // n_tiles: 1 where the first walk ended unsaturated with a cut
     size_t tile_sat;           // n_tiles: per camera, 2D prefix sums of tile_incomplete
+    size_t cut_rowmin, cut_rowmax;   // per tile row: the smallest and largest current cut key
     size_t sort_hist;          // (kRadixBlocks + 1) x 256
     size_t scan_aux;           // scan block sums
     size_t inst_grad;          // Mcap x kGradVals floats (per-instance partial 2D gradients)

@@ -58,15 +58,18 @@ void retile(const CamTable &ct, int bw, int bh, CamTable &out)
     out = ct;
     out.tile_w = bw;
     out.tile_h = bh;
-    int off = 0;
+    int off = 0, rows = 0;
     for (int c = 0; c < ct.n; ++c) {
         CamDev &d = out.c[c];
         d.tiles_x = (d.W + bw - 1) / bw;
         d.tiles_y = (d.H + bh - 1) / bh;
         d.tile_off = off;
+        d.row_off = rows;
         off += d.tiles_x * d.tiles_y;
+        rows += d.tiles_y;
     }
     out.n_tiles = off;
+    out.n_rows = rows;
 }
 
 // ------------------------------------------------------------------------------------
