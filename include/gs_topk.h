@@ -142,9 +142,11 @@ int gs_preprocess(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, i
  * same render, every tile that this shorter list leaves unsaturated: it sorts that
  * tile's remaining instances and walks the tile again over the whole list.  So every
  * walk sees exactly the full list up to where it stops, and the outputs are identical
- * to depth_cut = 0; only the amount of sorting changes.  A workspace's first render
- * (or one whose tile grid changed) records and uses no cut.  The lists are complete
- * for every later call once gs_topk_select has run. */
+ * to depth_cut = 0; only the amount of sorting changes.  A render uses the cuts an
+ * earlier render on the workspace recorded for the same tile grid (a signature in the
+ * header says which); a workspace whose first 256 bytes are zero, or one whose tile grid
+ * changed, starts without cuts.  The lists are complete for every later call once
+ * gs_topk_select has run. */
 int gs_bin_sort(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, int32_t n_gauss,
                 const float *proj, void *ws, size_t ws_bytes, void *stream);
 

@@ -317,7 +317,7 @@ __device__ __forceinline__ void mma_group(long long p0, long long n_pix, int lo,
                           float *__restrict__ dLdD, float *__restrict__ part, float *__restrict__ h, int lane,
                           MmaWarpSmem &sm)
 {
-    const int g = lane >> 2, t = lane & 3;
+    const int g = lane >> 2;
     const int KS = U <= 16 ? 1 : 2;               // 16-row k-steps
     const int nrows = 16 * KS;
     uint32_t afr[2][3][4];
@@ -325,6 +325,17 @@ __device__ __forceinline__ void mma_group(long long p0, long long n_pix, int lo,
     __syncwarp();                                 // W is read: the pixel buffers it shares memory with are free
     const int nchunk = D / kMmaCols;
     const int steps = LOSS ? 2 * nchunk : nchunk;
+    // per-pixel sums F.F, F.G, G.G of the first pass.  K >= 16 (wider weight tables, two
+    // k-steps in most groups): as the diagonals of the 16 x 16 products F F^T, F G^T, G G^T
+    // on the tensor cores (two 8-pixel n-tiles each), which issues fewer instructions than
+    // the 12 FMAs per value pair; K < 16: FMAs per lane, summed over the quad (fewer
+    // registers, one more resident CTA per SM -- measured faster there)
+    constexpr bool kTcSums = K >= 16;
+    float ffc[2][4], fgc[2][4], ggc[2][4];
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) ffc[n][v] = fgc[n][v] = ggc[n][v] = 0.f;
     float ffa = 0.f, fga = 0.f, gga = 0.f, ffb = 0.f, fgb = 0.f, ggb = 0.f;
     float caa = 0.f, cba = 0.f, cab = 0.f, cbb = 0.f, cosa = 0.f, cosb = 0.f;
     float hacc[4][4];
@@ -340,15 +351,28 @@ __device__ __forceinline__ void mma_group(long long p0, long long n_pix, int lo,
         const int ch = step % nchunk;
         const bool pass2 = LOSS && step >= nchunk;
         if (LOSS && step == nchunk) {
-            // end of pass 1: per-pixel sums over the quad, then the loss coefficients
+            // end of pass 1: the diagonals -- pixel g's entry of n-tile 0 and pixel g + 8's
+            // of n-tile 1 sit in lane 4 g + g / 2 -- for the whole quad, then the loss
+            // coefficients
+            if constexpr (kTcSums) {
+                const int src = 4 * g + (g >> 1);
+                auto diag = [&](const float (&c)[2][4], float &va, float &vb) {
+                    va = __shfl_sync(0xffffffffu, (g & 1) ? c[0][1] : c[0][0], src);
+                    vb = __shfl_sync(0xffffffffu, (g & 1) ? c[1][3] : c[1][2], src);
+                };
+                diag(ffc, ffa, ffb);
+                diag(fgc, fga, fgb);
+                diag(ggc, gga, ggb);
+            } else {
 #pragma unroll
-            for (int o = 1; o < 4; o <<= 1) {
-                ffa += __shfl_xor_sync(0xffffffffu, ffa, o);
-                fga += __shfl_xor_sync(0xffffffffu, fga, o);
-                gga += __shfl_xor_sync(0xffffffffu, gga, o);
-                ffb += __shfl_xor_sync(0xffffffffu, ffb, o);
-                fgb += __shfl_xor_sync(0xffffffffu, fgb, o);
-                ggb += __shfl_xor_sync(0xffffffffu, ggb, o);
+                for (int o = 1; o < 4; o <<= 1) {
+                    ffa += __shfl_xor_sync(0xffffffffu, ffa, o);
+                    fga += __shfl_xor_sync(0xffffffffu, fga, o);
+                    gga += __shfl_xor_sync(0xffffffffu, gga, o);
+                    ffb += __shfl_xor_sync(0xffffffffu, ffb, o);
+                    fgb += __shfl_xor_sync(0xffffffffu, fgb, o);
+                    ggb += __shfl_xor_sync(0xffffffffu, ggb, o);
+                }
             }
             auto coef = [&](float ff, float fg, float gg, float &ca, float &cb, float &cs) {
                 const float nf = sqrtf(ff), ng = sqrtf(gg);
@@ -383,7 +407,24 @@ __device__ __forceinline__ void mma_group(long long p0, long long n_pix, int lo,
             fo[j][1] = pack_bf16(acc[j][2], acc[j][3]);
         }
         if (!pass2) {
-            if (LOSS) {                           // the loss sees F as stored
+            // the loss sees F as stored: F (bf16, the A layout of its accumulators) against
+            // G^T and F^T (B fragments read from the staged rows of the chunk)
+            const uint32_t pb = smem_addr(sm.pix[buf]);
+            const int mi = lane >> 3, mr = lane & 7;
+            if (LOSS && kTcSums) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    uint32_t b0, b1, b2, b3;
+                    ldsm_x4(pb + (mr + 8 * (mi >> 1)) * kMmaPitch + 2 * (16 * m + 8 * (mi & 1)), b0, b1, b2, b3);
+                    const uint32_t af[4] = {fo[2 * m][0], fo[2 * m][1], fo[2 * m + 1][0], fo[2 * m + 1][1]};
+                    const uint32_t ag[4] = {gt[2 * m][0], gt[2 * m][1], gt[2 * m + 1][0], gt[2 * m + 1][1]};
+                    mma16816(fgc[0], af, b0, b1);
+                    mma16816(fgc[1], af, b2, b3);
+                    mma16816(ggc[0], ag, b0, b1);
+                    mma16816(ggc[1], ag, b2, b3);
+                }
+                __syncwarp();                     // every lane has read the target values
+            } else if (LOSS) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const float a0 = bf_lo(fo[j][0]), a1 = bf_hi(fo[j][0]), b0 = bf_lo(fo[j][1]), b1 = bf_hi(fo[j][1]);
@@ -398,6 +439,16 @@ __device__ __forceinline__ void mma_group(long long p0, long long n_pix, int lo,
                 __syncwarp();                     // every lane has read the target values
             }
             mma_pix_store(fo, sm, buf, lane, F, p0, n_pix, lo, hi, D, c0);
+            if (LOSS && kTcSums) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {     // the buffer now holds F as stored
+                    uint32_t b0, b1, b2, b3;
+                    ldsm_x4(pb + (mr + 8 * (mi >> 1)) * kMmaPitch + 2 * (16 * m + 8 * (mi & 1)), b0, b1, b2, b3);
+                    const uint32_t af[4] = {fo[2 * m][0], fo[2 * m][1], fo[2 * m + 1][0], fo[2 * m + 1][1]};
+                    mma16816(ffc[0], af, b0, b1);
+                    mma16816(ffc[1], af, b2, b3);
+                }
+            }
         } else {
             // dL/dF = a Fgt + b F (F as stored), written in bf16; as stored it is the A
             // operand of h = dL/dF R^T (k-step m covers n-tiles 2m, 2m + 1)
@@ -493,7 +544,7 @@ __device__ __forceinline__ void mma_group_tail(long long p0, long long n_pix, in
 }
 
 template <int K, bool LOSS>
-__global__ void __launch_bounds__(kMmaWarps * 32, 4) k_blend_mma(long long n_pix, int D, const int *__restrict__ idx,
+__global__ void __launch_bounds__(kMmaWarps * 32, (LOSS && K >= 16) ? 3 : 4) k_blend_mma(long long n_pix, int D, const int *__restrict__ idx,
                                                               const float *__restrict__ wts,
                                                               const __nv_bfloat16 *__restrict__ feats,
                                                               const __nv_bfloat16 *__restrict__ Fgt,

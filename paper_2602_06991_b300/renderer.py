@@ -72,6 +72,9 @@ class TopKRenderer:
     def _ensure_ws(self, N: int):
         if self.ws is None or self.ws_n != N:
             self.ws = torch.empty(self.workspace_bytes(N), dtype=torch.uint8, device=self.device)
+            # a zeroed header: the first render records depth cuts instead of reading
+            # whatever an earlier tenant of the memory left
+            self.ws[:256].zero_()
             self.ws_n = N
 
     def _stream(self):
