@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256) k_count_tiles(CamTable ct, int N, long lo
 // Second binning pass, after the first walk: per element, its instances in tiles that
 // walk left unsaturated and behind their cut (key > cut).  Elements whose footprint box
 // holds no such tile (a summed-area table of the flags) are skipped at once; with no
-// unsaturated tile the counts are zero.
+// unsaturated tile nothing is written, and the scan and emission after it skip as well.
 __global__ void __launch_bounds__(256) k_count_tiles2(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
                                                       const uint32_t *__restrict__ sorted_e,
                                                       const uint32_t *__restrict__ sorted_key,
@@ -179,9 +179,9 @@ __global__ void __launch_bounds__(256) k_count_tiles2(CamTable ct, int N, long l
                                                       uint32_t *counts2)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= NE) return;
+    if (r >= NE || hdr[kHdrIncomplete] == 0) return;   // (nothing flagged: counts and their scan are skipped)
     uint32_t n2 = 0;
-    if (hdr[kHdrIncomplete] != 0) {
+    {
         const uint32_t e = sorted_e[r];
         int c, tx0, tx1, ty0, ty1;
         if (tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1) > 0) {
@@ -539,7 +539,9 @@ void launch_complete_lists(const CamTable &ct, const WsLayout &L, int N, const f
     const unsigned nb = (unsigned)((NE + 255) / 256);
     k_incomplete_sat<<<ct.n, 1024, 0, s>>>(ct, incomplete, hdr, sat);
     k_count_tiles2<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv, dk, cut_cur, incomplete, sat, hdr, counts2);
-    exclusive_scan_u32(counts2, counts2, NE, hdr + kHdrN2, ws_ptr<uint32_t>(ws, L.scan_aux), s);
+    // with no flagged tile the scan is skipped too: the second sort's count stays the zero
+    // binning set
+    exclusive_scan_u32(counts2, counts2, NE, hdr + kHdrN2, ws_ptr<uint32_t>(ws, L.scan_aux), s, hdr + kHdrIncomplete);
     k_duplicate<2><<<nb, 256, 0, s>>>(ct, N, NE, proj, dv, dk, cut_cur, incomplete, 1, nullptr, counts2, hdr,
                                       (uint32_t)L.Mcap, ik, iv, ws_ptr<uint32_t>(ws, L.inst_elem),
                                       ws_ptr<uint32_t>(ws, L.elem_off), ws_ptr<uint32_t>(ws, L.elem_cnt), err);

@@ -462,8 +462,10 @@ int radix_sort_pairs(uint32_t *keys0, uint32_t *keys1, uint32_t *vals0, uint32_t
                      long long n_host, const uint32_t *n_dev, int n_bits, uint32_t *hist,
                      cudaStream_t s, bool vals_are_index = false);
 // Exclusive scan of n uint32 in -> out (may alias); *total (device) = sum if non-null.
+// run_if (optional, device): when it points to zero every launch returns at once and
+// neither out nor *total is written (the caller keeps them valid for that case).
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t *total,
-                        uint32_t *aux, cudaStream_t s);
+                        uint32_t *aux, cudaStream_t s, const uint32_t *run_if = nullptr);
 
 void launch_preprocess(const CamTable &ct, int N, const float *mean3d, const float *cov3d, const float *opac,
                        const float *rgb, float *proj, cudaStream_t s);

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_upsweep(const uint32_t *__r
                                                              const uint32_t *n_dev, int shift,
                                                              uint32_t *__restrict__ hist)
 {
+    if (n_dev && *n_dev == 0u) return;           // an empty device-counted sort: nothing to do
     constexpr int W = kSortThreads / 32;
     __shared__ uint32_t cnt[W][256];
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -59,8 +60,9 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_upsweep(const uint32_t *__r
 // G blocks (hist[b][d] becomes the exclusive prefix over blocks 0..b-1; each thread
 // takes a contiguous run of blocks) and writes the digit total to hist[G][d].  The
 // downsweep adds the prefix of the digit totals.
-__global__ void __launch_bounds__(512) k_rs_scan(uint32_t *hist, int G)
+__global__ void __launch_bounds__(512) k_rs_scan(uint32_t *hist, int G, const uint32_t *n_dev)
 {
+    if (n_dev && *n_dev == 0u) return;
     __shared__ uint32_t warp_sums[16];
     const int d = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int per = (G + 511) / 512;
@@ -87,8 +89,10 @@ __global__ void __launch_bounds__(512) k_rs_scan(uint32_t *hist, int G)
 }
 
 // Exclusive scan in place of len uint32 by one block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_scan_single(uint32_t *data, int len, uint32_t *total)
+__global__ void __launch_bounds__(1024) k_scan_single(uint32_t *data, int len, uint32_t *total,
+                                                      const uint32_t *run_if = nullptr)
 {
+    if (run_if && *run_if == 0u) return;
     __shared__ uint32_t warp_sums[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int per = (len + 1023) / 1024;
@@ -149,6 +153,7 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_downsweep(const uint32_t *_
                                                                long long n_host, const uint32_t *n_dev, int shift,
                                                                const uint32_t *__restrict__ hist)
 {
+    if (n_dev && *n_dev == 0u) return;
     constexpr int W = kSortThreads / 32;
     constexpr int kChunks = kSortTile / 4;           // 16-byte chunks per tile and array
     __shared__ uint32_t s_base[256];     // global position of this block's next key of each digit
@@ -293,7 +298,7 @@ int radix_sort_pairs(uint32_t *keys0, uint32_t *keys1, uint32_t *vals0, uint32_t
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
         k_rs_upsweep<<<G, kSortThreads, 0, s>>>(kb[cur], n_host, n_dev, shift, hist);
-        k_rs_scan<<<256, 512, 0, s>>>(hist, G);
+        k_rs_scan<<<256, 512, 0, s>>>(hist, G, n_dev);
         const uint32_t *vin = (p == 0 && vals_are_index) ? nullptr : vb[cur];
         k_rs_downsweep<<<G, kSortThreads, 0, s>>>(kb[cur], vin, kb[cur ^ 1], vb[cur ^ 1], n_host, n_dev, shift, hist);
         cur ^= 1;
@@ -336,8 +341,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *warp_s
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ in, long long n,
-                                                              long long per_block, uint32_t *aux)
+                                                              long long per_block, uint32_t *aux,
+                                                              const uint32_t *run_if)
 {
+    if (run_if && *run_if == 0u) return;
     __shared__ uint32_t warp_sums[32];
     long long b0 = (long long)blockIdx.x * per_block, b1 = min(b0 + per_block, n);
     uint32_t s = 0;
@@ -348,8 +355,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *in, uint32_t *out, long long n,
-                                                            long long per_block, const uint32_t *aux)
+                                                            long long per_block, const uint32_t *aux,
+                                                            const uint32_t *run_if)
 {
+    if (run_if && *run_if == 0u) return;
     __shared__ uint32_t warp_sums[32];
     __shared__ uint32_t tile[kScanTile];
     const int tid = threadIdx.x;
@@ -380,7 +389,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *in, 
     }
 }
 
-void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t *total, uint32_t *aux, cudaStream_t s)
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t *total, uint32_t *aux, cudaStream_t s,
+                        const uint32_t *run_if)
 {
     if (n <= 0) {
         if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
@@ -391,9 +401,9 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, long long n, uint32_t
     long long tiles_per_block = (n_tiles + G - 1) / G;
     long long per_block = tiles_per_block * kScanTile;
     G = (int)((n + per_block - 1) / per_block);
-    k_scan_reduce<<<G, kScanThreads, 0, s>>>(in, n, per_block, aux);
-    k_scan_single<<<1, 1024, 0, s>>>(aux, G, total);
-    k_scan_down<<<G, kScanThreads, 0, s>>>(in, out, n, per_block, aux);
+    k_scan_reduce<<<G, kScanThreads, 0, s>>>(in, n, per_block, aux, run_if);
+    k_scan_single<<<1, 1024, 0, s>>>(aux, G, total, run_if);
+    k_scan_down<<<G, kScanThreads, 0, s>>>(in, out, n, per_block, aux, run_if);
 }
 
 }  // namespace gs
