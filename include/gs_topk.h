@@ -336,9 +336,11 @@ int gs_workspace_counts(const void *ws, size_t ws_bytes, void *stream, int64_t *
 int gs_sync_status(const void *ws, size_t ws_bytes, void *stream, int64_t *n_instances);
 
 /* Binning statistics of the last render on ws (synchronises `stream`, reads the
- * workspace header): out[0] the (Gaussian, tile) instances, out[1] those sorted by
- * gs_bin_sort (in front of the depth cut; all of them without cuts), out[2] those sorted
- * by gs_topk_select to complete unsaturated tiles, out[3] the tiles it completed. */
+ * workspace header): out[0] the instance slots -- every (Gaussian, tile) instance without
+ * cuts; with cuts, those of the Gaussians in front of some cut of their rows plus those
+ * the completion emitted -- out[1] the instances sorted by gs_bin_sort (in front of the
+ * depth cut), out[2] those sorted by gs_topk_select to complete unsaturated tiles, out[3]
+ * the tiles it completed. */
 int gs_binning_stats(const void *ws, size_t ws_bytes, void *stream, int64_t out[4]);
 
 /* Kernel timers, for measurement.  While enabled (gs_timer_enable(1)), each launch of a

@@ -138,6 +138,7 @@ bool make_layout(const gs_config *cfg, const gs_camera *cams, int n_cams, int N,
     L.tile_sat = take(u * (size_t)L.n_tiles);
     L.cut_rowmin = take(u * (size_t)ct.n_rows);
     L.cut_rowmax = take(u * (size_t)ct.n_rows);
+    L.cut_rowmax_st = take(u * (size_t)kCutLevels * ct.n_rows);
     L.sort_hist = take(u * 256 * (kRadixBlocks + 1));
     L.scan_aux = take(u * (kSortBlocks + 32));
     L.inst_grad = take(sizeof(float) * kGradVals * L.Mcap);
@@ -596,9 +597,9 @@ int gs_workspace_counts(const void *ws, size_t ws_bytes, void *stream, int64_t *
 {
     if (!ws || ws_bytes < 256) return GS_ERR_WORKSPACE;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GS_ERR_CUDA;
-    uint32_t h[9];
+    uint32_t h[16];
     if (cudaMemcpy(h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
-    if (n_instances) *n_instances = (int64_t)h[1];
+    if (n_instances) *n_instances = (int64_t)h[1] + (int64_t)h[kHdrFresh];
     if (n_feature_rows) *n_feature_rows = (int64_t)h[8];
     return GS_OK;
 }
@@ -608,9 +609,9 @@ int gs_binning_stats(const void *ws, size_t ws_bytes, void *stream, int64_t out[
     if (!ws || ws_bytes < 256) return GS_ERR_WORKSPACE;
     if (!out) return GS_ERR_ARG;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GS_ERR_CUDA;
-    uint32_t h[8];
+    uint32_t h[16];
     if (cudaMemcpy(h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
-    out[0] = (int64_t)h[1];
+    out[0] = (int64_t)h[1] + (int64_t)h[kHdrFresh];
     out[1] = (int64_t)h[kHdrN1];
     out[2] = (int64_t)h[kHdrN2];
     out[3] = (int64_t)h[kHdrIncomplete];
@@ -648,9 +649,9 @@ int gs_sync_status(const void *ws, size_t ws_bytes, void *stream, int64_t *n_ins
 {
     if (!ws || ws_bytes < 256) return GS_ERR_WORKSPACE;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GS_ERR_CUDA;
-    uint32_t h[2];
+    uint32_t h[16];
     if (cudaMemcpy(h, ws, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
-    if (n_instances) *n_instances = (int64_t)h[1];
+    if (n_instances) *n_instances = (int64_t)h[1] + (int64_t)h[kHdrFresh];
     if (h[0] & kErrOverflow) return GS_ERR_OVERFLOW;
     if (h[0] & kErrTimeout) return GS_ERR_TIMEOUT;
     return GS_OK;

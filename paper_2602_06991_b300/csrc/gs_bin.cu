@@ -126,13 +126,17 @@ struct RowCull {
 // Instances of each element, in depth order: the tiles of its footprint box that its
 // ellipse reaches (RowCull runs) -- n, the element's instance slots -- and n1, those in
 // front of their tile's depth cut (key <= cut; all of them without cuts), by depth rank.
+// An element behind the largest cut of every row of its box has no instance in front of
+// any cut: it gets no slots here (n = 0, no run is computed), and slots only if the
+// completion pass emits some of its instances.
 __global__ void __launch_bounds__(256) k_count_tiles(CamTable ct, int N, long long NE, const float4 *__restrict__ proj,
                                                      const uint32_t *__restrict__ sorted_e,
                                                      const uint32_t *__restrict__ sorted_key,
                                                      const uint32_t *__restrict__ cut,
                                                      const uint32_t *__restrict__ rowmin,
-                                                     const uint32_t *__restrict__ rowmax, int use_cut, uint32_t *counts,
-                                                     uint32_t *counts1, uint32_t *elem_cnt)
+                                                     const uint32_t *__restrict__ rowmax,
+                                                     const uint32_t *__restrict__ rowmax_st, int use_cut,
+                                                     uint32_t *counts, uint32_t *counts1, uint32_t *elem_cnt)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= NE) return;
@@ -140,10 +144,18 @@ __global__ void __launch_bounds__(256) k_count_tiles(CamTable ct, int N, long lo
     int c, tx0, tx1, ty0, ty1;
     const uint32_t box = tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1);
     uint32_t n = 0, n1 = 0;
-    if (box > 0) {
+    bool any = box > 0;
+    const uint32_t key = sorted_key[r];
+    if (any && use_cut) {
+        // the largest cut over the box's rows: two lookups in the sparse table
+        const int row0 = ct.c[c].row_off, len = ty1 - ty0 + 1;
+        const int l = 31 - __clz(len);
+        const uint32_t *st = rowmax_st + (size_t)l * ct.n_rows;
+        any = key <= max(__ldg(st + row0 + ty0), __ldg(st + row0 + ty1 - (1 << l) + 1));
+    }
+    if (any) {
         const RowCull rc(proj[4 * (size_t)e], proj[4 * (size_t)e + 1]);
         const CamDev &cam = ct.c[c];
-        const uint32_t key = sorted_key[r];
         const float itw = __frcp_rn((float)ct.tile_w);
         for (int ty = ty0; ty <= ty1; ++ty) {
             int a, b;
@@ -176,7 +188,8 @@ __global__ void __launch_bounds__(256) k_count_tiles2(CamTable ct, int N, long l
                                                       const uint32_t *__restrict__ cut,
                                                       const uint32_t *__restrict__ incomplete,
                                                       const uint32_t *__restrict__ sat, const uint32_t *hdr,
-                                                      uint32_t *counts2)
+                                                      const uint32_t *__restrict__ elem_cnt, uint32_t *counts2,
+                                                      uint32_t *fresh2)
 {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= NE || hdr[kHdrIncomplete] == 0) return;   // (nothing flagged: counts and their scan are skipped)
@@ -205,6 +218,7 @@ __global__ void __launch_bounds__(256) k_count_tiles2(CamTable ct, int N, long l
         }
     }
     counts2[r] = n2;
+    fresh2[r] = (n2 > 0 && elem_cnt[sorted_e[r]] == 0) ? n2 : 0u;
 }
 
 // Per camera, the inclusive 2D prefix sums of the unsaturated-tile flags over its tile
@@ -253,13 +267,16 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
                                                    const uint32_t *__restrict__ pass_off, const uint32_t *hdr,
                                                    uint32_t mcap, uint32_t *keys_out, uint32_t *vals_out,
                                                    uint32_t *inst_elem, uint32_t *elem_off, uint32_t *elem_cnt,
-                                                   int *err)
+                                                   uint8_t *walked, int *err)
 {
     if (PASS == 2 && hdr[kHdrIncomplete] == 0) return;
+    // PASS 2, an element the first pass gave no slots: its emitted instances take fresh
+    // slots after the first pass's, in emission order (offsets: the scanned counts of those)
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const uint32_t pass_total = PASS == 1 ? hdr[kHdrN1] : hdr[kHdrN2];
     uint32_t e = 0, o = 0, n = 0, po = 0, pn = 0, key = 0;
+    int fresh = 0;
     int c = 0, tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
     RowCull own = {};                             // this lane's element's record
     if (r < NE) {
@@ -274,6 +291,13 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
         n = elem_cnt[e];                          // the instance slots counted by k_count_tiles
         po = pass_off[r];
         pn = (r + 1 < NE ? pass_off[r + 1] : pass_total) - po;
+        if (PASS == 2 && n == 0 && pn > 0) {
+            fresh = 1;
+            o = hdr[1] + offsets[r];
+            elem_off[e] = o;
+            elem_cnt[e] = pn;
+            if ((unsigned long long)o + pn > mcap) atomicOr(err, kErrOverflow);
+        }
         if (pn > 0) {
             tiles_of(ct, proj, e, N, c, tx0, tx1, ty0, ty1);
             own = RowCull(proj[4 * (size_t)e], proj[4 * (size_t)e + 1]);
@@ -291,6 +315,8 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
         const uint32_t ej = __shfl_sync(0xffffffffu, e, j), oj = __shfl_sync(0xffffffffu, o, j);
         const uint32_t kj = __shfl_sync(0xffffffffu, key, j);
         uint32_t pbase = __shfl_sync(0xffffffffu, po, j);
+        const uint32_t pstart = pbase;
+        const bool fj = __shfl_sync(0xffffffffu, fresh, j) != 0;
         const int cj = __shfl_sync(0xffffffffu, c, j);
         const int x0 = __shfl_sync(0xffffffffu, tx0, j), x1 = __shfl_sync(0xffffffffu, tx1, j);
         const int y0 = __shfl_sync(0xffffffffu, ty0, j), y1 = __shfl_sync(0xffffffffu, ty1, j);
@@ -326,11 +352,13 @@ __global__ void __launch_bounds__(256) k_duplicate(CamTable ct, int N, long long
                     keep = PASS == 1 ? kj <= ck : (__ldg(incomplete + tile) != 0u && kj > ck);
                 }
                 const uint32_t kept = __ballot_sync(0xffffffffu, keep);
-                const uint32_t slot = base + t, pos = pbase + __popc(kept & lt_mask);
+                const uint32_t pos = pbase + __popc(kept & lt_mask);
+                const uint32_t slot = fj ? oj + (pos - pstart) : base + t;
                 if (keep && slot < mcap && pos < mcap) {
                     keys_out[pos] = tile;
                     vals_out[pos] = slot;
                     inst_elem[slot] = ej;
+                    if (fj) walked[slot] = 0;         // (beyond the first pass's cleared slots)
                 }
                 pbase += __popc(kept);
             }
@@ -368,6 +396,24 @@ __global__ void __launch_bounds__(256) k_cut_prepare(CamTable ct, const uint32_t
     if (live && (__ffs(same) - 1) == (int)(threadIdx.x & 31)) {
         atomicMin(rowmin + row, mn);
         atomicMax(rowmax + row, mx);
+    }
+}
+
+// Range maxima of the row maxima, per camera: level l holds the largest over rows
+// [i, i + 2^l) of the camera (clipped at its last row).  One block per camera.
+__global__ void __launch_bounds__(256) k_cut_rowmax_table(CamTable ct, const uint32_t *__restrict__ rowmax,
+                                                          uint32_t *st)
+{
+    const CamDev &cam = ct.c[blockIdx.x];
+    const int r0 = cam.row_off, H = cam.tiles_y;
+    for (int i = threadIdx.x; i < H; i += blockDim.x) st[r0 + i] = rowmax[r0 + i];
+    for (int l = 1; l < kCutLevels; ++l) {
+        __syncthreads();
+        const uint32_t *prev = st + (size_t)(l - 1) * ct.n_rows;
+        uint32_t *cur = st + (size_t)l * ct.n_rows;
+        const int half = 1 << (l - 1);
+        for (int i = threadIdx.x; i < H; i += blockDim.x)
+            cur[r0 + i] = i + half < H ? max(prev[r0 + i], prev[r0 + i + half]) : prev[r0 + i];
     }
 }
 
@@ -476,12 +522,15 @@ void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *
     int2 *ranges = ws_ptr<int2>(ws, L.tile_range);
 
     cudaMemsetAsync(hdr + kHdrN1, 0, 3 * sizeof(uint32_t), s);     // N1, N2, incomplete tiles
+    cudaMemsetAsync(hdr + kHdrFresh, 0, sizeof(uint32_t), s);       // fresh slots of the completion
     uint32_t *rowmin = ws_ptr<uint32_t>(ws, L.cut_rowmin), *rowmax = ws_ptr<uint32_t>(ws, L.cut_rowmax);
     cudaMemsetAsync(rowmin, 0xff, sizeof(uint32_t) * (size_t)ct.n_rows, s);
     cudaMemsetAsync(rowmax, 0, sizeof(uint32_t) * (size_t)ct.n_rows, s);
     k_cut_prepare<<<(unsigned)((L.n_tiles + 255) / 256), 256, 0, s>>>(
         ct, hdr, L.cut_sig, L.depth_cut ? 1 : 0, ws_ptr<uint32_t>(ws, L.cut_store), cut_cur,
         ws_ptr<int2>(ws, L.tile_range2), rowmin, rowmax);
+    uint32_t *rowmax_st = ws_ptr<uint32_t>(ws, L.cut_rowmax_st);
+    k_cut_rowmax_table<<<ct.n, 256, 0, s>>>(ct, rowmax, rowmax_st);
     k_store_u32<<<1, 1, 0, s>>>(hdr + kHdrCutSig, L.cut_sig);
     if (NE <= 0) {
         cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)L.n_tiles, s);
@@ -494,13 +543,13 @@ void launch_bin_sort(const CamTable &ct, const WsLayout &L, int N, const float *
     const int use_cut = L.depth_cut ? 1 : 0;
     {
         TimerScope tm(GS_TIMER_BINNING, s);
-        k_count_tiles<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], dk[dcur], cut_cur, rowmin, rowmax, use_cut,
-                                         counts, counts1, elem_cnt);
+        k_count_tiles<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], dk[dcur], cut_cur, rowmin, rowmax, rowmax_st,
+                                         use_cut, counts, counts1, elem_cnt);
         exclusive_scan_u32(counts, counts, NE, n_inst, aux, s);
         exclusive_scan_u32(counts1, counts1, NE, hdr + kHdrN1, aux, s);
         k_duplicate<1><<<nb, 256, 0, s>>>(ct, N, NE, proj, dv[dcur], dk[dcur], cut_cur, nullptr, use_cut, counts,
                                           counts1, hdr, (uint32_t)L.Mcap, ik[0], iv[0], inst_elem, elem_off, elem_cnt,
-                                          err);
+                                          nullptr, err);
         k_clear_walked<<<148 * 8, 256, 0, s>>>(n_inst, (uint32_t)L.Mcap, ws_ptr<uint8_t>(ws, L.inst_walked));
     }
     {
@@ -538,13 +587,17 @@ void launch_complete_lists(const CamTable &ct, const WsLayout &L, int N, const f
     const uint32_t *incomplete = ws_ptr<uint32_t>(ws, L.tile_incomplete);
     const unsigned nb = (unsigned)((NE + 255) / 256);
     k_incomplete_sat<<<ct.n, 1024, 0, s>>>(ct, incomplete, hdr, sat);
-    k_count_tiles2<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv, dk, cut_cur, incomplete, sat, hdr, counts2);
+    uint32_t *fresh2 = ws_ptr<uint32_t>(ws, L.counts);                 // (the first pass's offsets are in elem_off)
+    k_count_tiles2<<<nb, 256, 0, s>>>(ct, N, NE, proj, dv, dk, cut_cur, incomplete, sat, hdr,
+                                      ws_ptr<uint32_t>(ws, L.elem_cnt), counts2, fresh2);
     // with no flagged tile the scan is skipped too: the second sort's count stays the zero
     // binning set
     exclusive_scan_u32(counts2, counts2, NE, hdr + kHdrN2, ws_ptr<uint32_t>(ws, L.scan_aux), s, hdr + kHdrIncomplete);
-    k_duplicate<2><<<nb, 256, 0, s>>>(ct, N, NE, proj, dv, dk, cut_cur, incomplete, 1, nullptr, counts2, hdr,
+    exclusive_scan_u32(fresh2, fresh2, NE, hdr + kHdrFresh, ws_ptr<uint32_t>(ws, L.scan_aux), s, hdr + kHdrIncomplete);
+    k_duplicate<2><<<nb, 256, 0, s>>>(ct, N, NE, proj, dv, dk, cut_cur, incomplete, 1, fresh2, counts2, hdr,
                                       (uint32_t)L.Mcap, ik, iv, ws_ptr<uint32_t>(ws, L.inst_elem),
-                                      ws_ptr<uint32_t>(ws, L.elem_off), ws_ptr<uint32_t>(ws, L.elem_cnt), err);
+                                      ws_ptr<uint32_t>(ws, L.elem_off), ws_ptr<uint32_t>(ws, L.elem_cnt),
+                                      ws_ptr<uint8_t>(ws, L.inst_walked), err);
     uint32_t *scratch_v = scratch + ((L.Mcap + 3) & ~3ll);              // 16-byte aligned
     const int cur = radix_sort_pairs(ik, scratch, iv, scratch_v, L.Mcap, hdr + kHdrN2, bits_for(L.n_tiles),
                                      ws_ptr<uint32_t>(ws, L.sort_hist), s);

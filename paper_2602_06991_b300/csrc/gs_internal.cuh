@@ -321,6 +321,8 @@ constexpr int kHdrN1 = 4;           // header word: instances in front of the de
 constexpr int kHdrN2 = 5;           // header word: instances of unsaturated tiles behind it (second sort)
 constexpr int kHdrIncomplete = 6;   // header word: tiles the first walk left unsaturated with a cut
 constexpr int kHdrCutSig = 7;       // header word: the tile grid the recorded cuts belong to
+constexpr int kCutLevels = 13;      // sparse-table levels over tile rows (a camera has at most 4096)
+constexpr int kHdrFresh = 10;       // header word: slots the completion pass gave elements the first had none for
 constexpr uint32_t kNoCut = 0xffffffffu;
 constexpr float kCutMargin = 1.0625f;   // recorded cut = depth where the tile saturated x this
 constexpr int kHdrWaitLimitByte = 96;   // header bytes [96, 104): bound of the pipeline waits (0: default)
@@ -339,8 +341,8 @@ struct WsLayout {
     size_t header;             // 256 B: [0] error word, [1] instance count, [2] pieces, [3] multi-piece
                                // segments, [4] / [5] instances of the first / second tile sort,
                                // [6] incomplete tiles, [7] cut grid signature, [8] partial rows,
-                               // [9] pairs, [16] re-walk tile counter, [24..25] the wait limit
-                               // (64-bit, SM cycles, 0 = default)
+                               // [9] pairs, [10] fresh completion slots, [16] re-walk tile counter,
+                               // [24..25] the wait limit (64-bit, SM cycles, 0 = default)
     size_t depth_keys[2], depth_vals[2];   // NE
     size_t elem_cnt;           // NE (tiles touched, per element)
     size_t elem_off;           // NE (first pre-sort instance of each element)
@@ -355,6 +357,7 @@ struct WsLayout {
     size_t tile_incomplete;    // n_tiles: 1 where the first walk ended unsaturated with a cut
     size_t tile_sat;           // n_tiles: per camera, 2D prefix sums of tile_incomplete
     size_t cut_rowmin, cut_rowmax;   // per tile row: the smallest and largest current cut key
+    size_t cut_rowmax_st;      // kCutLevels x n_rows: range maxima of cut_rowmax over 2^l rows (per camera)
     size_t sort_hist;          // (kRadixBlocks + 1) x 256
     size_t scan_aux;           // scan block sums
     size_t inst_grad;          // Mcap x kGradVals floats (per-instance partial 2D gradients)
