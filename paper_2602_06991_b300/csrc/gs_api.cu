@@ -25,7 +25,7 @@ bool cfg_ok(const gs_config *cfg)
     return cfg && cfg->K >= 1 && cfg->K <= GS_MAX_K && cfg->D >= 8 && cfg->D <= 1024 && cfg->D % 8 == 0 &&
            tile_ok(cfg->tile_w, cfg->tile_h) && (cfg->feat_dtype == GS_F32 || cfg->feat_dtype == GS_BF16) &&
            cfg->max_instances >= 0 && cfg->max_feature_rows >= 0 &&
-           (cfg->topk_layout == 0 || ((cfg->topk_layout == 1 || cfg->topk_layout == 2) && cfg->K <= 16)) &&
+           (cfg->topk_layout == 0 || (cfg->topk_layout >= 1 && cfg->topk_layout <= 2 && cfg->K <= 16)) &&
            (cfg->depth_cut == 0 || cfg->depth_cut == 1);
 }
 

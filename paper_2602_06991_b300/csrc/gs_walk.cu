@@ -155,8 +155,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
                         if (lane == ql) tk.wmin = nmin;
                     }
                 }
-                continue;
-            }
+            } else {
             while (live && !done) {
             const int j = jc + __ffs(live) - 1;
             live &= live - 1;
@@ -181,6 +180,7 @@ __global__ void __launch_bounds__(TW *TH) k_walk_fwd(CamTable ct, int K, int N, 
             T = test_T;
             ++nc;
             tk.insert(w, s_g[j]);
+            }
             }
         }
     }
@@ -498,6 +498,7 @@ static bool walk_fwd_k(int KM, int kbuf, dim3 grid, cudaStream_t s, const CamTab
         }
         return false;
     }
+
     switch (KM) {
     case 4: GS_WF(4, 0); return true;
     case 8: GS_WF(8, 0); return true;

@@ -65,7 +65,8 @@ def test_pixel_count_and_workspace(lib):
 
 @pytest.mark.parametrize("field,value", [("K", 0), ("K", 33), ("D", 12), ("D", 0), ("D", 2048),
                                          ("tile_w", 12), ("feat_dtype", 7), ("max_instances", -1),
-                                         ("max_feature_rows", -1), ("depth_cut", 2), ("depth_cut", -1)])
+                                         ("max_feature_rows", -1), ("depth_cut", 2), ("depth_cut", -1),
+                                         ("topk_layout", 3), ("topk_layout", -1)])
 def test_bad_config_rejected_on_host(lib, field, value):
     from paper_2602_06991_b300 import _abi as A
     cams = _cams((64, 48))
