@@ -942,7 +942,17 @@ def cpu_baseline(workload, budget_s=15.0, seed=0, all_cores=True):
     beside it, one process per core (capped at 16: each holds its own copy of the scene)
     on disjoint random pixel draws, started by spawn."""
     done, el = _cpu_pixels(workload, budget_s, seed, seed)
-    out = {"value": round(done / el / 1e6, 9), "unit": UNIT, "cores": 1, "kind": "oracle",
+    cpu_model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    cpu_model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    out = {"value": round(done / el / 1e6, 9), "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model,
+           "host_cores": os.cpu_count(),
            "sample": f"{done} random pixels of the '{workload}' workload, forward + loss + backward, "
                      f"FP64 single-threaded C, {el:.1f} s (projection included)"}
     if all_cores:
