@@ -118,9 +118,11 @@ __global__ void __launch_bounds__(256) k_blend(long long n_pix, int K, int nch, 
 // flat pixels), never on the tile shape; the blend-only and the fused kernels group
 // identically and give bit-identical F.
 // ------------------------------------------------------------------------------------
+// pixels per warp of the group kernels, for the device code and the launch grids alike
+__host__ __device__ constexpr int group_pixels(int KM) { return KM <= 8 ? 4 : 2; }
 template <int KM>
 struct Group {
-    static constexpr int G = KM <= 8 ? 4 : 2;             // pixels per warp (KM <= 16)
+    static constexpr int G = group_pixels(KM);            // pixels per warp (KM <= 16)
 };
 
 struct GroupTable {
@@ -316,7 +318,7 @@ bool launch_blend(int dtype, int K, int D, long long n_pix, long long N, const i
     const int nch = dtype == GS_BF16 ? D / 8 : D / 4;
     const int cpl = group_cpl(dtype, K, nch);
     if (cpl) {
-        const int G = KM <= 8 ? 4 : 2;
+        const int G = group_pixels(KM);
         const long long warps = (n_pix + G - 1) / G;
         const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
         if (dtype == GS_BF16) {
@@ -473,7 +475,7 @@ bool launch_h(int dtype, int K, int D, long long n_pix, long long N, const int *
     const int nch = dtype == GS_BF16 ? D / 8 : D / 4;
     const int cpl = group_cpl(dtype, K, nch);
     if (cpl) {
-        const int G = KM <= 8 ? 4 : 2;
+        const int G = group_pixels(KM);
         const long long warps = (n_pix + G - 1) / G;
         const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
 #define GS_HG(KMV, BF)                                                                                            \
@@ -888,7 +890,7 @@ bool launch_blend_loss(const CamTable &ct, int dtype, int K, int D, long long n_
     bool ok = true;
     const int gcpl = group_cpl(dtype, K, nch);
     if (gcpl) {
-        const int G = KM <= 8 ? 4 : 2;
+        const int G = group_pixels(KM);
         const long long gw = (n_pix + G - 1) / G;
         const unsigned gblocks = (unsigned)((gw * 32 + 255) / 256);
 #define GS_BLG(KMV, BF)                                                                                          \
