@@ -225,7 +225,7 @@ TimerScope::~TimerScope()
 // backward call; created on first use, kept until the process exits.
 struct AuxStream {
     cudaStream_t s = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, hold = nullptr;
 };
 constexpr int kMaxDevices = 64;
 
@@ -252,7 +252,8 @@ static const AuxStream *aux_stream(cudaStream_t s)
     AuxStream n;
     if (cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&n.fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&n.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&n.join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&n.hold, cudaEventDisableTiming) != cudaSuccess) {
         failed[dev] = true;
         cudaGetLastError();
         return nullptr;
@@ -419,7 +420,9 @@ int gs_backward_ex(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, 
     // Two independent chains: (h, re-walk, projection adjoint) on `stream`, the
     // feature-gradient reduction on the device's auxiliary stream, forked after the
     // work already queued on `stream` and joined back before returning.  The re-walk is
-    // issue-bound and the reduction memory-bound, so they overlap.
+    // issue-bound and the reduction memory-bound, so they overlap.  On the CUDA-core block
+    // product's path `stream` also waits (aux->hold) for the block records, so that the
+    // product's CTAs are placed before the persistent re-walk's fill the SMs.
     std::unique_lock<std::mutex> lk(aux_mutex());
     const AuxStream *aux = with_feature ? aux_stream(s) : nullptr;
     if (aux) {
@@ -433,7 +436,7 @@ int gs_backward_ex(const gs_config *cfg, const gs_camera *cams, int32_t n_cams, 
         const bool h_ready =
             (flags & GS_BWD_H_FROM_LOSS) && blend_loss_writes_h(cfg->feat_dtype, cfg->K, cfg->D, n_gauss);
         ok = launch_feature_grad(ct, L, cfg->feat_dtype, n_gauss, topk_idx, topk_w, dL_dF, grads->feat, ws,
-                                 aux ? aux->s : s) &&
+                                 aux ? aux->s : s, aux ? s : nullptr, aux ? aux->hold : nullptr) &&
              (h_ready || launch_feature_h(L, cfg->feat_dtype, topk_idx, feats, dL_dF, ws, s));
     }
     ok = ok && launch_walk_bwd(ct, L, cfg->K, n_gauss, proj, ws, rgb_out, depth_out, topk_idx, topk_w, dL_dC, dL_dD,

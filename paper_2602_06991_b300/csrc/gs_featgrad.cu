@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(kFixCols *kFixGroups) k_fgrad_fixup(int D4, co
 }
 
 bool launch_tile_grad(const CamTable &ct, const WsLayout &L, int dtype, const int *topk_idx, const float *topk_w,
-                      const void *dLdF, void *ws, cudaStream_t s);
+                      const void *dLdF, void *ws, cudaStream_t s, cudaStream_t hold, cudaEvent_t hold_ev);
 
 // h = dL/dF . f per slot, read by the re-walk.
 bool launch_feature_h(const WsLayout &L, int dtype, const int *topk_idx, const void *feats, const void *dLdF,
@@ -229,7 +229,8 @@ bool launch_feature_h(const WsLayout &L, int dtype, const int *topk_idx, const v
 // The feature gradient proper: per-block partial rows, then per-Gaussian sums.  It
 // reads only the Top-K record and dL/dF, so it may run beside the re-walk.
 bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N, const int *topk_idx,
-                         const float *topk_w, const void *dLdF, float *grad_feat, void *ws, cudaStream_t s)
+                         const float *topk_w, const void *dLdF, float *grad_feat, void *ws, cudaStream_t s,
+                         cudaStream_t hold, cudaEvent_t hold_ev)
 {
     if (!L.use_tiles) return false;
     uint32_t *hdr = ws_ptr<uint32_t>(ws, L.header);
@@ -248,7 +249,7 @@ bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N
     const unsigned nbN = (unsigned)((N + 255) / 256);
 
     // per-block partial rows
-    if (!launch_tile_grad(ct, L, dtype, topk_idx, topk_w, dLdF, ws, s)) return false;
+    if (!launch_tile_grad(ct, L, dtype, topk_idx, topk_w, dLdF, ws, s, hold, hold_ev)) return false;
     // T4: (Gaussian, row) pairs sorted by Gaussian, segments, pieces
     k_markers<<<nbN, 256, 0, s>>>(N, pk[0], pv[0]);
     k_pair_count<<<1, 1, 0, s>>>(N, u_tot, (uint32_t)L.rows_cap, (const int *)hdr, n_pairs_dev);

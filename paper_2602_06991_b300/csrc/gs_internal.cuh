@@ -499,8 +499,11 @@ bool launch_blend_loss_mma(int K, int D, long long n_pix, const int *idx, const 
                            float *part, float *h, const int *err, cudaStream_t s);
 bool launch_feature_h(const WsLayout &L, int dtype, const int *topk_idx, const void *feats, const void *dLdF,
                       void *ws, cudaStream_t s);
+// hold / hold_ev (both or neither): the stream of the re-walk, made to wait (through
+// hold_ev) for the block records before the CUDA-core block product is queued on s
 bool launch_feature_grad(const CamTable &ct, const WsLayout &L, int dtype, int N, const int *topk_idx,
-                         const float *topk_w, const void *dLdF, float *grad_feat, void *ws, cudaStream_t s);
+                         const float *topk_w, const void *dLdF, float *grad_feat, void *ws, cudaStream_t s,
+                         cudaStream_t hold = nullptr, cudaEvent_t hold_ev = nullptr);
 bool tile_grad_supported(int dtype, int D, int K);
 // Feature-gradient pixel blocks: the largest of 8x8, 8x4, 4x4 whose dL/dF rows fit one
 // 64 KB shared-memory stage ({0, 0}: none).

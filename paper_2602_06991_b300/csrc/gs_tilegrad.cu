@@ -899,7 +899,7 @@ static int sm_count()
 
 template <int TW, int TH>
 static bool tile_launch(const CamTable &cb, const WsLayout &L, int dtype, const int *topk_idx, const float *topk_w,
-                        const void *dLdF, void *ws, cudaStream_t s)
+                        const void *dLdF, void *ws, cudaStream_t s, cudaStream_t hold, cudaEvent_t hold_ev)
 {
     constexpr int B = TW * TH;
     uint32_t *hdr = ws_ptr<uint32_t>(ws, L.header);
@@ -945,6 +945,16 @@ static bool tile_launch(const CamTable &cb, const WsLayout &L, int dtype, const 
     }
     TmaMaps maps;
     if (!make_maps(cb, dtype, L.D, dLdF, maps)) return false;
+    // The re-walk on the other stream holds until the block records are written, so it
+    // becomes ready together with the block product queued next: the product's CTAs (one
+    // per SM) are placed first and the re-walk's persistent CTAs fill the rest of each SM.
+    // Launched earlier, the re-walk takes every SM's registers and the product starts only
+    // as it drains.  (The tensor-core product, many CTAs per SM, is not held: it would take
+    // the SMs from the re-walk instead.)
+    if (hold && hold_ev && hold != s) {
+        if (cudaEventRecord(hold_ev, s) != cudaSuccess || cudaStreamWaitEvent(hold, hold_ev, 0) != cudaSuccess)
+            return false;
+    }
     const size_t sm3 = block_accum_smem(B, L.K, L.D, dtype);
     const int st_sz = (int)stage_bytes(B, L.K, dtype, L.D);
     const int nch = L.D / (dtype == GS_BF16 ? 8 : 4);
@@ -965,14 +975,14 @@ static bool tile_launch(const CamTable &cb, const WsLayout &L, int dtype, const 
 // row) pairs after N marker slots in pair buffer 0, the partial rows, and U_tot in
 // header word 8.
 bool launch_tile_grad(const CamTable &ct, const WsLayout &L, int dtype, const int *topk_idx, const float *topk_w,
-                      const void *dLdF, void *ws, cudaStream_t s)
+                      const void *dLdF, void *ws, cudaStream_t s, cudaStream_t hold, cudaEvent_t hold_ev)
 {
     const FgBlock fb = fg_block_shape(dtype, L.D, L.K);
     CamTable cb;
     retile(ct, fb.bw, fb.bh, cb);
-    if (fb.bw == 8 && fb.bh == 8) return tile_launch<8, 8>(cb, L, dtype, topk_idx, topk_w, dLdF, ws, s);
-    if (fb.bw == 8 && fb.bh == 4) return tile_launch<8, 4>(cb, L, dtype, topk_idx, topk_w, dLdF, ws, s);
-    if (fb.bw == 4 && fb.bh == 4) return tile_launch<4, 4>(cb, L, dtype, topk_idx, topk_w, dLdF, ws, s);
+    if (fb.bw == 8 && fb.bh == 8) return tile_launch<8, 8>(cb, L, dtype, topk_idx, topk_w, dLdF, ws, s, hold, hold_ev);
+    if (fb.bw == 8 && fb.bh == 4) return tile_launch<8, 4>(cb, L, dtype, topk_idx, topk_w, dLdF, ws, s, hold, hold_ev);
+    if (fb.bw == 4 && fb.bh == 4) return tile_launch<4, 4>(cb, L, dtype, topk_idx, topk_w, dLdF, ws, s, hold, hold_ev);
     return false;
 }
 
