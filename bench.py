@@ -391,11 +391,36 @@ def unique_rows(step):
     return int(torch.unique(v).numel())
 
 
+def graph_stage_ms(fn, reps):
+    """fn captured alone as one CUDA graph and replayed `reps` times (CUDA events on the
+    replaying stream): its device time as it runs inside the graph-replayed step, with no
+    host launch latency between its kernels and its streams ordered as the step orders them."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()                                        # warm inside the side stream before capture
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    g.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def stage_rooflines(step, hbm, reps=10):
     """The step's two HBM-bound stages timed alone with CUDA events on the launching
     stream (averaged over reps): the fused gather-blend + loss (one kernel and two small
     fixed-order sums) and the whole adjoint (gs_backward_ex), against their algorithmic
-    bytes."""
+    bytes.  The adjoint is timed twice: by direct launches, and captured alone as a graph
+    the way the step runs it (stage_ms_graph, frac_graph)."""
     import torch
     s = 2 if step.fdt == "bf16" else 4
     uniq = unique_rows(step)
@@ -409,6 +434,8 @@ def stage_rooflines(step, hbm, reps=10):
     ev[2].record()
     torch.cuda.synchronize()
     bl_ms, bw_ms = ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps
+    bw_graph_ms = graph_stage_ms(lambda: step.r.backward(step.lo["dL_dF"], step.lo["dL_dC"], step.lo["dL_dD"],
+                                                         grads=step.grads, h_from_loss=True), reps)
     blb = blend_loss_bytes(step.P, step.D, step.K, s, uniq)
     bwb = backward_bytes(step.P, step.D, step.K, s, step.N, step.N * len(step.cams))
     kname = ("gs_feature_blend_loss (k_blend_mma: tensor-core, bf16 rows)" if step.fdt == "bf16"
@@ -420,7 +447,8 @@ def stage_rooflines(step, hbm, reps=10):
            "backward": {"stage": "gs_backward_ex (feature gradient, re-walk, projection adjoint)", "bound": "hbm",
                         "achieved": round(bwb / (bw_ms * 1e-3) / 1e9, 1), "peak": hbm, "unit": "GB/s",
                         "frac": round(bwb / (bw_ms * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": bwb,
-                        "stage_ms": round(bw_ms, 4)}}
+                        "stage_ms": round(bw_ms, 4), "stage_ms_graph": round(bw_graph_ms, 4),
+                        "frac_graph": round(bwb / (bw_graph_ms * 1e-3) / 1e9 / hbm, 4)}}
     return out
 
 
@@ -569,6 +597,16 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     stages = {"select_ms": ev[0].elapsed_time(ev[1]), "blend_loss_ms": ev[1].elapsed_time(ev[2]),
               "backward_ms": ev[2].elapsed_time(ev[3])}
+    # the same three stages, each captured alone as a graph and replayed (as the step runs them)
+    stages_graph = None
+    if graph is not None:
+        r, o = step.r, step.out
+        stages_graph = {
+            "select_ms": graph_stage_ms(lambda: r._select_into(step.N, *step.inp[:4], o), 20),
+            "blend_loss_ms": graph_stage_ms(lambda: r.blend_loss(step.inp[4], step.tgt[0], step.tgt[1], step.tgt[2],
+                                                                 lo=step.lo), 20),
+            "backward_ms": graph_stage_ms(lambda: r.backward(step.lo["dL_dF"], step.lo["dL_dC"], step.lo["dL_dD"],
+                                                             grads=step.grads, h_from_loss=True), 20)}
     # blend kernel alone, averaged, for the roofline
     nb = 20
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -618,6 +656,7 @@ def run_ours(args, rank, world, local_rank):
                        **({"depth_cut": False} if args.no_depth_cut else {})),
         "graph": graph is not None, "status": status,
         "stages": {k: round(v, 4) for k, v in stages.items()},
+        "stages_graph": {k: round(v, 4) for k, v in stages_graph.items()} if stages_graph else None,
         "backward_roofline": sr["backward"],
         "roofline": {"kernel": ("gs_feature_blend_loss (k_blend_loss_group): the step's a4 stage" if step.fdt == "f32"
                                 else "gs_feature_blend_loss (k_blend_mma: tensor-core, bf16 rows): the step's a4 stage"),
