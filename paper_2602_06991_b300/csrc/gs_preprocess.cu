@@ -161,8 +161,13 @@ __global__ void __launch_bounds__(256) k_preprocess(CamTable ct, int N, const fl
 // the ranges longer than kElemSerial (Gaussians near the camera, over many tiles) are
 // then taken one at a time by the whole warp (strided lanes, a fixed shuffle tree).
 // Either way the order is fixed, so the result is deterministic.
+// STEP4: the per-thread loop takes four instances per step, their walked flags and then
+// the reached instances' loads issued before the adds (in the same order, so the same
+// sums).  It doubles the registers (64 against 32), so it is chosen only for grids of
+// under about two waves, which are bound by the loop's latency rather than by occupancy.
 constexpr uint32_t kElemSerial = 48;
 
+template <bool STEP4>
 __global__ void __launch_bounds__(256) k_elem_grad_sum(long long NE, const uint32_t *__restrict__ elem_off,
                                                        const uint32_t *__restrict__ elem_cnt,
                                                        const float *__restrict__ inst_grad,
@@ -180,7 +185,31 @@ __global__ void __launch_bounds__(256) k_elem_grad_sum(long long NE, const uint3
         float v[kGradVals];
 #pragma unroll
         for (int k = 0; k < kGradVals; ++k) v[k] = 0.f;
-        for (uint32_t i = 0; i < n; ++i) {
+        uint32_t i = 0;
+        if constexpr (STEP4) {
+            for (; i + 4 <= n; i += 4) {
+                bool wk[4];
+                float2 x[4][kGradVals / 2];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) wk[u] = walked[o0 + i + u] != 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 *pg = (const float2 *)(inst_grad + kGradVals * (size_t)(o0 + i + u));
+#pragma unroll
+                    for (int k = 0; k < kGradVals / 2; ++k) x[u][k] = wk[u] ? __ldg(pg + k) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (wk[u]) {
+#pragma unroll
+                        for (int k = 0; k < kGradVals / 2; ++k) {
+                            v[2 * k] += x[u][k].x;
+                            v[2 * k + 1] += x[u][k].y;
+                        }
+                    }
+            }
+        }
+        for (; i < n; ++i) {
             if (!walked[o0 + i]) continue;                  // past where its tile's walk stopped
             // 40-byte record, 8-byte aligned: five 8-byte loads
             const float2 *pg = (const float2 *)(inst_grad + kGradVals * (size_t)(o0 + i));
@@ -378,8 +407,15 @@ void launch_project_backward(const CamTable &ct, int N, const float *mean3d, con
 {
     if (N <= 0) return;
     long long NE = (long long)ct.n * N;
-    k_elem_grad_sum<<<(unsigned)((NE + 255) / 256), 256, 0, s>>>(NE, elem_off, elem_cnt, inst_grad, walked, err,
-                                                                   elem_grad);
+    const unsigned nb = (unsigned)((NE + 255) / 256);
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 148;
+    // four-instance steps while the grid is under two waves of that form (4 CTAs per SM)
+    if (nb <= (unsigned)(2 * 4 * sms))
+        k_elem_grad_sum<true><<<nb, 256, 0, s>>>(NE, elem_off, elem_cnt, inst_grad, walked, err, elem_grad);
+    else
+        k_elem_grad_sum<false><<<nb, 256, 0, s>>>(NE, elem_off, elem_cnt, inst_grad, walked, err, elem_grad);
     float *pp = gr->viewmat ? pose_part : nullptr;
     k_project_backward<<<(N + 255) / 256, 256, 0, s>>>(ct, N, mean3d, cov3d, (const float4 *)proj, elem_grad, err,
                                                       gr->opacity, gr->rgb, gr->mean3d, gr->cov3d, gr->mean2d,
